@@ -1,0 +1,356 @@
+#!/usr/bin/env python
+"""Benchmark: Barnes-Hut bodies/s per leapfrog step on one GB300.
+
+Workload (default): two colliding Plummer spheres of 8,388,608 equal-mass bodies each
+(N = 16,777,216, G = 1, total mass 1, centres at x = -5 and +5, closing speed 0.5), softening
+eps = 0.002, opening angle theta = 0.5, dt = 5e-4, FP32 forces with compensated (Kahan)
+accumulation and FP64 positions and velocities.  A step is one full kick-drift-kick step through
+the C ABI (nbody_step): kick + drift + root box, Morton keys, radix sort, permutation, node
+split, moments, walk + second kick.  Inputs (0.94 GB) are larger than L2 (129 MB), so no flush
+is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank advances its own independent replica (no collective on the
+data path): value = all ranks' bodies / max-over-ranks time.  `--impl reference` times the CPU
+oracle on a bounded sample of the same workload (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import io
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import ics  # noqa: E402
+
+METRIC = "Barnes-Hut bodies/s per step at N=16M theta=0.5"
+FLOP_PER_INTERACTION = 20          # softened monopole pair term, counting rsqrt as 2 flops
+FP32_LANES_PER_SM = 128            # FP32 FMA lanes per SM (Blackwell)
+CPU_SAMPLE_N = 1 << 20             # bodies in the CPU-baseline sample
+REF_SAMPLE_N = 1 << 19             # bodies per step of the reference arm
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="two_plummer_16m", choices=sorted(ics.WORKLOADS))
+    ap.add_argument("--n", type=int, default=0, help="override N (smaller runs, profiling)")
+    ap.add_argument("--precision", default="fp32_kahan", choices=["fp64", "fp32", "fp32_kahan"])
+    ap.add_argument("--theta", type=float, default=None)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def make_workload(name, n_override=0):
+    w = dict(ics.WORKLOADS[name])
+    n = n_override or w["n"]
+    if w["kind"] == "two_plummer":
+        pos, vel, mass = ics.two_plummer(n, seeds=w["seeds"])
+    elif w["kind"] == "plummer":
+        pos, vel, mass = ics.plummer(n, w["seed"])
+    elif w["kind"] == "disk_bulge":
+        pos, vel, mass = ics.disk_bulge(n, w["seed"])
+    else:
+        raise SystemExit(f"workload {name} is not a single system")
+    w["n"] = n
+    return w, pos, vel, mass
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ------------------------------------------------------------------ clocks during the timed region
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.f = None
+
+    def __enter__(self):
+        try:
+            self.f = tempfile.TemporaryFile(mode="w+")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or self.f is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.f.seek(0)
+        rows = [r for r in csv.reader(io.StringIO(self.f.read())) if len(r) >= 9]
+        sm, smax, power, reasons = [], [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+                power.append(float(r[3]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if r[5 + k].strip().lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "power_w_max": max(power), "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------ CPU oracle (baseline only)
+
+def oracle_step_rate(name, w, n_sample, steps=1):
+    """Bodies/s per step of the CPU oracle (FP64 Barnes-Hut + KDK) on `n_sample` bodies drawn
+    with the same recipe as the workload; OpenMP over all host cores for the force walk."""
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    oracle.set_threads(cores)
+    _, pos, vel, mass = make_workload(name, n_sample)
+    acc, _, _ = oracle.bh(pos, mass, 1.0, w["eps"], w["theta"])
+    t0 = time.perf_counter()
+    oracle.kdk(pos, vel, mass, acc, 1.0, w["eps"], w["theta"], w["dt"], steps)
+    dt = time.perf_counter() - t0
+    return n_sample * steps / dt, dt, cores
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+        if rank != 0:
+            dist.destroy_process_group()
+            return
+    w = dict(ics.WORKLOADS[args.workload])
+    if args.theta is not None:
+        w["theta"] = args.theta
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    oracle.set_threads(cores)
+    _, pos, vel, mass = make_workload(args.workload, REF_SAMPLE_N)
+    acc, _, _ = oracle.bh(pos, mass, 1.0, w["eps"], w["theta"])
+    for _ in range(args.warmup):
+        pos, vel, acc = oracle.kdk(pos, vel, mass, acc, 1.0, w["eps"], w["theta"], w["dt"], 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        pos, vel, acc = oracle.kdk(pos, vel, mass, acc, 1.0, w["eps"], w["theta"], w["dt"], 1)
+    dt = time.perf_counter() - t0
+    value = REF_SAMPLE_N * args.steps / dt
+    sample = (f"CPU oracle (FP64 pointer-octree Barnes-Hut by insertion + KDK), "
+              f"{REF_SAMPLE_N} bodies drawn with the workload's recipe per step")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "bodies/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{args.workload} sampled at N={REF_SAMPLE_N}",
+                   "theta": w["theta"], "eps": w["eps"], "dt": w["dt"]},
+        "cpu_baseline": {"value": value, "unit": "bodies/s", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "bodies/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------------------ GPU arm
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import __graft_entry__
+    import paper_2203_08966_gb300 as nb
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    if rank == 0 or ws == 1:
+        __graft_entry__.build()
+    if ws > 1:
+        dist.barrier()
+    nb.load_library()
+
+    w, pos, vel, mass = make_workload(args.workload, args.n)
+    if args.theta is not None:
+        w["theta"] = args.theta
+    n = w["n"]
+    prec = nb.PRECISIONS[args.precision]
+    dev = torch.device("cuda", local)
+    tp = torch.from_numpy(pos).to(dev)
+    tv = torch.from_numpy(vel).to(dev)
+    tm = torch.from_numpy(mass).to(dev)
+    stream = torch.cuda.current_stream()
+
+    ctx = nb.Context(n, 1.0, w["eps"], w["theta"], w["dt"], prec, stream=stream)
+    ctx.enable_timing(True)
+    for _ in range(args.warmup):
+        ctx.step(tp, tv, tm, 1)
+    ctx.sync()
+
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    walk_ms, phase = [], np.zeros(5)
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = nb.launch_count()
+    with ClockSampler(torch.cuda.current_device()) as clocks:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            ctx.step(tp, tv, tm, 1)
+            t = ctx.timings()
+            walk_ms.append(float(t[3]))
+            phase += t
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    launches = nb.launch_count() - l0
+    if ws > 1:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1)
+    t_max = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if ws > 1:
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+    ms_max = float(t_max.item())
+    value = n * ws * args.steps / (ms_max * 1e-3)
+
+    # interactions of the last timed step (counters of its walk) -> algorithmic FP32 flops
+    pp, pc = ctx.counters(n)
+    inter = float(pp.astype(np.float64).sum() + pc.astype(np.float64).sum())
+    walk_avg = float(np.mean(walk_ms))
+    achieved = inter * FLOP_PER_INTERACTION / (walk_avg * 1e-3) / 1e12
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peaks, peak_src = load_peaks()
+    clk = clocks.summary()
+    peak_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_tf = sms * FP32_LANES_PER_SM * 2 * peak_mhz * 1e6 / 1e12
+
+    # end to end through the host-buffer entry point: pinned inputs copied in, result read back
+    e2e = None
+    if not args.no_e2e:
+        hp = torch.from_numpy(pos).pin_memory().numpy()
+        hv = torch.from_numpy(vel).pin_memory().numpy()
+        hm = torch.from_numpy(mass).pin_memory().numpy()
+        ctx.enable_timing(False)
+        # a^(0) at the initial positions (set-up, outside the timed region)
+        ha = ctx.forces(torch.from_numpy(pos).to(dev), tm).cpu().pin_memory().numpy()
+        ctx.step_host(hp, hv, hm, 1, acc=ha)    # warm-up of the host path
+        if ws > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            ctx.step_host(hp, hv, hm, 1, acc=ha)
+        e2e_s = time.perf_counter() - t0
+        t_e = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+        if ws > 1:
+            dist.all_reduce(t_e, op=dist.ReduceOp.MAX)
+        e2e = {"value": n * ws * args.steps / float(t_e.item()), "unit": "bodies/s",
+               "h2d_bytes_per_step": int(hp.nbytes + hv.nbytes + ha.nbytes + hm.nbytes),
+               "d2h_bytes_per_step": int(hp.nbytes + hv.nbytes + ha.nbytes),
+               "api": "nbody_step_host (pinned host buffers, one step per call)"}
+    ctx.close()
+
+    if rank != 0:
+        if ws > 1:
+            dist.destroy_process_group()
+        return
+
+    cpu = None
+    if not args.no_cpu_baseline and ws == 1:
+        rate, secs, cores = oracle_step_rate(args.workload, w, CPU_SAMPLE_N)
+        cpu = {"value": rate, "unit": "bodies/s", "cores": cores, "kind": "oracle",
+               "sample": f"one KDK step of the FP64 CPU oracle on {CPU_SAMPLE_N} bodies drawn "
+                         f"with the same recipe ({secs:.1f} s)"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "bodies/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp64": "f64", "fp32": "f32", "fp32_kahan": "f32"}[args.precision],
+        "data": "synthetic",
+        "config": {"workload": f"{args.workload}", "n": n, "theta": w["theta"], "eps": w["eps"],
+                   "dt": w["dt"], "precision": args.precision,
+                   "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas{ws}"},
+        "phase_ms": {k: float(v / args.steps) for k, v in
+                     zip(("kick_box_keys", "sort", "permute_split_moments", "walk", "step"),
+                         phase)},
+        "interactions_per_step": inter,
+        "interactions_per_s": inter / (walk_avg * 1e-3),
+        "roofline": {"kernel": "walk32 (Kahan)" if args.precision == "fp32_kahan" else
+                     ("walk32" if args.precision == "fp32" else "walk64"),
+                     "bound": "alu", "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
+                     "frac": achieved / peak_tf, "traffic": None,
+                     "peak_source": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x "
+                                    f"{peak_mhz:.0f} MHz ({peak_src} max SM clock)",
+                     "walk_ms": walk_avg},
+        "clocks": clk,
+        "gpu_launches": int(launches),
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,180 @@
+/*
+ * nbody.h -- C ABI of the GB300 Barnes-Hut timestep library (libnbody.so).
+ *
+ * Method: A. Brandt, "On Distributed Gravitational N-Body Simulations" (arXiv 2203.08966).
+ * One call advances or evaluates one gravitational system on one GPU:
+ *   octree build  (§3 and Algorithm 2 "Build Tree"; Morton keys of §4.4; the tree is the
+ *                  uncompressed octree whose leaves hold one body, or several bodies that share
+ *                  one level-21 cell),
+ *   moments       (Algorithm 2: total mass and centre of mass from the leaves to the root;
+ *                  eq. `approxforce` of §2.1),
+ *   traversal     (Algorithm 2 "Compute Cell Force": for every body, the children of each
+ *                  opened cell are visited in Morton order; a leaf gives particle-particle
+ *                  interactions, a cell with side l and centre-of-mass distance d is accepted
+ *                  when l/d < theta, evaluated as l*l < theta*theta*d*d, else it is opened;
+ *                  the root itself is never tested),
+ *   softened pair kernel  (eq. `motion` of §2.1 with |r|^2 replaced by |r|^2 + eps^2),
+ *   leapfrog      (kick-drift-kick, eqs. `leapkick1`, `leapdrift`, `leapkick2` of §2.3).
+ *
+ * Conventions shared by every entry point
+ *   - Array layout is structure-of-arrays float64: pos = [x_0..x_{N-1} | y_0.. | z_0..] (3N
+ *     doubles), vel likewise, mass[N], acc[3N].  Bodies are in the caller's order ("user
+ *     order") on input and output; the library reorders internally.
+ *   - Pointers named d_* are DEVICE pointers on the context's device; h_* are HOST pointers.
+ *     The caller owns every buffer it passes and must keep it alive until the call's work on
+ *     the context stream has completed; the library never frees caller memory.
+ *   - All work is enqueued on the context's CUDA stream.  Entry points that must read a
+ *     device-side size (the node count of the tree) synchronise that stream once per build;
+ *     every other call returns without waiting.  Results in device buffers are valid once the
+ *     stream has reached the call; nbody_sync() waits for it and reports device-side errors.
+ *   - Errors are returned as nbody_status codes; nbody_last_error() gives a one-line message.
+ *     A failed call leaves caller buffers in an unspecified state but the context usable,
+ *     except after NBODY_ECUDA, after which the context should be destroyed.
+ *   - Preconditions: n <= n_capacity; masses positive and finite; positions finite;
+ *     theta >= 0, eps >= 0, G and dt finite.  Violations found on the host give NBODY_EINVAL.
+ *   - Contexts are not thread-safe: one host thread at a time per context.
+ */
+#ifndef NBODY_H
+#define NBODY_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct nbody_ctx nbody_ctx;
+
+typedef enum {
+    NBODY_OK = 0,
+    NBODY_EINVAL = 1,    /* bad argument (null pointer, size, parameter) */
+    NBODY_ENOMEM = 2,    /* device or host allocation failed */
+    NBODY_ECUDA = 3,     /* a CUDA runtime call or kernel launch failed */
+    NBODY_ESTACK = 4,    /* reserved: a traversal exceeded its work bound */
+    NBODY_ETIMEOUT = 5,  /* a bounded device-side wait gave up */
+    NBODY_ESTATE = 6     /* call out of order (e.g. introspection before any build) */
+} nbody_status;
+
+typedef enum {
+    NBODY_FP64 = 0,        /* pair interactions, walk and accumulation in FP64 */
+    NBODY_FP32 = 1,        /* FP32 pair interactions, MAC and accumulation */
+    NBODY_FP32_KAHAN = 2   /* FP32 pair interactions with compensated (Kahan) accumulation */
+} nbody_precision;
+
+/* Physical and numerical parameters.  G: gravitational constant; eps: Plummer softening length
+ * (§2.1); theta: opening angle of the acceptance test l/d < theta (§3); dt: leapfrog time step
+ * (§2.3); precision: nbody_precision; flags: 0 (reserved, must be 0). */
+typedef struct {
+    double G;
+    double eps;
+    double theta;
+    double dt;
+    int32_t precision;
+    uint32_t flags;
+} nbody_params;
+
+/* One node of the octree in the paper's pre-order serialisation (§4.2) with its hashed-octree
+ * key (§4.7: root key 1, child key = parent key << 3 | octant, octant digit = 4x + 2y + z).
+ * first = rank of the node's first body in Morton order, count = bodies in its subtree. */
+typedef struct {
+    uint64_t key;
+    int32_t level;
+    int32_t child_mask;   /* bit c set when octant c has a child */
+    int64_t first;
+    int64_t count;
+} nbody_tree_record;
+
+/* Creates a context on the current CUDA device for systems of up to n_capacity bodies.
+ * cuda_stream: a cudaStream_t (NULL = the legacy default stream).  Allocates the per-body
+ * working set (about 120 bytes per body plus the tree, which is grown on demand).
+ * Errors: EINVAL (out == NULL, n_capacity < 0 or > 2^30, bad params), ENOMEM, ECUDA. */
+nbody_status nbody_create(nbody_ctx **out, int64_t n_capacity, const nbody_params *p,
+                          void *cuda_stream);
+
+/* Releases all device and host memory of the context after its stream has drained. */
+nbody_status nbody_destroy(nbody_ctx *c);
+
+/* Replaces the parameters; the next nbody_step recomputes the starting acceleration. */
+nbody_status nbody_set_params(nbody_ctx *c, const nbody_params *p);
+
+/* Builds the octree of d_pos/d_mass (n bodies): root box, Morton keys, sort, node split and
+ * moments (Algorithm 2, "Build Tree" and the leaves-to-root pass).  Synchronises the stream
+ * once to learn the node count.  Errors: EINVAL, ENOMEM (tree larger than the device can
+ * hold), ECUDA. */
+nbody_status nbody_build_tree(nbody_ctx *c, const double *d_pos, const double *d_mass,
+                              int64_t n);
+
+/* Barnes-Hut accelerations of all bodies (Algorithm 2): builds the tree of d_pos/d_mass and
+ * writes d_acc (3n doubles, user order) in the context's precision.  Per-body interaction
+ * counters (pp: particle-particle, pc: particle-cell; Algorithm 9 counts pp + 2 pc) are kept
+ * for nbody_get_counters.  Errors as nbody_build_tree. */
+nbody_status nbody_forces(nbody_ctx *c, const double *d_pos, const double *d_mass, int64_t n,
+                          double *d_acc);
+
+/* Advances d_pos/d_vel in place by nsteps kick-drift-kick steps of the context's dt (§2.3):
+ * v += a dt/2; r += v dt; a = BH(r); v += a dt/2.  The acceleration at the current positions
+ * is kept in the context between calls; the first call after create, set_params or a change
+ * of n computes it first.  Synchronises once per step (node count).  nsteps >= 0. */
+nbody_status nbody_step(nbody_ctx *c, double *d_pos, double *d_vel, const double *d_mass,
+                        int64_t n, int32_t nsteps);
+
+/* nbody_step on HOST buffers (the call is synchronous).  Copies h_pos, h_vel, h_mass (and
+ * h_acc) to the device, runs nsteps kick-drift-kick steps and copies h_pos, h_vel (and h_acc)
+ * back before returning.  h_acc (3n doubles, in/out, may be NULL): on entry the acceleration
+ * at h_pos, as left by the previous call, so the first kick needs no force evaluation; on exit
+ * the acceleration at the new positions.  With h_acc == NULL the acceleration at h_pos is
+ * computed first.  Page-locked host buffers give the fastest copies.  The device copies are
+ * scratch owned by the context and allocated on the first call. */
+nbody_status nbody_step_host(nbody_ctx *c, double *h_pos, double *h_vel, double *h_acc,
+                             const double *h_mass, int64_t n, int32_t nsteps);
+
+/* Direct-sum accelerations (Algorithm 1) of nt target bodies against all n sources, in the
+ * context's precision (FP32_KAHAN runs as FP32).  d_targets: device int64 user indices, or NULL
+ * for all n bodies (then nt is ignored).  d_acc: 3*nt doubles, row-major (x row, y row, z row).
+ * Sources are summed in ascending index order; a target never interacts with itself. */
+nbody_status nbody_direct_forces(nbody_ctx *c, const double *d_pos, const double *d_mass,
+                                 int64_t n, const int64_t *d_targets, int64_t nt, double *d_acc);
+
+/* Waits for the context stream and reports any device-side error flag. */
+nbody_status nbody_sync(nbody_ctx *c);
+
+/* ---- introspection (copies to caller-provided HOST buffers; synchronous) ---- */
+
+/* Sorted Morton keys and the user index of each sorted body, from the last build
+ * (n entries each).  Errors: ESTATE before any build. */
+nbody_status nbody_get_keys(nbody_ctx *c, uint64_t *h_keys_sorted, uint32_t *h_ids_sorted);
+
+/* Root box of the last build: h_box[0..2] = min corner, [3] = side L, [4] = 2^21 / L. */
+nbody_status nbody_get_box(nbody_ctx *c, double *h_box);
+
+/* Pre-order node records of the last build.  Writes *n_nodes; fills h_records when
+ * h_records != NULL and cap >= *n_nodes (else only *n_nodes is written). */
+nbody_status nbody_get_tree(nbody_ctx *c, int64_t *n_nodes, nbody_tree_record *h_records,
+                            int64_t cap);
+
+/* FP64 moments of the last build, pre-order: h_out[4*k .. 4*k+3] = (m, x, y, z) of node k. */
+nbody_status nbody_get_moments(nbody_ctx *c, double *h_out, int64_t cap_nodes);
+
+/* Interaction counters of the last force evaluation, user order (n entries each). */
+nbody_status nbody_get_counters(nbody_ctx *c, uint32_t *h_pp, uint32_t *h_pc);
+
+/* Device time in milliseconds of the phases of the last build/force/step call (for
+ * nbody_step: of its last step), measured with CUDA events recorded on the context stream:
+ * [0] kick/drift + box + keys, [1] radix sort, [2] permutation + node split + moments,
+ * [3] walk, [4] whole call.  Recorded only while timing is enabled with nbody_enable_timing;
+ * nbody_get_timings waits for the last call's final event. */
+nbody_status nbody_enable_timing(nbody_ctx *c, int32_t on);
+nbody_status nbody_get_timings(nbody_ctx *c, float *h_ms5);
+
+/* Number of kernel launches the library has made in this process (all contexts), so callers
+ * can count the launches inside a timed region.  Errors: EINVAL when out == NULL. */
+nbody_status nbody_get_launch_count(int64_t *out);
+
+/* Copies the last error message (NUL-terminated, truncated to cap bytes). */
+nbody_status nbody_last_error(nbody_ctx *c, char *buf, int64_t cap);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NBODY_H */

@@ -13,7 +13,8 @@ Parity status of each function (what pins it is in ``tests/test_oracle_pins.py``
     sort_pairs                           pinned (Python sorted())
     tree build / records                 pinned (independent prefix-grouping construction,
                                          paper's octal key examples, invariants)
-    moments                              pinned (root centre of mass = global centre of mass)
+    moments                              pinned (root centre of mass = global centre of mass;
+                                         every cell = mass-weighted mean of its children)
     direct                               pinned (Kepler closed forms, Newton's third law)
     tree forces (Barnes-Hut)             pinned (theta = 0 equals direct sum, N = 2 exact,
                                          brute-force recursive walk on small N)
@@ -77,6 +78,7 @@ def _load():
         "orc_tree_box": (None, [vp, _f64p]),
         "orc_tree_root": (None, [vp, _f64p]),
         "orc_tree_records": (i64, [vp, _i64p, vp]),
+        "orc_tree_moments": (i64, [vp, _f64p]),
         "orc_tree_forces": (None, [vp, vp, i64, d, d, d, _f64p, vp, vp]),
         "orc_bh": (None, [_f64p, _f64p, i64, d, d, d, _f64p, vp, vp]),
         "orc_kdk": (None, [_f64p, _f64p, _f64p, i64, _f64p, d, d, d, d, ctypes.c_int32,
@@ -212,6 +214,13 @@ class Tree:
         if with_leaf_order:
             return rec, order[:self.n]
         return rec
+
+    def moments(self):
+        """(n_nodes, 4) float64: m, x, y, z of every node, in the pre-order of records()."""
+        nn = self.stats()["nodes"]
+        out = np.zeros((max(nn, 1), 4))
+        k = _load().orc_tree_moments(self._h, out)
+        return out[:k]
 
     def forces(self, G=1.0, eps=0.0, theta=0.5, targets=None):
         """Barnes-Hut accelerations (3, nt) and counters pp, pc (nt,) uint32."""

@@ -409,6 +409,27 @@ int64_t orc_tree_records(void *h, int64_t *rec, int64_t *leaf_ids)
     return k;
 }
 
+/* Moments of every node in the pre-order of orc_tree_records: out[4k..4k+3] = (m, x, y, z). */
+static void emit_moments(const orc_tree *t, int32_t nd, double *out, int64_t *k)
+{
+    const orc_node *N = &t->nodes[nd];
+    double *r = out + 4 * (*k);
+    (*k)++;
+    r[0] = N->m; r[1] = N->x; r[2] = N->y; r[3] = N->z;
+    if (N->is_leaf) return;
+    for (int c = 0; c < 8; ++c)
+        if (N->child[c] >= 0) emit_moments(t, N->child[c], out, k);
+}
+
+int64_t orc_tree_moments(void *h, double *out)
+{
+    orc_tree *t = (orc_tree *)h;
+    if (t->n == 0) return 0;
+    int64_t k = 0;
+    emit_moments(t, 0, out, &k);
+    return k;
+}
+
 /* ------------------------------------------------------------------ */
 /* Barnes-Hut walk (Algorithm 2, "Compute Cell Force"; counters of Algorithm 9). */
 /* ------------------------------------------------------------------ */

@@ -1,0 +1,304 @@
+"""GB300 Barnes-Hut timestep (arXiv 2203.08966, Algorithm 2 with kick-drift-kick leapfrog).
+
+A thin ctypes binding over the C ABI in ``include/nbody.h`` (``libnbody.so`` next to this file,
+built by ``build_lib.build()``).  This module only marshals arguments: every step of the method
+(box, Morton keys, radix sort, node split, moments, walk, leapfrog) runs in the library's CUDA
+kernels.  There is no CPU fallback: importing works without the library, but creating a
+``Context`` raises when ``libnbody.so`` is missing or no GPU is present.
+
+Tensors are torch float64 CUDA tensors in the library's structure-of-arrays layout:
+``pos`` and ``vel`` of shape (3, N) (rows x, y, z), ``mass`` of shape (N,), ``acc`` (3, N).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libnbody.so")
+
+FP64, FP32, FP32_KAHAN = 0, 1, 2
+PRECISIONS = {"fp64": FP64, "fp32": FP32, "fp32_kahan": FP32_KAHAN}
+
+STATUS = {0: "NBODY_OK", 1: "NBODY_EINVAL", 2: "NBODY_ENOMEM", 3: "NBODY_ECUDA",
+          4: "NBODY_ESTACK", 5: "NBODY_ETIMEOUT", 6: "NBODY_ESTATE"}
+
+# Every entry point declared in include/nbody.h.
+EXPORTS = ("nbody_create", "nbody_destroy", "nbody_set_params", "nbody_build_tree",
+           "nbody_forces", "nbody_step", "nbody_step_host", "nbody_direct_forces", "nbody_sync",
+           "nbody_get_keys", "nbody_get_box", "nbody_get_tree", "nbody_get_moments",
+           "nbody_get_counters", "nbody_enable_timing", "nbody_get_timings",
+           "nbody_last_error", "nbody_get_launch_count")
+
+
+class NBodyError(RuntimeError):
+    def __init__(self, status, what, msg=""):
+        self.status = status
+        super().__init__(f"{what} -> {STATUS.get(status, status)}{': ' + msg if msg else ''}")
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("G", ctypes.c_double), ("eps", ctypes.c_double), ("theta", ctypes.c_double),
+                ("dt", ctypes.c_double), ("precision", ctypes.c_int32),
+                ("flags", ctypes.c_uint32)]
+
+
+class TreeRecord(ctypes.Structure):
+    _fields_ = [("key", ctypes.c_uint64), ("level", ctypes.c_int32),
+                ("child_mask", ctypes.c_int32), ("first", ctypes.c_int64),
+                ("count", ctypes.c_int64)]
+
+
+_RECORD_DTYPE = np.dtype([("key", np.uint64), ("level", np.int32), ("child_mask", np.int32),
+                          ("first", np.int64), ("count", np.int64)])
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Loads libnbody.so (raises OSError when it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise OSError(f"{path} is missing: build it with paper_2203_08966_gb300.build_lib.build()")
+    lib = ctypes.CDLL(path)
+    vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
+    P = ctypes.POINTER(Params)
+    sig = {
+        "nbody_create": [ctypes.POINTER(vp), i64, P, vp],
+        "nbody_destroy": [vp],
+        "nbody_set_params": [vp, P],
+        "nbody_build_tree": [vp, vp, vp, i64],
+        "nbody_forces": [vp, vp, vp, i64, vp],
+        "nbody_step": [vp, vp, vp, vp, i64, i32],
+        "nbody_step_host": [vp, vp, vp, vp, vp, i64, i32],
+        "nbody_direct_forces": [vp, vp, vp, i64, vp, i64, vp],
+        "nbody_sync": [vp],
+        "nbody_get_keys": [vp, vp, vp],
+        "nbody_get_box": [vp, vp],
+        "nbody_get_tree": [vp, ctypes.POINTER(i64), vp, i64],
+        "nbody_get_moments": [vp, vp, i64],
+        "nbody_get_counters": [vp, vp, vp],
+        "nbody_enable_timing": [vp, i32],
+        "nbody_get_timings": [vp, vp],
+        "nbody_last_error": [vp, ctypes.c_char_p, i64],
+        "nbody_get_launch_count": [ctypes.POINTER(i64)],
+    }
+    for name, args in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _dptr(t, dtype, shape=None, name="tensor"):
+    """Device pointer of a contiguous CUDA tensor of the given dtype (and shape)."""
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _hptr(a, dtype, shape, name):
+    if not isinstance(a, np.ndarray) or a.dtype != dtype or not a.flags.c_contiguous:
+        raise TypeError(f"{name} must be a C-contiguous numpy {np.dtype(dtype).name} array")
+    if tuple(a.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}")
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+class Context:
+    """One nbody_ctx: a system of up to ``capacity`` bodies on the current CUDA device.
+
+    All work goes to the CUDA stream that is current when the context is created (or
+    ``stream``, a torch.cuda.Stream)."""
+
+    def __init__(self, capacity, G=1.0, eps=0.0, theta=0.5, dt=1e-3, precision=FP32,
+                 stream=None):
+        import torch
+        self._lib = load_library()
+        if isinstance(precision, str):
+            precision = PRECISIONS[precision]
+        self.params = Params(G, eps, theta, dt, precision, 0)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        h = ctypes.c_void_p()
+        st = self._lib.nbody_create(ctypes.byref(h), int(capacity), ctypes.byref(self.params),
+                                    ctypes.c_void_p(stream.cuda_stream))
+        if st != 0:
+            raise NBodyError(st, "nbody_create")
+        self._h = h
+        self.capacity = int(capacity)
+
+    # ---------------------------------------------------------------- plumbing
+    def _check(self, st, what):
+        if st != 0:
+            buf = ctypes.create_string_buffer(256)
+            self._lib.nbody_last_error(self._h, buf, 256)
+            raise NBodyError(st, what, buf.value.decode(errors="replace"))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.nbody_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_params(self, G=None, eps=None, theta=None, dt=None, precision=None):
+        p = self.params
+        if isinstance(precision, str):
+            precision = PRECISIONS[precision]
+        new = Params(p.G if G is None else G, p.eps if eps is None else eps,
+                     p.theta if theta is None else theta, p.dt if dt is None else dt,
+                     p.precision if precision is None else precision, 0)
+        self._check(self._lib.nbody_set_params(self._h, ctypes.byref(new)), "nbody_set_params")
+        self.params = new
+
+    # ---------------------------------------------------------------- compute
+    def build_tree(self, pos, mass):
+        import torch
+        n = int(mass.shape[0])
+        self._check(self._lib.nbody_build_tree(self._h, _dptr(pos, torch.float64, (3, n), "pos"),
+                                               _dptr(mass, torch.float64, (n,), "mass"), n),
+                    "nbody_build_tree")
+
+    def forces(self, pos, mass, acc=None):
+        import torch
+        n = int(mass.shape[0])
+        if acc is None:
+            acc = torch.empty((3, n), dtype=torch.float64, device=pos.device)
+        self._check(self._lib.nbody_forces(self._h, _dptr(pos, torch.float64, (3, n), "pos"),
+                                           _dptr(mass, torch.float64, (n,), "mass"), n,
+                                           _dptr(acc, torch.float64, (3, n), "acc")),
+                    "nbody_forces")
+        return acc
+
+    def step(self, pos, vel, mass, nsteps=1):
+        import torch
+        n = int(mass.shape[0])
+        self._check(self._lib.nbody_step(self._h, _dptr(pos, torch.float64, (3, n), "pos"),
+                                         _dptr(vel, torch.float64, (3, n), "vel"),
+                                         _dptr(mass, torch.float64, (n,), "mass"), n,
+                                         int(nsteps)), "nbody_step")
+
+    def step_host(self, pos, vel, mass, nsteps=1, acc=None):
+        """Host-buffer step on numpy float64 arrays (ideally page-locked), updated in place.
+
+        ``acc`` (3, N), optional, in/out: the acceleration at ``pos`` from the previous call."""
+        n = int(mass.shape[0])
+        ap = None if acc is None else _hptr(acc, np.float64, (3, n), "acc")
+        self._check(self._lib.nbody_step_host(self._h, _hptr(pos, np.float64, (3, n), "pos"),
+                                              _hptr(vel, np.float64, (3, n), "vel"), ap,
+                                              _hptr(mass, np.float64, (n,), "mass"), n,
+                                              int(nsteps)), "nbody_step_host")
+
+    def direct_forces(self, pos, mass, targets=None, acc=None):
+        import torch
+        n = int(mass.shape[0])
+        nt = n if targets is None else int(targets.shape[0])
+        if acc is None:
+            acc = torch.empty((3, nt), dtype=torch.float64, device=pos.device)
+        tp = None if targets is None else _dptr(targets, torch.int64, (nt,), "targets")
+        self._check(self._lib.nbody_direct_forces(self._h,
+                                                  _dptr(pos, torch.float64, (3, n), "pos"),
+                                                  _dptr(mass, torch.float64, (n,), "mass"), n,
+                                                  tp, nt,
+                                                  _dptr(acc, torch.float64, (3, nt), "acc")),
+                    "nbody_direct_forces")
+        return acc
+
+    def sync(self):
+        self._check(self._lib.nbody_sync(self._h), "nbody_sync")
+
+    # ---------------------------------------------------------------- introspection
+    def keys(self, n):
+        k = np.zeros(n, dtype=np.uint64)
+        ids = np.zeros(n, dtype=np.uint32)
+        self._check(self._lib.nbody_get_keys(self._h, k.ctypes.data_as(ctypes.c_void_p),
+                                             ids.ctypes.data_as(ctypes.c_void_p)),
+                    "nbody_get_keys")
+        return k, ids
+
+    def box(self):
+        b = np.zeros(5)
+        self._check(self._lib.nbody_get_box(self._h, b.ctypes.data_as(ctypes.c_void_p)),
+                    "nbody_get_box")
+        return b
+
+    def tree(self):
+        """Pre-order records (n_nodes, 5) int64: key, level, child mask, first rank, count."""
+        nn = ctypes.c_int64()
+        self._check(self._lib.nbody_get_tree(self._h, ctypes.byref(nn), None, 0), "nbody_get_tree")
+        recs = np.zeros(max(nn.value, 1), dtype=_RECORD_DTYPE)
+        self._check(self._lib.nbody_get_tree(self._h, ctypes.byref(nn),
+                                             recs.ctypes.data_as(ctypes.c_void_p), nn.value),
+                    "nbody_get_tree")
+        recs = recs[:nn.value]
+        out = np.empty((nn.value, 5), dtype=np.int64)
+        out[:, 0] = recs["key"].view(np.int64)
+        out[:, 1] = recs["level"]
+        out[:, 2] = recs["child_mask"]
+        out[:, 3] = recs["first"]
+        out[:, 4] = recs["count"]
+        return out
+
+    def n_nodes(self):
+        nn = ctypes.c_int64()
+        self._check(self._lib.nbody_get_tree(self._h, ctypes.byref(nn), None, 0), "nbody_get_tree")
+        return nn.value
+
+    def moments(self):
+        """(n_nodes, 4) float64: m, x, y, z of every node in pre-order."""
+        nn = self.n_nodes()
+        out = np.zeros((max(nn, 1), 4))
+        self._check(self._lib.nbody_get_moments(self._h, out.ctypes.data_as(ctypes.c_void_p), nn),
+                    "nbody_get_moments")
+        return out[:nn]
+
+    def counters(self, n):
+        pp = np.zeros(n, dtype=np.uint32)
+        pc = np.zeros(n, dtype=np.uint32)
+        self._check(self._lib.nbody_get_counters(self._h, pp.ctypes.data_as(ctypes.c_void_p),
+                                                 pc.ctypes.data_as(ctypes.c_void_p)),
+                    "nbody_get_counters")
+        return pp, pc
+
+    def enable_timing(self, on=True):
+        self._check(self._lib.nbody_enable_timing(self._h, 1 if on else 0), "nbody_enable_timing")
+
+    def timings(self):
+        """Device ms of the last call: box+keys, sort, split+moments, walk, whole call."""
+        t = np.zeros(5, dtype=np.float32)
+        self._check(self._lib.nbody_get_timings(self._h, t.ctypes.data_as(ctypes.c_void_p)),
+                    "nbody_get_timings")
+        return t
+
+
+def launch_count() -> int:
+    """Kernel launches made by the library so far in this process."""
+    v = ctypes.c_int64()
+    st = load_library().nbody_get_launch_count(ctypes.byref(v))
+    if st != 0:
+        raise NBodyError(st, "nbody_get_launch_count")
+    return int(v.value)

@@ -1,0 +1,779 @@
+// Tree-build kernels: root box, Morton keys, LSD radix sort, body permutation, octree node
+// split and bottom-up moments.
+//
+// Paper: Algorithm 2 ("Build Tree", moments from the leaves to the root), §4.4 (Morton keys:
+// 21 bits per axis interleaved with x > y > z), §4.7 (hashed cell keys), §4.2 (pre-order node
+// serialisation).  Every step here is integer or exact FP64 work, so keys, order and topology
+// are bit-identical to a plain CPU evaluation of the same definitions.
+#include <float.h>
+#include <atomic>
+#include <math.h>
+
+#include "nbody_internal.cuh"
+
+namespace nb {
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// ------------------------------------------------------------------------------------------
+// Root box (§3: the root is the bounding box of all particles; §4.4 maps it onto [0, 2^21)).
+// ------------------------------------------------------------------------------------------
+
+constexpr int kBoxThreads = 256;
+
+__device__ __forceinline__ void block_minmax6(double v[6], double *out)
+{
+    // v[0..2] minima, v[3..5] maxima -> out[0..5] written by thread 0
+    __shared__ double sh[6][kBoxThreads / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        double x = v[k];
+        for (int o = 16; o > 0; o >>= 1) {
+            double y = __shfl_xor_sync(kFull, x, o);
+            x = k < 3 ? fmin(x, y) : fmax(x, y);
+        }
+        if (lane == 0) sh[k][wid] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < 6; ++k) {
+            double x = sh[k][0];
+            for (int w = 1; w < kBoxThreads / 32; ++w) x = k < 3 ? fmin(x, sh[k][w]) : fmax(x, sh[k][w]);
+            out[k] = x;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kBoxThreads) bbox_partials_kernel(const double *__restrict__ pos,
+                                                                    int n, double *partials)
+{
+    double v[6] = {DBL_MAX, DBL_MAX, DBL_MAX, -DBL_MAX, -DBL_MAX, -DBL_MAX};
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            double x = pos[(size_t)d * n + i];
+            v[d] = fmin(v[d], x);
+            v[3 + d] = fmax(v[3 + d], x);
+        }
+    }
+    block_minmax6(v, partials + 6 * blockIdx.x);
+}
+
+// Kick and drift of the leapfrog (eqs. leapkick1, leapdrift of §2.3), FP64 with separately
+// rounded products and sums, fused with the box partials of the new positions.
+__global__ void __launch_bounds__(kBoxThreads) kick_drift_bbox_kernel(
+    double *__restrict__ pos, double *__restrict__ vel, const double *__restrict__ acc, int n,
+    double h, double dt, double *partials)
+{
+    double v[6] = {DBL_MAX, DBL_MAX, DBL_MAX, -DBL_MAX, -DBL_MAX, -DBL_MAX};
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const size_t k = (size_t)d * n + i;
+            double vh = __dadd_rn(vel[k], __dmul_rn(acc[k], h));
+            double x = __dadd_rn(pos[k], __dmul_rn(vh, dt));
+            vel[k] = vh;
+            pos[k] = x;
+            v[d] = fmin(v[d], x);
+            v[3 + d] = fmax(v[3 + d], x);
+        }
+    }
+    block_minmax6(v, partials + 6 * blockIdx.x);
+}
+
+__global__ void __launch_bounds__(kBoxThreads) bbox_finalize_kernel(const double *partials,
+                                                                    int nblk, Box *box,
+                                                                    LevelTables *tab, double theta)
+{
+    double v[6] = {DBL_MAX, DBL_MAX, DBL_MAX, -DBL_MAX, -DBL_MAX, -DBL_MAX};
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
+        for (int k = 0; k < 3; ++k) v[k] = fmin(v[k], partials[6 * b + k]);
+        for (int k = 3; k < 6; ++k) v[k] = fmax(v[k], partials[6 * b + k]);
+    }
+    __shared__ double r[6];
+    block_minmax6(v, r);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double ext = 0.0;
+        for (int d = 0; d < 3; ++d) {
+            double e = __dsub_rn(r[3 + d], r[d]);
+            if (e > ext) ext = e;
+        }
+        if (!(ext > 0.0)) ext = 1.0;
+        for (int d = 0; d < 3; ++d) {
+            box->o[d] = r[d];
+            box->c[d] = __dadd_rn(r[d], __dmul_rn(ext, 0.5));
+        }
+        box->L = ext;
+        box->s = __ddiv_rn(2097152.0, ext);
+        const double th2 = __dmul_rn(theta, theta);
+        for (int lev = 0; lev < kLevels; ++lev) {
+            double l = ldexp(ext, -lev);
+            double l2 = __dmul_rn(l, l);
+            tab->l2[lev] = l2;
+            tab->crit32[lev] = th2 > 0.0 ? (float)__ddiv_rn(l2, th2) : __int_as_float(0x7f800000);
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Morton keys (§4.4): q = clamp(floor((x - o) * s), 0, 2^21 - 1) per axis, then the bits of
+// q_x, q_y, q_z interleaved with x most significant (a 63-bit key in one 64-bit word).
+// ------------------------------------------------------------------------------------------
+
+__device__ __forceinline__ uint32_t quantise(double x, double o, double s)
+{
+    double t = __dmul_rn(__dsub_rn(x, o), s);
+    if (!(t > 0.0)) return 0u;
+    double f = floor(t);
+    if (f >= (double)kQMax) return kQMax;
+    return (uint32_t)f;
+}
+
+// Spreads the low 21 bits of v so that bit b lands on bit 3b.
+__device__ __forceinline__ uint64_t spread3(uint64_t v)
+{
+    v &= 0x1fffffull;
+    v = (v | (v << 32)) & 0x001f00000000ffffull;
+    v = (v | (v << 16)) & 0x001f0000ff0000ffull;
+    v = (v | (v << 8)) & 0x100f00f00f00f00full;
+    v = (v | (v << 4)) & 0x10c30c30c30c30c3ull;
+    v = (v | (v << 2)) & 0x1249249249249249ull;
+    return v;
+}
+
+__global__ void keys_kernel(const double *__restrict__ pos, int n, const Box *__restrict__ box,
+                            uint64_t *__restrict__ keys, uint32_t *__restrict__ ids)
+{
+    const double ox = box->o[0], oy = box->o[1], oz = box->o[2], s = box->s;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        uint32_t qx = quantise(pos[i], ox, s);
+        uint32_t qy = quantise(pos[(size_t)n + i], oy, s);
+        uint32_t qz = quantise(pos[2 * (size_t)n + i], oz, s);
+        keys[i] = (spread3(qx) << 2) | (spread3(qy) << 1) | spread3(qz);
+        ids[i] = (uint32_t)i;
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Stable LSD radix sort of (key, id) pairs, 8 passes of 8 bits (keys have 63 significant bits).
+// Per pass: tile digit counts (upsweep) -> per-digit scan over tiles (row scan, seeded by the
+// global digit histogram) -> stable scatter through a shared-memory reorder (downsweep).
+// No inter-block waiting anywhere: every kernel only reads what earlier launches wrote.
+// ------------------------------------------------------------------------------------------
+
+constexpr int kSortThreads = 256;
+constexpr int kSortWarps = kSortThreads / 32;
+constexpr int kSortItems = 16;                         // per thread
+constexpr int kSortTile = kSortThreads * kSortItems;   // 4096 keys per tile
+constexpr int kPasses = 8;
+constexpr size_t kDownSmem = (size_t)kSortTile * 8 + (size_t)kSortTile * 4 +
+                             (size_t)kSortWarps * 256 * 4 + 256 * 4 + 256 * 4;
+
+__device__ __forceinline__ unsigned lanemask_lt()
+{
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+__global__ void __launch_bounds__(kSortThreads) radix_hist_kernel(const uint64_t *__restrict__ keys,
+                                                                 int n, uint32_t *hist)
+{
+    __shared__ uint32_t sh[kPasses][256];
+    for (int k = threadIdx.x; k < kPasses * 256; k += blockDim.x) (&sh[0][0])[k] = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int stride = gridDim.x * blockDim.x;
+    for (int base = blockIdx.x * blockDim.x; base < n; base += stride) {
+        const int i = base + threadIdx.x;
+        const bool ok = i < n;
+        const uint64_t k = ok ? keys[i] : 0;
+#pragma unroll
+        for (int p = 0; p < kPasses; ++p) {
+            const unsigned d = ok ? (unsigned)((k >> (8 * p)) & 255u) : 256u;
+            const unsigned peers = __match_any_sync(kFull, d);
+            if (ok && (__ffs(peers) - 1) == lane) atomicAdd(&sh[p][d], __popc(peers));
+        }
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < kPasses * 256; k += blockDim.x) {
+        uint32_t v = (&sh[0][0])[k];
+        if (v) atomicAdd(&hist[k], v);
+    }
+}
+
+__global__ void __launch_bounds__(kSortThreads) radix_upsweep_kernel(const uint64_t *__restrict__ keys,
+                                                                    int n, int shift,
+                                                                    uint32_t *counts, int tiles)
+{
+    __shared__ uint32_t sh[256];
+    sh[threadIdx.x] = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int tile0 = blockIdx.x * kSortTile + wid * (kSortItems * 32);
+#pragma unroll 4
+    for (int r = 0; r < kSortItems; ++r) {
+        const int i = tile0 + r * 32 + lane;
+        const bool ok = i < n;
+        const unsigned d = ok ? (unsigned)((keys[i] >> shift) & 255u) : 256u;
+        const unsigned peers = __match_any_sync(kFull, d);
+        if (ok && (__ffs(peers) - 1) == lane) atomicAdd(&sh[d], __popc(peers));
+    }
+    __syncthreads();
+    counts[(size_t)threadIdx.x * tiles + blockIdx.x] = sh[threadIdx.x];
+}
+
+// Block-wide exclusive scan of one uint32 per thread; *total receives the block sum.
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *total)
+{
+    __shared__ uint32_t sh[33];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(kFull, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sh[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        uint32_t s = lane < nw ? sh[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(kFull, s, o);
+            if (lane >= o) s += y;
+        }
+        sh[lane] = s;
+    }
+    __syncthreads();
+    const uint32_t before = wid > 0 ? sh[wid - 1] : 0u;
+    *total = sh[nw - 1];
+    __syncthreads();
+    return before + x - v;
+}
+
+// One block per digit: offsets of that digit's run in every tile, seeded by the number of keys
+// with a smaller digit (from the global histogram of this pass).
+__global__ void __launch_bounds__(kSortThreads) radix_rowscan_kernel(uint32_t *counts, int tiles,
+                                                                    const uint32_t *hist_pass)
+{
+    const int d = blockIdx.x;
+    uint32_t part = 0;
+    for (int k = threadIdx.x; k < d; k += blockDim.x) part += hist_pass[k];
+    uint32_t base;
+    (void)block_exclusive_scan(part, &base);
+    uint32_t *row = counts + (size_t)d * tiles;
+    uint32_t carry = base;
+    for (int t0 = 0; t0 < tiles; t0 += blockDim.x) {
+        const int t = t0 + threadIdx.x;
+        const uint32_t v = t < tiles ? row[t] : 0u;
+        uint32_t tot;
+        const uint32_t ex = block_exclusive_scan(v, &tot);
+        if (t < tiles) row[t] = carry + ex;
+        carry += tot;
+    }
+}
+
+__global__ void __launch_bounds__(kSortThreads) radix_downsweep_kernel(
+    const uint64_t *__restrict__ keys_in, const uint32_t *__restrict__ ids_in,
+    uint64_t *__restrict__ keys_out, uint32_t *__restrict__ ids_out, int n, int shift,
+    const uint32_t *__restrict__ offsets, int tiles)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint64_t *s_keys = reinterpret_cast<uint64_t *>(smem);
+    uint32_t *s_ids = reinterpret_cast<uint32_t *>(s_keys + kSortTile);
+    uint32_t *s_warp = s_ids + kSortTile;                 // [warp][256]
+    uint32_t *s_start = s_warp + kSortWarps * 256;        // digit start inside the tile
+    int *s_gofs = reinterpret_cast<int *>(s_start + 256); // global offset minus s_start
+
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int tile_base = blockIdx.x * kSortTile;
+    const int tile_n = min(kSortTile, n - tile_base);
+    for (int k = threadIdx.x; k < kSortWarps * 256; k += blockDim.x) s_warp[k] = 0;
+    __syncthreads();
+
+    uint64_t k[kSortItems];
+    uint32_t id[kSortItems];
+    uint32_t rank[kSortItems];
+    const int w0 = tile_base + wid * (kSortItems * 32);
+    uint32_t *hist = s_warp + wid * 256;
+    const unsigned below = lanemask_lt();
+#pragma unroll
+    for (int r = 0; r < kSortItems; ++r) {
+        const int i = w0 + r * 32 + lane;
+        const bool ok = i < n;
+        k[r] = ok ? keys_in[i] : 0ull;
+        id[r] = ok ? ids_in[i] : 0u;
+        const unsigned d = ok ? (unsigned)((k[r] >> shift) & 255u) : 256u;
+        const unsigned peers = __match_any_sync(kFull, d);
+        const uint32_t before = ok ? hist[d] : 0u;
+        __syncwarp();
+        rank[r] = before + __popc(peers & below);
+        if (ok && (__ffs(peers) - 1) == lane) hist[d] = before + __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    // exclusive prefix over warps for every digit; digit totals of the tile
+    {
+        const int d = threadIdx.x;  // 256 threads <-> 256 digits
+        uint32_t sum = 0;
+        for (int w = 0; w < kSortWarps; ++w) {
+            const uint32_t t = s_warp[w * 256 + d];
+            s_warp[w * 256 + d] = sum;
+            sum += t;
+        }
+        uint32_t tot;
+        const uint32_t start = block_exclusive_scan(sum, &tot);
+        s_start[d] = start;
+        s_gofs[d] = (int)offsets[(size_t)d * tiles + blockIdx.x] - (int)start;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kSortItems; ++r) {
+        const int i = w0 + r * 32 + lane;
+        if (i < n) {
+            const unsigned d = (unsigned)((k[r] >> shift) & 255u);
+            const uint32_t p = s_start[d] + s_warp[wid * 256 + d] + rank[r];
+            s_keys[p] = k[r];
+            s_ids[p] = id[r];
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < tile_n; i += blockDim.x) {
+        const uint64_t kk = s_keys[i];
+        const unsigned d = (unsigned)((kk >> shift) & 255u);
+        const int o = s_gofs[d] + i;
+        keys_out[o] = kk;
+        ids_out[o] = s_ids[i];
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Permutation into Morton order: FP64 (x, y, z, m) and the FP32 copy relative to the box
+// centre with w = G m.
+// ------------------------------------------------------------------------------------------
+
+__global__ void permute_kernel(const double *__restrict__ pos, const double *__restrict__ mass,
+                               const uint32_t *__restrict__ ids, int n, const Box *__restrict__ box,
+                               double G, D4 *__restrict__ sbody64, float4 *__restrict__ sbody32)
+{
+    const double cx = box->c[0], cy = box->c[1], cz = box->c[2];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const uint32_t id = ids[i];
+        D4 b;
+        b.x = pos[id];
+        b.y = pos[(size_t)n + id];
+        b.z = pos[2 * (size_t)n + id];
+        b.w = mass[id];
+        sbody64[i] = b;
+        sbody32[i] = make_float4((float)(b.x - cx), (float)(b.y - cy), (float)(b.z - cz),
+                                 (float)(G * b.w));
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Node split.  With lcp(i) = number of leading 3-bit digits shared by sorted keys i and i+1
+// (21 when the keys are equal; -1 past either end), the uncompressed octree has
+//   - an internal cell at level l (0 <= l <= 20) for every maximal run of pairs with lcp >= l,
+//   - a level-21 bucket for every maximal run of pairs with lcp == 21,
+//   - a one-body leaf at level max(lcp(a-1), lcp(a)) + 1 for every body a outside a bucket.
+// In pre-order a node's subtree is a contiguous index range, nodes are ordered by
+// (first body, level), and body a starts the nodes at levels lcp(a-1)+1 .. onwards.  A count
+// per body, one exclusive scan and one emit pass therefore lay the tree out in pre-order.
+// ------------------------------------------------------------------------------------------
+
+__device__ __forceinline__ int lcp_digits(uint64_t a, uint64_t b)
+{
+    const uint64_t x = a ^ b;
+    if (x == 0) return kMaxLevel;
+    return (__clzll((long long)x) - 1) / 3;
+}
+
+__device__ __forceinline__ void body_lcps(const uint64_t *keys, int n, int a, int &lp, int &la)
+{
+    const uint64_t ka = keys[a];
+    lp = a > 0 ? lcp_digits(keys[a - 1], ka) : -1;
+    la = a + 1 < n ? lcp_digits(ka, keys[a + 1]) : -1;
+}
+
+__device__ __forceinline__ uint32_t nodes_started(int lp, int la)
+{
+    if (la == kMaxLevel) return lp == kMaxLevel ? 0u : (uint32_t)(kMaxLevel - lp);
+    if (lp == kMaxLevel) return 0u;
+    return (uint32_t)(max(0, la - lp) + 1);
+}
+
+__global__ void count_nodes_kernel(const uint64_t *__restrict__ keys, int n, uint32_t *counts)
+{
+    for (int a = blockIdx.x * blockDim.x + threadIdx.x; a <= n; a += gridDim.x * blockDim.x) {
+        if (a == n) { counts[n] = 0; continue; }
+        int lp, la;
+        body_lcps(keys, n, a, lp, la);
+        counts[a] = nodes_started(lp, la);
+    }
+}
+
+// First index c > lo (c <= n) whose key differs from keys[lo] above `shift`, given that
+// keys[lo] already shares the prefix.  Exponential then binary search.
+__device__ int run_end(const uint64_t *keys, int n, int lo, uint64_t prefix, int shift)
+{
+    int step = 1;
+    for (;;) {
+        const int probe = lo + step;
+        if (probe >= n || (keys[probe] >> shift) != prefix) break;
+        lo = probe;
+        step <<= 1;
+    }
+    int hi = min(lo + step, n);
+    while (hi - lo > 1) {
+        const int mid = lo + ((hi - lo) >> 1);
+        if ((keys[mid] >> shift) == prefix) lo = mid; else hi = mid;
+    }
+    return hi;
+}
+
+__global__ void emit_nodes_kernel(const uint64_t *__restrict__ keys, int n,
+                                  const uint32_t *__restrict__ node_off, NodeArrays na)
+{
+    for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < n; a += gridDim.x * blockDim.x) {
+        int lp, la;
+        body_lcps(keys, n, a, lp, la);
+        const uint32_t k = nodes_started(lp, la);
+        if (k == 0) continue;
+        const int base = (int)node_off[a];
+        const uint64_t ka = keys[a];
+        // levels of the cells (internal or bucket) that start at body a, deepest first so each
+        // search starts from the end of the nested deeper run.
+        const int top = lp + 1;
+        const int deepest_run = (la == kMaxLevel) ? kMaxLevel : la;  // may be < top: no runs
+        int end = a + 1;
+        for (int l = deepest_run; l >= top; --l) {
+            const int shift = 3 * (kMaxLevel - l);
+            const uint64_t prefix = shift >= 64 ? 0ull : (ka >> shift);
+            end = run_end(keys, n, max(a + 1, end - 1), prefix, shift);
+            const int idx = base + (l - top);
+            WalkNode w;
+            w.c = make_float4(0.f, 0.f, 0.f, 0.f);
+            w.first = a;
+            w.count = (l == kMaxLevel) ? (end - a) : 0;   // buckets are leaves
+            w.skip = (int)node_off[end];
+            w.crit = 0.f;
+            na.wn[idx] = w;
+            na.level[idx] = (uint8_t)l;
+        }
+        if (la != kMaxLevel) {
+            const int l = max(lp, la) + 1;  // one-body leaf
+            const int idx = base + (int)k - 1;
+            WalkNode w;
+            w.c = make_float4(0.f, 0.f, 0.f, 0.f);
+            w.first = a;
+            w.count = 1;
+            w.skip = idx + 1;
+            w.crit = 0.f;
+            na.wn[idx] = w;
+            na.level[idx] = (uint8_t)l;
+        }
+    }
+}
+
+// Parent links, child masks (octant digit of each child) and child counts of internal cells.
+__global__ void link_nodes_kernel(const uint64_t *__restrict__ keys, int n_nodes, NodeArrays na)
+{
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n_nodes; j += gridDim.x * blockDim.x) {
+        if (j == 0) na.parent[0] = -1;
+        na.arrive[j] = 0;
+        const WalkNode w = na.wn[j];
+        if (w.count != 0) { na.mask[j] = 0; na.nchild[j] = 0; continue; }
+        const int lev = na.level[j];
+        const int shift = 3 * (kMaxLevel - 1 - lev);
+        unsigned mask = 0, nc = 0;
+        // an internal cell has at most 8 children; the bound also ends the loop on a malformed
+        // skip chain
+        for (int c = j + 1; c < w.skip && nc < 8; c = max(na.wn[c].skip, c + 1)) {
+            na.parent[c] = j;
+            mask |= 1u << (unsigned)((keys[na.wn[c].first] >> shift) & 7u);
+            ++nc;
+        }
+        na.mask[j] = (uint8_t)mask;
+        na.nchild[j] = (uint8_t)nc;
+    }
+}
+
+__device__ __forceinline__ D4 ld_cg(const D4 *p)
+{
+    const double2 *q = reinterpret_cast<const double2 *>(p);
+    const double2 a = __ldcg(q), b = __ldcg(q + 1);
+    D4 r;
+    r.x = a.x; r.y = a.y; r.z = b.x; r.w = b.y;
+    return r;
+}
+
+__device__ __forceinline__ void store_node(NodeArrays &na, int j, const D4 &m, const Box *box,
+                                           double G, float crit)
+{
+    na.com64[j] = m;
+    WalkNode w = na.wn[j];
+    w.c = make_float4((float)(m.x - box->c[0]), (float)(m.y - box->c[1]),
+                      (float)(m.z - box->c[2]), (float)(G * m.w));
+    w.crit = crit;
+    na.wn[j] = w;
+}
+
+// Moments from the leaves to the root (Algorithm 2): a leaf takes its body (or the mass-
+// weighted mean of its bucket, bodies in Morton order); the last child to finish computes its
+// parent from all children in octant order: m = sum m_c, r = (sum m_c r_c) / m, every product
+// and sum separately rounded.  Counters only: nothing ever waits for another thread.
+__global__ void moments_kernel(int n_nodes, const D4 *__restrict__ sbody64,
+                               const Box *__restrict__ box, const LevelTables *__restrict__ tab,
+                               double G, NodeArrays na)
+{
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n_nodes; j += gridDim.x * blockDim.x) {
+        const WalkNode w = na.wn[j];
+        if (w.count == 0) continue;
+        D4 m;
+        if (w.count == 1) {
+            m = sbody64[w.first];
+        } else {
+            double s = 0.0, sx = 0.0, sy = 0.0, sz = 0.0;
+            for (int b = w.first; b < w.first + w.count; ++b) {
+                const D4 q = sbody64[b];
+                s = __dadd_rn(s, q.w);
+                sx = __dadd_rn(sx, __dmul_rn(q.w, q.x));
+                sy = __dadd_rn(sy, __dmul_rn(q.w, q.y));
+                sz = __dadd_rn(sz, __dmul_rn(q.w, q.z));
+            }
+            m.w = s;
+            m.x = __ddiv_rn(sx, s);
+            m.y = __ddiv_rn(sy, s);
+            m.z = __ddiv_rn(sz, s);
+        }
+        store_node(na, j, m, box, G, 0.f);
+        int cur = j;
+        for (;;) {
+            const int p = na.parent[cur];
+            if (p < 0) break;
+            __threadfence();
+            const int seen = atomicAdd(&na.arrive[p], 1);
+            if (seen != (int)na.nchild[p] - 1) break;
+            __threadfence();
+            const int pskip = __ldcg(&na.wn[p].skip);
+            double s = 0.0, sx = 0.0, sy = 0.0, sz = 0.0;
+            int nc = 0;
+            for (int c = p + 1; c < pskip && nc < 8; c = max(__ldcg(&na.wn[c].skip), c + 1), ++nc) {
+                const D4 q = ld_cg(&na.com64[c]);
+                s = __dadd_rn(s, q.w);
+                sx = __dadd_rn(sx, __dmul_rn(q.w, q.x));
+                sy = __dadd_rn(sy, __dmul_rn(q.w, q.y));
+                sz = __dadd_rn(sz, __dmul_rn(q.w, q.z));
+            }
+            D4 pm;
+            pm.w = s;
+            pm.x = __ddiv_rn(sx, s);
+            pm.y = __ddiv_rn(sy, s);
+            pm.z = __ddiv_rn(sz, s);
+            store_node(na, p, pm, box, G, tab->crit32[na.level[p]]);
+            cur = p;
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Generic exclusive scan of uint32 (reduce -> spine -> downsweep).
+// ------------------------------------------------------------------------------------------
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 16;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+__global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(const uint32_t *__restrict__ in,
+                                                                  int len, uint32_t *block_sums)
+{
+    const int base = blockIdx.x * kScanTile;
+    uint32_t s = 0;
+    for (int k = threadIdx.x; k < kScanTile; k += blockDim.x) {
+        const int i = base + k;
+        if (i < len) s += in[i];
+    }
+    uint32_t tot;
+    (void)block_exclusive_scan(s, &tot);
+    if (threadIdx.x == 0) block_sums[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(1024) scan_spine_kernel(uint32_t *block_sums, int nb)
+{
+    uint32_t carry = 0;
+    for (int t0 = 0; t0 < nb; t0 += blockDim.x) {
+        const int t = t0 + threadIdx.x;
+        const uint32_t v = t < nb ? block_sums[t] : 0u;
+        uint32_t tot;
+        const uint32_t ex = block_exclusive_scan(v, &tot);
+        if (t < nb) block_sums[t] = carry + ex;
+        carry += tot;
+    }
+    if (threadIdx.x == 0) block_sums[nb] = carry;
+}
+
+__global__ void __launch_bounds__(kScanThreads) scan_down_kernel(const uint32_t *__restrict__ in,
+                                                                uint32_t *__restrict__ out, int len,
+                                                                const uint32_t *__restrict__ block_sums)
+{
+    __shared__ uint32_t tile[kScanTile];
+    const int base = blockIdx.x * kScanTile;
+    for (int k = threadIdx.x; k < kScanTile; k += blockDim.x) {
+        const int i = base + k;
+        tile[k] = i < len ? in[i] : 0u;
+    }
+    __syncthreads();
+    uint32_t v[kScanItems];
+    uint32_t s = 0;
+#pragma unroll
+    for (int r = 0; r < kScanItems; ++r) {
+        v[r] = tile[threadIdx.x * kScanItems + r];
+        s += v[r];
+    }
+    uint32_t tot;
+    uint32_t run = block_exclusive_scan(s, &tot) + block_sums[blockIdx.x];
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kScanItems; ++r) {
+        tile[threadIdx.x * kScanItems + r] = run;
+        run += v[r];
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < kScanTile; k += blockDim.x) {
+        const int i = base + k;
+        if (i < len) out[i] = tile[k];
+    }
+}
+
+inline int grid_for(int64_t n, int threads, int max_blocks)
+{
+    int64_t b = (n + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > max_blocks) b = max_blocks;
+    return (int)b;
+}
+
+constexpr int kMaxGrid = 152 * 16;
+
+}  // namespace
+
+// ---------------------------------------------------------------- launchers
+
+namespace {
+std::atomic<int64_t> g_launches{0};
+}
+
+void count_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+int64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
+
+int bbox_blocks(int64_t n) { return grid_for(n, kBoxThreads * 4, 152 * 8); }
+
+void launch_bbox_partials(const double *pos, int n, double *partials, int nblk, cudaStream_t s)
+{
+    bbox_partials_kernel<<<nblk, kBoxThreads, 0, s>>>(pos, n, partials);
+    count_launches(1);
+}
+
+void launch_kick_drift_bbox(double *pos, double *vel, const double *acc, int n, double h,
+                            double dt, double *partials, int nblk, cudaStream_t s)
+{
+    kick_drift_bbox_kernel<<<nblk, kBoxThreads, 0, s>>>(pos, vel, acc, n, h, dt, partials);
+    count_launches(1);
+}
+
+void launch_bbox_finalize(const double *partials, int nblk, Box *box, LevelTables *tab,
+                          double theta, cudaStream_t s)
+{
+    bbox_finalize_kernel<<<1, kBoxThreads, 0, s>>>(partials, nblk, box, tab, theta);
+    count_launches(1);
+}
+
+void launch_keys(const double *pos, int n, const Box *box, uint64_t *keys, uint32_t *ids,
+                 cudaStream_t s)
+{
+    keys_kernel<<<grid_for(n, 256, kMaxGrid), 256, 0, s>>>(pos, n, box, keys, ids);
+    count_launches(1);
+}
+
+int sort_tiles(int n) { return (n + kSortTile - 1) / kSortTile; }
+
+cudaError_t sort_prepare()
+{
+    return cudaFuncSetAttribute(radix_downsweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)kDownSmem);
+}
+
+void launch_radix_sort(uint64_t *keys, uint32_t *ids, int n, const SortScratch &sc, cudaStream_t s)
+{
+    if (n <= 1) return;
+    const int tiles = sort_tiles(n);
+    cudaMemsetAsync(sc.hist, 0, sizeof(uint32_t) * kPasses * 256, s);
+    radix_hist_kernel<<<grid_for(n, kSortThreads * 8, 152 * 4), kSortThreads, 0, s>>>(keys, n, sc.hist);
+    uint64_t *kin = keys, *kout = sc.keys_alt;
+    uint32_t *iin = ids, *iout = sc.ids_alt;
+    for (int p = 0; p < kPasses; ++p) {
+        const int shift = 8 * p;
+        radix_upsweep_kernel<<<tiles, kSortThreads, 0, s>>>(kin, n, shift, sc.counts, tiles);
+        radix_rowscan_kernel<<<256, kSortThreads, 0, s>>>(sc.counts, tiles, sc.hist + 256 * p);
+        radix_downsweep_kernel<<<tiles, kSortThreads, kDownSmem, s>>>(kin, iin, kout, iout, n, shift,
+                                                                     sc.counts, tiles);
+        uint64_t *tk = kin; kin = kout; kout = tk;
+        uint32_t *ti = iin; iin = iout; iout = ti;
+    }
+    count_launches(1 + 3 * kPasses);
+    // an even number of passes leaves the result in the caller's buffers
+}
+
+void launch_permute(const double *pos, const double *mass, const uint32_t *ids, int n,
+                    const Box *box, double G, D4 *sbody64, float4 *sbody32, cudaStream_t s)
+{
+    permute_kernel<<<grid_for(n, 256, kMaxGrid), 256, 0, s>>>(pos, mass, ids, n, box, G, sbody64,
+                                                              sbody32);
+    count_launches(1);
+}
+
+int scan_tiles(int len) { return (len + kScanTile - 1) / kScanTile; }
+
+void launch_count_nodes(const uint64_t *keys, int n, uint32_t *counts, cudaStream_t s)
+{
+    count_nodes_kernel<<<grid_for((int64_t)n + 1, 256, kMaxGrid), 256, 0, s>>>(keys, n, counts);
+    count_launches(1);
+}
+
+void launch_exclusive_scan(const uint32_t *in, uint32_t *out, int len, const ScanScratch &sc,
+                           cudaStream_t s)
+{
+    const int nb = scan_tiles(len);
+    scan_reduce_kernel<<<nb, kScanThreads, 0, s>>>(in, len, sc.block_sums);
+    scan_spine_kernel<<<1, 1024, 0, s>>>(sc.block_sums, nb);
+    scan_down_kernel<<<nb, kScanThreads, 0, s>>>(in, out, len, sc.block_sums);
+    count_launches(3);
+}
+
+void launch_emit_nodes(const uint64_t *keys, int n, const uint32_t *node_off, NodeArrays na,
+                       cudaStream_t s)
+{
+    emit_nodes_kernel<<<grid_for(n, 128, kMaxGrid * 4), 128, 0, s>>>(keys, n, node_off, na);
+    count_launches(1);
+}
+
+void launch_link_nodes(const uint64_t *keys, int n_nodes, NodeArrays na, cudaStream_t s)
+{
+    link_nodes_kernel<<<grid_for(n_nodes, 256, kMaxGrid * 4), 256, 0, s>>>(keys, n_nodes, na);
+    count_launches(1);
+}
+
+void launch_moments(int n_nodes, const D4 *sbody64, const Box *box, const LevelTables *tab,
+                    double G, NodeArrays na, cudaStream_t s)
+{
+    moments_kernel<<<grid_for(n_nodes, 256, kMaxGrid * 4), 256, 0, s>>>(n_nodes, sbody64, box, tab,
+                                                                       G, na);
+    count_launches(1);
+}
+
+}  // namespace nb

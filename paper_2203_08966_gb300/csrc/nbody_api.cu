@@ -1,0 +1,586 @@
+// C ABI of the Barnes-Hut timestep library: context, build / force / step entry points and
+// introspection.  Every step of the method runs in the kernels of build_kernels.cu and
+// walk_kernels.cu; this file only allocates, orders launches on the context stream and copies.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "nbody_internal.cuh"
+
+using namespace nb;
+
+struct nbody_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    nbody_params p{};
+    int64_t cap = 0;
+
+    // per-body working set (capacity `cap`)
+    uint64_t *keys = nullptr, *keys_alt = nullptr;
+    uint32_t *ids = nullptr, *ids_alt = nullptr;
+    D4 *sbody64 = nullptr;
+    float4 *sbody32 = nullptr;
+    uint32_t *node_off = nullptr;   // cap + 1
+    uint32_t *hist = nullptr;       // 8 x 256
+    uint32_t *counts = nullptr;     // 256 x sort tiles
+    uint32_t *block_sums = nullptr; // scan tiles + 1
+    double *partials = nullptr;     // 6 x bbox blocks
+    int nblk = 0;
+    Box *box = nullptr;             // [0] last build, [1] direct sum
+    LevelTables *tab = nullptr;     // [0] last build, [1] direct sum
+    double *acc = nullptr;          // 3 x cap: a^(k) kept between steps
+    uint32_t *pp = nullptr, *pc = nullptr;
+    int *err = nullptr;             // device error word
+    uint32_t *h_word = nullptr;     // pinned host word for the node count
+
+    // octree
+    NodeArrays na{};
+    int64_t n_nodes = 0;
+
+    // host-buffer stepping
+    double *hpos = nullptr, *hvel = nullptr, *hmass = nullptr;
+
+    // state
+    int64_t n_built = -1;       // n of the last build (-1: none)
+    int64_t n_forces = -1;      // n of the last force evaluation (counters valid)
+    int64_t acc_n = -1;         // n for which ctx->acc holds a^(k)
+    bool timing = false;
+    bool timing_pending = false;  // events of the last call not yet read
+    cudaEvent_t ev[6] = {};
+    float ms[5] = {0, 0, 0, 0, 0};
+    char msg[256] = {0};
+};
+
+namespace {
+
+nbody_status fail(nbody_ctx *c, nbody_status st, const char *fmt, ...)
+{
+    if (c) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(c->msg, sizeof(c->msg), fmt, ap);
+        va_end(ap);
+    }
+    return st;
+}
+
+#define CK(call)                                                                              \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return fail(c, e_ == cudaErrorMemoryAllocation ? NBODY_ENOMEM : NBODY_ECUDA,      \
+                        "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)
+
+#define CKS(expr)                        \
+    do {                                 \
+        nbody_status s_ = (expr);        \
+        if (s_ != NBODY_OK) return s_;   \
+    } while (0)
+
+bool params_ok(const nbody_params *p)
+{
+    if (!p) return false;
+    if (!isfinite(p->G) || !isfinite(p->dt)) return false;
+    if (!(p->eps >= 0.0) || !isfinite(p->eps)) return false;
+    if (!(p->theta >= 0.0) || !isfinite(p->theta)) return false;
+    if (p->precision < NBODY_FP64 || p->precision > NBODY_FP32_KAHAN) return false;
+    if (p->flags != 0) return false;
+    return true;
+}
+
+template <class T>
+cudaError_t dalloc(T **p, size_t count)
+{
+    *p = nullptr;
+    if (count == 0) count = 1;
+    return cudaMalloc((void **)p, sizeof(T) * count);
+}
+
+template <class T>
+void dfree(T *&p)
+{
+    if (p) cudaFree((void *)p);
+    p = nullptr;
+}
+
+void free_nodes(nbody_ctx *c)
+{
+    dfree(c->na.wn);
+    dfree(c->na.com64);
+    dfree(c->na.level);
+    dfree(c->na.mask);
+    dfree(c->na.nchild);
+    dfree(c->na.parent);
+    dfree(c->na.arrive);
+    c->na.cap = 0;
+}
+
+nbody_status ensure_nodes(nbody_ctx *c, int64_t need)
+{
+    if (need <= c->na.cap) return NBODY_OK;
+    free_nodes(c);
+    const int64_t cap = std::max<int64_t>(need + need / 8, 1024);
+    CK(dalloc(&c->na.wn, cap));
+    CK(dalloc(&c->na.com64, cap));
+    CK(dalloc(&c->na.level, cap));
+    CK(dalloc(&c->na.mask, cap));
+    CK(dalloc(&c->na.nchild, cap));
+    CK(dalloc(&c->na.parent, cap));
+    CK(dalloc(&c->na.arrive, cap));
+    c->na.cap = cap;
+    return NBODY_OK;
+}
+
+nbody_status check_launch(nbody_ctx *c, const char *what)
+{
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(c, NBODY_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+    return NBODY_OK;
+}
+
+nbody_status check_n(nbody_ctx *c, int64_t n)
+{
+    if (n < 0 || n > c->cap)
+        return fail(c, NBODY_EINVAL, "n = %lld outside [0, capacity %lld]", (long long)n,
+                    (long long)c->cap);
+    return NBODY_OK;
+}
+
+void record(nbody_ctx *c, int k)
+{
+    if (c->timing) cudaEventRecord(c->ev[k], c->stream);
+}
+
+// Root box, keys, sort, permutation, node split and moments of (pos, mass).  When
+// `have_partials` the bbox partial reductions of pos are already in c->partials.
+nbody_status build(nbody_ctx *c, const double *pos, const double *mass, int n,
+                   bool have_partials)
+{
+    cudaStream_t s = c->stream;
+    if (n == 0) {
+        c->n_nodes = 0;
+        c->n_built = 0;
+        return NBODY_OK;
+    }
+    if (!have_partials) launch_bbox_partials(pos, n, c->partials, c->nblk, s);
+    launch_bbox_finalize(c->partials, c->nblk, c->box, c->tab, c->p.theta, s);
+    launch_keys(pos, n, c->box, c->keys, c->ids, s);
+    record(c, 1);
+    SortScratch sc{c->keys_alt, c->ids_alt, c->hist, c->counts, sort_tiles((int)c->cap)};
+    launch_radix_sort(c->keys, c->ids, n, sc, s);
+    record(c, 2);
+    launch_permute(pos, mass, c->ids, n, c->box, c->p.G, c->sbody64, c->sbody32, s);
+    launch_count_nodes(c->keys, n, c->node_off, s);
+    ScanScratch ss{c->block_sums, scan_tiles((int)c->cap + 1)};
+    launch_exclusive_scan(c->node_off, c->node_off, n + 1, ss, s);
+    CKS(check_launch(c, "tree build"));
+    CK(cudaMemcpyAsync(c->h_word, c->node_off + n, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const int64_t nn = (int64_t)*c->h_word;
+    if (nn < 1 || nn > 22 * (int64_t)n)
+        return fail(c, NBODY_ECUDA, "node count %lld out of range for n = %d", (long long)nn, n);
+    CKS(ensure_nodes(c, nn));
+    c->n_nodes = nn;
+    launch_emit_nodes(c->keys, n, c->node_off, c->na, s);
+    launch_link_nodes(c->keys, (int)nn, c->na, s);
+    launch_moments((int)nn, c->sbody64, c->box, c->tab, c->p.G, c->na, s);
+    record(c, 3);
+    CKS(check_launch(c, "node split / moments"));
+    c->n_built = n;
+    return NBODY_OK;
+}
+
+nbody_status walk(nbody_ctx *c, int n, double *acc, double *vel, double h)
+{
+    if (n == 0) return NBODY_OK;
+    WalkArgs a;
+    a.wn = c->na.wn;
+    a.com64 = c->na.com64;
+    a.level = c->na.level;
+    a.tab = c->tab;
+    a.n_nodes = (int)c->n_nodes;
+    a.sbody64 = c->sbody64;
+    a.sbody32 = c->sbody32;
+    a.ids = c->ids;
+    a.n = n;
+    a.G = c->p.G;
+    a.eps = c->p.eps;
+    a.theta = c->p.theta;
+    a.acc = acc;
+    a.vel = vel;
+    a.h = h;
+    a.pp = c->pp;
+    a.pc = c->pc;
+    launch_walk(c->p.precision, a, c->stream);
+    record(c, 4);
+    CKS(check_launch(c, "walk"));
+    c->n_forces = n;
+    return NBODY_OK;
+}
+
+nbody_status begin_timing(nbody_ctx *c)
+{
+    if (!c->timing) return NBODY_OK;
+    c->timing_pending = false;
+    for (int k = 0; k < 5; ++k) c->ms[k] = 0.f;
+    CK(cudaEventRecord(c->ev[0], c->stream));
+    for (int k = 1; k < 5; ++k) CK(cudaEventRecord(c->ev[k], c->stream));
+    return NBODY_OK;
+}
+
+nbody_status end_timing(nbody_ctx *c)
+{
+    if (!c->timing) return NBODY_OK;
+    CK(cudaEventRecord(c->ev[5], c->stream));
+    c->timing_pending = true;
+    return NBODY_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+nbody_status nbody_create(nbody_ctx **out, int64_t n_capacity, const nbody_params *p,
+                          void *cuda_stream)
+{
+    nbody_ctx *c = nullptr;
+    if (!out) return NBODY_EINVAL;
+    *out = nullptr;
+    if (n_capacity < 0 || n_capacity > ((int64_t)1 << 30) || !params_ok(p)) return NBODY_EINVAL;
+    c = new (std::nothrow) nbody_ctx;
+    if (!c) return NBODY_ENOMEM;
+    c->p = *p;
+    c->cap = n_capacity;
+    c->stream = (cudaStream_t)cuda_stream;
+    nbody_status st = NBODY_OK;
+    auto body = [&]() -> nbody_status {
+        CK(cudaGetDevice(&c->device));
+        CK(sort_prepare());
+        const size_t cap = (size_t)std::max<int64_t>(n_capacity, 1);
+        CK(dalloc(&c->keys, cap));
+        CK(dalloc(&c->keys_alt, cap));
+        CK(dalloc(&c->ids, cap));
+        CK(dalloc(&c->ids_alt, cap));
+        CK(dalloc(&c->sbody64, cap));
+        CK(dalloc(&c->sbody32, cap));
+        CK(dalloc(&c->node_off, cap + 1));
+        CK(dalloc(&c->hist, 8 * 256));
+        CK(dalloc(&c->counts, (size_t)256 * sort_tiles((int)cap)));
+        CK(dalloc(&c->block_sums, (size_t)scan_tiles((int)cap + 1) + 1));
+        c->nblk = bbox_blocks((int64_t)cap);
+        CK(dalloc(&c->partials, (size_t)6 * c->nblk));
+        CK(dalloc(&c->box, 2));
+        CK(dalloc(&c->tab, 2));
+        CK(dalloc(&c->acc, 3 * cap));
+        CK(dalloc(&c->pp, cap));
+        CK(dalloc(&c->pc, cap));
+        CK(dalloc(&c->err, 1));
+        CK(cudaMemset(c->err, 0, sizeof(int)));
+        CK(cudaMallocHost((void **)&c->h_word, sizeof(uint32_t)));
+        for (int k = 0; k < 6; ++k) CK(cudaEventCreate(&c->ev[k]));
+        return NBODY_OK;
+    };
+    st = body();
+    if (st != NBODY_OK) {
+        nbody_destroy(c);
+        return st;
+    }
+    *out = c;
+    return NBODY_OK;
+}
+
+nbody_status nbody_destroy(nbody_ctx *c)
+{
+    if (!c) return NBODY_EINVAL;
+    cudaStreamSynchronize(c->stream);
+    dfree(c->keys);
+    dfree(c->keys_alt);
+    dfree(c->ids);
+    dfree(c->ids_alt);
+    dfree(c->sbody64);
+    dfree(c->sbody32);
+    dfree(c->node_off);
+    dfree(c->hist);
+    dfree(c->counts);
+    dfree(c->block_sums);
+    dfree(c->partials);
+    dfree(c->box);
+    dfree(c->tab);
+    dfree(c->acc);
+    dfree(c->pp);
+    dfree(c->pc);
+    dfree(c->err);
+    dfree(c->hpos);
+    dfree(c->hvel);
+    dfree(c->hmass);
+    free_nodes(c);
+    if (c->h_word) cudaFreeHost(c->h_word);
+    for (int k = 0; k < 6; ++k)
+        if (c->ev[k]) cudaEventDestroy(c->ev[k]);
+    delete c;
+    return NBODY_OK;
+}
+
+nbody_status nbody_set_params(nbody_ctx *c, const nbody_params *p)
+{
+    if (!c) return NBODY_EINVAL;
+    if (!params_ok(p)) return fail(c, NBODY_EINVAL, "invalid parameters");
+    c->p = *p;
+    c->acc_n = -1;
+    return NBODY_OK;
+}
+
+nbody_status nbody_build_tree(nbody_ctx *c, const double *d_pos, const double *d_mass, int64_t n)
+{
+    if (!c) return NBODY_EINVAL;
+    CKS(check_n(c, n));
+    if (n > 0 && (!d_pos || !d_mass)) return fail(c, NBODY_EINVAL, "null pointer");
+    CKS(begin_timing(c));
+    CKS(build(c, d_pos, d_mass, (int)n, false));
+    return end_timing(c);
+}
+
+nbody_status nbody_forces(nbody_ctx *c, const double *d_pos, const double *d_mass, int64_t n,
+                          double *d_acc)
+{
+    if (!c) return NBODY_EINVAL;
+    CKS(check_n(c, n));
+    if (n > 0 && (!d_pos || !d_mass || !d_acc)) return fail(c, NBODY_EINVAL, "null pointer");
+    CKS(begin_timing(c));
+    CKS(build(c, d_pos, d_mass, (int)n, false));
+    CKS(walk(c, (int)n, d_acc, nullptr, 0.0));
+    return end_timing(c);
+}
+
+nbody_status nbody_step(nbody_ctx *c, double *d_pos, double *d_vel, const double *d_mass,
+                        int64_t n, int32_t nsteps)
+{
+    if (!c) return NBODY_EINVAL;
+    CKS(check_n(c, n));
+    if (nsteps < 0) return fail(c, NBODY_EINVAL, "nsteps < 0");
+    if (n > 0 && (!d_pos || !d_vel || !d_mass)) return fail(c, NBODY_EINVAL, "null pointer");
+    if (n == 0 || nsteps == 0) return NBODY_OK;
+    const double h = 0.5 * c->p.dt;
+    if (c->acc_n != n) {
+        CKS(build(c, d_pos, d_mass, (int)n, false));
+        CKS(walk(c, (int)n, c->acc, nullptr, 0.0));
+        c->acc_n = n;
+    }
+    for (int32_t k = 0; k < nsteps; ++k) {
+        CKS(begin_timing(c));
+        launch_kick_drift_bbox(d_pos, d_vel, c->acc, (int)n, h, c->p.dt, c->partials, c->nblk,
+                               c->stream);
+        CKS(check_launch(c, "kick/drift"));
+        CKS(build(c, d_pos, d_mass, (int)n, true));
+        CKS(walk(c, (int)n, c->acc, d_vel, h));
+        CKS(end_timing(c));
+    }
+    return NBODY_OK;
+}
+
+nbody_status nbody_step_host(nbody_ctx *c, double *h_pos, double *h_vel, double *h_acc,
+                             const double *h_mass, int64_t n, int32_t nsteps)
+{
+    if (!c) return NBODY_EINVAL;
+    CKS(check_n(c, n));
+    if (nsteps < 0) return fail(c, NBODY_EINVAL, "nsteps < 0");
+    if (n > 0 && (!h_pos || !h_vel || !h_mass)) return fail(c, NBODY_EINVAL, "null pointer");
+    if (n == 0) return NBODY_OK;
+    if (!c->hpos) {
+        const size_t cap = (size_t)c->cap;
+        CK(dalloc(&c->hpos, 3 * cap));
+        CK(dalloc(&c->hvel, 3 * cap));
+        CK(dalloc(&c->hmass, cap));
+    }
+    const size_t b3 = sizeof(double) * 3 * (size_t)n;
+    CK(cudaMemcpyAsync(c->hpos, h_pos, b3, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->hvel, h_vel, b3, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->hmass, h_mass, sizeof(double) * (size_t)n, cudaMemcpyHostToDevice,
+                       c->stream));
+    if (h_acc) {
+        // the caller's a^(k) at h_pos: no force evaluation before the first kick
+        CK(cudaMemcpyAsync(c->acc, h_acc, b3, cudaMemcpyHostToDevice, c->stream));
+        c->acc_n = n;
+    } else {
+        c->acc_n = -1;
+    }
+    CKS(nbody_step(c, c->hpos, c->hvel, c->hmass, n, nsteps));
+    if (c->acc_n != n) {  // nsteps == 0 without h_acc: nothing was computed
+        CKS(build(c, c->hpos, c->hmass, (int)n, false));
+        CKS(walk(c, (int)n, c->acc, nullptr, 0.0));
+        c->acc_n = n;
+    }
+    CK(cudaMemcpyAsync(h_pos, c->hpos, b3, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(h_vel, c->hvel, b3, cudaMemcpyDeviceToHost, c->stream));
+    if (h_acc) CK(cudaMemcpyAsync(h_acc, c->acc, b3, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->acc_n = -1;  // the device copy belongs to this call only
+    return NBODY_OK;
+}
+
+nbody_status nbody_direct_forces(nbody_ctx *c, const double *d_pos, const double *d_mass,
+                                 int64_t n, const int64_t *d_targets, int64_t nt, double *d_acc)
+{
+    if (!c) return NBODY_EINVAL;
+    CKS(check_n(c, n));
+    if (!d_targets) nt = n;
+    if (nt < 0 || nt > ((int64_t)1 << 30)) return fail(c, NBODY_EINVAL, "bad target count");
+    if (n > 0 && (!d_pos || !d_mass || !d_acc)) return fail(c, NBODY_EINVAL, "null pointer");
+    if (n == 0 || nt == 0) return NBODY_OK;
+    launch_bbox_partials(d_pos, (int)n, c->partials, c->nblk, c->stream);
+    launch_bbox_finalize(c->partials, c->nblk, c->box + 1, c->tab + 1, c->p.theta, c->stream);
+    launch_direct(c->p.precision, d_pos, d_mass, (int)n, d_targets, (int)nt, c->p.G, c->p.eps,
+                  c->box + 1, d_acc, c->stream);
+    return check_launch(c, "direct sum");
+}
+
+nbody_status nbody_sync(nbody_ctx *c)
+{
+    if (!c) return NBODY_EINVAL;
+    CK(cudaStreamSynchronize(c->stream));
+    int e = 0;
+    CK(cudaMemcpy(&e, c->err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (e & kErrTimeout) return fail(c, NBODY_ETIMEOUT, "a device-side wait gave up");
+    if (e & kErrNodeCap) return fail(c, NBODY_ENOMEM, "node capacity exceeded on the device");
+    return NBODY_OK;
+}
+
+nbody_status nbody_get_keys(nbody_ctx *c, uint64_t *h_keys_sorted, uint32_t *h_ids_sorted)
+{
+    if (!c) return NBODY_EINVAL;
+    if (c->n_built < 0) return fail(c, NBODY_ESTATE, "no tree built yet");
+    const size_t n = (size_t)c->n_built;
+    CK(cudaStreamSynchronize(c->stream));
+    if (h_keys_sorted) CK(cudaMemcpy(h_keys_sorted, c->keys, 8 * n, cudaMemcpyDeviceToHost));
+    if (h_ids_sorted) CK(cudaMemcpy(h_ids_sorted, c->ids, 4 * n, cudaMemcpyDeviceToHost));
+    return NBODY_OK;
+}
+
+nbody_status nbody_get_box(nbody_ctx *c, double *h_box)
+{
+    if (!c || !h_box) return NBODY_EINVAL;
+    if (c->n_built < 0) return fail(c, NBODY_ESTATE, "no tree built yet");
+    Box b;
+    CK(cudaStreamSynchronize(c->stream));
+    CK(cudaMemcpy(&b, c->box, sizeof(Box), cudaMemcpyDeviceToHost));
+    h_box[0] = b.o[0];
+    h_box[1] = b.o[1];
+    h_box[2] = b.o[2];
+    h_box[3] = b.L;
+    h_box[4] = b.s;
+    return NBODY_OK;
+}
+
+nbody_status nbody_get_tree(nbody_ctx *c, int64_t *n_nodes, nbody_tree_record *h_records,
+                            int64_t cap)
+{
+    if (!c || !n_nodes) return NBODY_EINVAL;
+    if (c->n_built < 0) return fail(c, NBODY_ESTATE, "no tree built yet");
+    const int64_t nn = c->n_nodes, n = c->n_built;
+    *n_nodes = nn;
+    if (!h_records || cap < nn || nn == 0) return NBODY_OK;
+    std::vector<WalkNode> wn((size_t)nn);
+    std::vector<uint8_t> lev((size_t)nn), mask((size_t)nn);
+    std::vector<uint64_t> keys((size_t)n);
+    CK(cudaStreamSynchronize(c->stream));
+    CK(cudaMemcpy(wn.data(), c->na.wn, sizeof(WalkNode) * nn, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(lev.data(), c->na.level, nn, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(mask.data(), c->na.mask, nn, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(keys.data(), c->keys, 8 * n, cudaMemcpyDeviceToHost));
+    for (int64_t j = 0; j < nn; ++j) {
+        const int l = lev[j];
+        const int64_t first = wn[j].first;
+        const uint64_t prefix = l == 0 ? 0ull : (keys[first] >> (3 * (kMaxLevel - l)));
+        nbody_tree_record &r = h_records[j];
+        r.key = (1ull << (3 * l)) | prefix;
+        r.level = l;
+        r.child_mask = mask[j];
+        r.first = first;
+        if (wn[j].count != 0) {
+            r.count = wn[j].count;
+        } else {
+            const int64_t sk = wn[j].skip;
+            r.count = (sk < nn ? (int64_t)wn[sk].first : n) - first;
+        }
+    }
+    return NBODY_OK;
+}
+
+nbody_status nbody_get_moments(nbody_ctx *c, double *h_out, int64_t cap_nodes)
+{
+    if (!c || !h_out) return NBODY_EINVAL;
+    if (c->n_built < 0) return fail(c, NBODY_ESTATE, "no tree built yet");
+    const int64_t nn = c->n_nodes;
+    if (cap_nodes < nn) return fail(c, NBODY_EINVAL, "cap_nodes < node count %lld", (long long)nn);
+    if (nn == 0) return NBODY_OK;
+    std::vector<D4> m((size_t)nn);
+    CK(cudaStreamSynchronize(c->stream));
+    CK(cudaMemcpy(m.data(), c->na.com64, sizeof(D4) * nn, cudaMemcpyDeviceToHost));
+    for (int64_t j = 0; j < nn; ++j) {
+        h_out[4 * j] = m[j].w;
+        h_out[4 * j + 1] = m[j].x;
+        h_out[4 * j + 2] = m[j].y;
+        h_out[4 * j + 3] = m[j].z;
+    }
+    return NBODY_OK;
+}
+
+nbody_status nbody_get_counters(nbody_ctx *c, uint32_t *h_pp, uint32_t *h_pc)
+{
+    if (!c || !h_pp || !h_pc) return NBODY_EINVAL;
+    if (c->n_forces < 0 || c->n_forces != c->n_built)
+        return fail(c, NBODY_ESTATE, "no force evaluation on the current tree");
+    const size_t n = (size_t)c->n_forces;
+    std::vector<uint32_t> ids(n), pp(n), pc(n);
+    CK(cudaStreamSynchronize(c->stream));
+    CK(cudaMemcpy(ids.data(), c->ids, 4 * n, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(pp.data(), c->pp, 4 * n, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(pc.data(), c->pc, 4 * n, cudaMemcpyDeviceToHost));
+    for (size_t i = 0; i < n; ++i) {
+        h_pp[ids[i]] = pp[i];
+        h_pc[ids[i]] = pc[i];
+    }
+    return NBODY_OK;
+}
+
+nbody_status nbody_enable_timing(nbody_ctx *c, int32_t on)
+{
+    if (!c) return NBODY_EINVAL;
+    c->timing = on != 0;
+    return NBODY_OK;
+}
+
+nbody_status nbody_get_timings(nbody_ctx *c, float *h_ms5)
+{
+    if (!c || !h_ms5) return NBODY_EINVAL;
+    if (c->timing_pending) {
+        CK(cudaEventSynchronize(c->ev[5]));
+        for (int k = 0; k < 4; ++k) CK(cudaEventElapsedTime(&c->ms[k], c->ev[k], c->ev[k + 1]));
+        CK(cudaEventElapsedTime(&c->ms[4], c->ev[0], c->ev[5]));
+        c->timing_pending = false;
+    }
+    for (int k = 0; k < 5; ++k) h_ms5[k] = c->ms[k];
+    return NBODY_OK;
+}
+
+nbody_status nbody_get_launch_count(int64_t *out)
+{
+    if (!out) return NBODY_EINVAL;
+    *out = launch_count();
+    return NBODY_OK;
+}
+
+nbody_status nbody_last_error(nbody_ctx *c, char *buf, int64_t cap)
+{
+    if (!c || !buf || cap <= 0) return NBODY_EINVAL;
+    snprintf(buf, (size_t)cap, "%s", c->msg);
+    return NBODY_OK;
+}
+
+}  // extern "C"

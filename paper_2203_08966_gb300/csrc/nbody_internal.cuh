@@ -1,0 +1,129 @@
+// Internal declarations shared by the library's translation units (not installed).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "nbody.h"
+
+namespace nb {
+
+constexpr int kBits = 21;          // bits per axis of a Morton key (§4.4)
+constexpr int kMaxLevel = 21;      // deepest octree level; cells there are buckets
+constexpr int kLevels = 22;        // levels 0..21
+constexpr uint32_t kQMax = 2097151u;
+
+// Sorted body or tree node in FP64: (x, y, z, m).
+struct alignas(32) D4 {
+    double x, y, z, w;
+};
+
+// What the FP32 walk reads per node (32 bytes, two 16-byte loads).
+//   c      centre of mass minus the box centre (FP32), c.w = G * m
+//   skip   pre-order index of the first node after this node's subtree
+//   first  sorted index of the node's first body
+//   count  0 for an internal cell; number of bodies for a leaf (1, or > 1 for a level-21 bucket)
+//   crit   internal cells: l^2 / theta^2 of the node's level, +inf when theta == 0
+struct alignas(16) WalkNode {
+    float4 c;
+    int skip;
+    int first;
+    int count;
+    float crit;
+};
+
+// Root box on the device.
+struct Box {
+    double o[3];      // min corner
+    double L;         // cube side
+    double s;         // 2^21 / L
+    double c[3];      // centre o + L/2 (origin of the FP32 coordinates)
+};
+
+// Device error word bits.
+enum : int { kErrNodeCap = 1, kErrTimeout = 2 };
+
+// Per-level tables written with the box.
+struct LevelTables {
+    double l2[kLevels];      // (L / 2^level)^2
+    float crit32[kLevels];   // l2 / theta^2 as FP32 (+inf when theta == 0)
+};
+
+// Process-wide count of kernel launches made by the library (every launcher adds its launches).
+void count_launches(int k);
+int64_t launch_count();
+
+// ---------------------------------------------------------------- build_kernels.cu
+int bbox_blocks(int64_t n);
+void launch_bbox_partials(const double *pos, int n, double *partials, int nblk, cudaStream_t s);
+void launch_kick_drift_bbox(double *pos, double *vel, const double *acc, int n, double h,
+                            double dt, double *partials, int nblk, cudaStream_t s);
+void launch_bbox_finalize(const double *partials, int nblk, Box *box, LevelTables *tab,
+                          double theta, cudaStream_t s);
+void launch_keys(const double *pos, int n, const Box *box, uint64_t *keys, uint32_t *ids,
+                 cudaStream_t s);
+
+struct SortScratch {
+    uint64_t *keys_alt;
+    uint32_t *ids_alt;
+    uint32_t *hist;       // 8 x 256 digit totals
+    uint32_t *counts;     // 256 x tiles
+    int max_tiles;
+};
+int sort_tiles(int n);
+cudaError_t sort_prepare(); // one-time function attributes
+void launch_radix_sort(uint64_t *keys, uint32_t *ids, int n, const SortScratch &sc,
+                       cudaStream_t s);
+
+void launch_permute(const double *pos, const double *mass, const uint32_t *ids, int n,
+                    const Box *box, double G, D4 *sbody64, float4 *sbody32, cudaStream_t s);
+
+struct ScanScratch {
+    uint32_t *block_sums;  // tiles + 1
+    int max_tiles;
+};
+int scan_tiles(int len);
+void launch_count_nodes(const uint64_t *keys, int n, uint32_t *counts, cudaStream_t s);
+void launch_exclusive_scan(const uint32_t *in, uint32_t *out, int len, const ScanScratch &sc,
+                           cudaStream_t s);
+
+struct NodeArrays {
+    WalkNode *wn;
+    D4 *com64;
+    uint8_t *level;
+    uint8_t *mask;
+    uint8_t *nchild;
+    int *parent;
+    int *arrive;
+    int64_t cap;
+};
+void launch_emit_nodes(const uint64_t *keys, int n, const uint32_t *node_off, NodeArrays na,
+                       cudaStream_t s);
+void launch_link_nodes(const uint64_t *keys, int n_nodes, NodeArrays na, cudaStream_t s);
+void launch_moments(int n_nodes, const D4 *sbody64, const Box *box, const LevelTables *tab,
+                    double G, NodeArrays na, cudaStream_t s);
+
+// ---------------------------------------------------------------- walk_kernels.cu
+struct WalkArgs {
+    const WalkNode *wn;
+    const D4 *com64;
+    const uint8_t *level;
+    const LevelTables *tab;
+    int n_nodes;
+    const D4 *sbody64;
+    const float4 *sbody32;
+    const uint32_t *ids;
+    int n;
+    double G, eps, theta;
+    double *acc;          // 3n, user order (written)
+    double *vel;          // 3n, user order, kicked by acc*h when non-null
+    double h;
+    uint32_t *pp, *pc;    // n, sorted order
+};
+void launch_walk(int precision, const WalkArgs &a, cudaStream_t s);
+
+void launch_direct(int precision, const double *pos, const double *mass, int n,
+                   const int64_t *targets, int nt, double G, double eps, const Box *box,
+                   double *acc, cudaStream_t s);
+
+}  // namespace nb

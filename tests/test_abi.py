@@ -1,0 +1,61 @@
+"""The C ABI library builds, loads and exports every entry point include/nbody.h declares, and the
+binding names the same set.  No compute call is made (these run without a GPU)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+import paper_2203_08966_gb300 as nb
+from paper_2203_08966_gb300 import build_lib
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", h)).read()
+            names |= set(re.findall(r"\bnbody_status\s+(nbody_\w+)\s*\(", txt))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib_path():
+    return build_lib.build()
+
+
+def test_header_declares_the_boundary():
+    d = _declared()
+    for name in ("nbody_create", "nbody_build_tree", "nbody_forces", "nbody_step"):
+        assert name in d
+
+
+def test_library_exports_every_declared_symbol(lib_path):
+    out = subprocess.run(["nm", "-D", "--defined-only", lib_path], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (nbody_\w+)", out))
+    missing = _declared() - exported
+    assert not missing, f"declared but not exported: {sorted(missing)}"
+
+
+def test_library_loads_and_binding_covers_exports(lib_path):
+    lib = ctypes.CDLL(lib_path)
+    for name in _declared():
+        assert hasattr(lib, name)
+    assert set(nb.EXPORTS) == _declared()
+
+
+def test_struct_layouts_match_header():
+    # nbody_params: 4 doubles, int32, uint32; nbody_tree_record: u64, 2 x i32, 2 x i64
+    assert ctypes.sizeof(nb.Params) == 40
+    assert ctypes.sizeof(nb.TreeRecord) == 32
+
+
+def test_null_context_is_rejected_without_gpu(lib_path):
+    lib = nb.load_library(lib_path)
+    assert lib.nbody_destroy(None) == 1
+    assert lib.nbody_sync(None) == 1
+    assert lib.nbody_create(None, 10, None, None) == 1

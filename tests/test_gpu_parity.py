@@ -1,0 +1,227 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle on the same seeded inputs.
+
+Bars: keys, sort order, tree topology and (pp, pc) counters bit-exact; FP64 moments, forces and
+leapfrog states bit-exact (the FP64 kernels perform the oracle's operations in the oracle's
+order, each separately rounded); FP32 and FP32-Kahan forces within a relative RMS error of 1e-4
+of the oracle's Barnes-Hut at the same theta.
+"""
+import numpy as np
+import pytest
+
+import ics
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2203_08966_gb300 as nb  # noqa: E402
+
+DEV = "cuda:0"
+FP32_TOL = 1e-4
+
+
+def rel_rms(a, ref):
+    """sqrt(mean_i |a_i - ref_i|^2 / |ref_i|^2) over bodies with a nonzero reference."""
+    num = ((a - ref) ** 2).sum(axis=0)
+    den = (ref ** 2).sum(axis=0)
+    ok = den > 0
+    return float(np.sqrt(np.mean(num[ok] / den[ok]))) if ok.any() else 0.0
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+
+
+def cases():
+    out = {}
+    out["plummer_4096"] = ics.plummer(4096, 1)
+    out["uniform_1000_ragged"] = ics.uniform_cube(1000, 2)
+    out["plummer_33"] = ics.plummer(33, 3)
+    out["two_plummer_20000"] = ics.two_plummer(20000, seeds=(4, 5))
+    p, v, m = ics.plummer(3000, 7)
+    p[:, 100:140] = p[:, 100:101]          # 40 coincident bodies -> a level-21 bucket
+    out["coincident_bucket"] = (p, v, m)
+    q = np.zeros((3, 257))
+    q[0] = np.linspace(-1.0, 1.0, 257)     # colinear
+    out["colinear_257"] = (q, np.zeros_like(q), np.full(257, 1.0 / 257))
+    p, v, m = ics.plummer(2000, 8)
+    p[:, 5] = [1e3, -2e3, 5e2]             # far outlier: a deep, lopsided tree
+    out["outlier"] = (p, v, m)
+    return out
+
+
+CASES = cases()
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_keys_sort_box_tree_moments_bit_exact(name):
+    pos, _, mass = CASES[name]
+    n = mass.shape[0]
+    with nb.Context(n, precision=nb.FP64) as ctx:
+        ctx.build_tree(dev(pos), dev(mass))
+        box = ctx.box()
+        keys, ids = ctx.keys(n)
+        rec = ctx.tree()
+        mom = ctx.moments()
+    assert np.array_equal(box, oracle.bbox(pos))
+    ko, io = oracle.sort_pairs(oracle.keys(pos))
+    assert np.array_equal(keys, ko)
+    assert np.array_equal(ids.astype(np.int64), io)
+    t = oracle.Tree(pos, mass)
+    ref = t.records()
+    assert rec.shape == ref.shape
+    assert np.array_equal(rec, ref)
+    assert np.array_equal(mom, t.moments())
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+@pytest.mark.parametrize("theta", [0.0, 0.5, 0.7])
+def test_fp64_forces_and_counters_bit_exact(name, theta):
+    pos, _, mass = CASES[name]
+    n = mass.shape[0]
+    eps = 0.0 if name == "colinear_257" else 0.01
+    ref, rpp, rpc = oracle.bh(pos, mass, 1.0, eps, theta)
+    with nb.Context(n, 1.0, eps, theta, 1e-3, nb.FP64) as ctx:
+        a = ctx.forces(dev(pos), dev(mass)).cpu().numpy()
+        pp, pc = ctx.counters(n)
+    assert np.array_equal(pp, rpp)
+    assert np.array_equal(pc, rpc)
+    assert np.array_equal(a, ref)
+
+
+@pytest.mark.parametrize("prec", [nb.FP32, nb.FP32_KAHAN])
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_fp32_forces_within_tolerance(name, prec):
+    pos, _, mass = CASES[name]
+    n = mass.shape[0]
+    theta, eps = 0.5, 0.01
+    ref, rpp, rpc = oracle.bh(pos, mass, 1.0, eps, theta)
+    with nb.Context(n, 1.0, eps, theta, 1e-3, prec) as ctx:
+        a = ctx.forces(dev(pos), dev(mass)).cpu().numpy()
+        pp, pc = ctx.counters(n)
+    assert np.isfinite(a).all()
+    assert rel_rms(a, ref) <= FP32_TOL
+    # FP32 acceptance tests may flip only for cells right at l/d = theta
+    agree = np.mean((pp == rpp) & (pc == rpc))
+    assert agree >= 0.99
+
+
+def test_theta_zero_equals_direct_sum_on_gpu():
+    pos, _, mass = ics.plummer(3000, 12)
+    with nb.Context(3000, 1.0, 0.01, 0.0, 1e-3, nb.FP64) as ctx:
+        a_bh = ctx.forces(dev(pos), dev(mass)).cpu().numpy()
+        a_d = ctx.direct_forces(dev(pos), dev(mass)).cpu().numpy()
+    ref = oracle.direct(pos, mass, 1.0, 0.01)
+    assert np.array_equal(a_d, ref)
+    assert rel_rms(a_bh, ref) <= 1e-13
+
+
+@pytest.mark.parametrize("prec", [nb.FP64, nb.FP32])
+def test_direct_sum_targets(prec):
+    pos, _, mass = ics.plummer(5000, 13)
+    tg = np.random.default_rng(3).choice(5000, 700, replace=False).astype(np.int64)
+    ref = oracle.direct(pos, mass, 1.0, 0.005, targets=tg)
+    with nb.Context(5000, 1.0, 0.005, 0.5, 1e-3, prec) as ctx:
+        a = ctx.direct_forces(dev(pos), dev(mass), targets=dev(tg)).cpu().numpy()
+    if prec == nb.FP64:
+        assert np.array_equal(a, ref)
+    else:
+        assert rel_rms(a, ref) <= 1e-5
+
+
+def test_fp64_leapfrog_bit_exact_plummer_4096():
+    """The small configuration: Plummer N=4096, eps=0.01, theta=0.5, dt=1e-3, 10 KDK steps."""
+    w = ics.WORKLOADS["plummer_4k"]
+    pos, vel, mass = ics.plummer(w["n"], w["seed"])
+    acc0, _, _ = oracle.bh(pos, mass, 1.0, w["eps"], w["theta"])
+    rp, rv, ra = oracle.kdk(pos, vel, mass, acc0, 1.0, w["eps"], w["theta"], w["dt"], w["steps"])
+    tp, tv, tm = dev(pos), dev(vel), dev(mass)
+    with nb.Context(w["n"], 1.0, w["eps"], w["theta"], w["dt"], nb.FP64) as ctx:
+        ctx.step(tp, tv, tm, w["steps"])
+        ctx.sync()
+    assert np.array_equal(tp.cpu().numpy(), rp)
+    assert np.array_equal(tv.cpu().numpy(), rv)
+
+
+@pytest.mark.parametrize("prec", [nb.FP32, nb.FP32_KAHAN])
+def test_fp32_leapfrog_close_to_oracle(prec):
+    w = ics.WORKLOADS["plummer_4k"]
+    pos, vel, mass = ics.plummer(w["n"], w["seed"])
+    acc0, _, _ = oracle.bh(pos, mass, 1.0, w["eps"], w["theta"])
+    rp, rv, _ = oracle.kdk(pos, vel, mass, acc0, 1.0, w["eps"], w["theta"], w["dt"], w["steps"])
+    tp, tv, tm = dev(pos), dev(vel), dev(mass)
+    with nb.Context(w["n"], 1.0, w["eps"], w["theta"], w["dt"], prec) as ctx:
+        ctx.step(tp, tv, tm, w["steps"])
+        ctx.sync()
+    # force errors <= 1e-4 relative, integrated over 10 steps of dt = 1e-3
+    dv = np.abs(tv.cpu().numpy() - rv).max()
+    dp = np.abs(tp.cpu().numpy() - rp).max()
+    vscale = np.abs(acc0).max() * w["dt"] * w["steps"]
+    assert dv <= 1e-4 * vscale + 1e-12
+    assert dp <= 1e-4 * vscale * w["dt"] * w["steps"] + 1e-12
+
+
+def test_step_host_matches_device_step():
+    pos, vel, mass = ics.plummer(2048, 21)
+    tp, tv, tm = dev(pos), dev(vel), dev(mass)
+    hp, hv = pos.copy(), vel.copy()
+    with nb.Context(2048, 1.0, 0.01, 0.5, 1e-3, nb.FP64) as ctx:
+        ctx.step(tp, tv, tm, 3)
+        ctx.sync()
+    with nb.Context(2048, 1.0, 0.01, 0.5, 1e-3, nb.FP64) as ctx:
+        ctx.step_host(hp, hv, mass, 3)
+    assert np.array_equal(hp, tp.cpu().numpy())
+    assert np.array_equal(hv, tv.cpu().numpy())
+
+
+def test_tiny_and_empty_systems():
+    with nb.Context(8, 1.0, 0.0, 0.5, 1e-3, nb.FP64) as ctx:
+        # n = 0: nothing to do
+        e = torch.zeros((3, 0), dtype=torch.float64, device=DEV)
+        ctx.step(e, e.clone(), torch.zeros(0, dtype=torch.float64, device=DEV), 2)
+        # n = 1: the root is a leaf, no force
+        p1 = np.array([[0.5], [0.25], [2.0]])
+        a = ctx.forces(dev(p1), dev(np.ones(1))).cpu().numpy()
+        assert np.array_equal(a, np.zeros((3, 1)))
+        assert ctx.tree().tolist() == oracle.Tree(p1, np.ones(1)).records().tolist()
+        # n = 2: exact pair force
+        p2 = np.array([[0.0, 3.0], [0.0, 4.0], [0.0, 0.0]])
+        m2 = np.array([2.0, 5.0])
+        a = ctx.forces(dev(p2), dev(m2)).cpu().numpy()
+        ref, _, _ = oracle.bh(p2, m2, 1.0, 0.0, 0.5)
+        assert np.array_equal(a, ref)
+        assert np.allclose(a[:, 0], [5.0 * 3 / 125, 5.0 * 4 / 125, 0.0], rtol=1e-15)
+
+
+def test_bad_arguments_are_rejected():
+    with nb.Context(100, precision=nb.FP32) as ctx:
+        p = torch.zeros((3, 200), dtype=torch.float64, device=DEV)
+        m = torch.ones(200, dtype=torch.float64, device=DEV)
+        with pytest.raises(nb.NBodyError) as ei:
+            ctx.forces(p, m)
+        assert ei.value.status == 1
+        with pytest.raises(nb.NBodyError):
+            ctx.set_params(theta=-1.0)
+        with pytest.raises(nb.NBodyError):
+            ctx.step(p[:, :10].contiguous(), p[:, :10].contiguous(), m[:10].contiguous(), -1)
+        with pytest.raises(nb.NBodyError) as ei:
+            ctx.counters(10)
+        assert ei.value.status == 6
+
+
+def test_repeated_builds_reuse_context():
+    """Growing and shrinking n inside one context gives the same trees as fresh contexts."""
+    with nb.Context(30000, 1.0, 0.01, 0.6, 1e-3, nb.FP64) as ctx:
+        for n, seed in ((30000, 40), (500, 41), (12345, 42)):
+            pos, _, mass = ics.plummer(n, seed)
+            a = ctx.forces(dev(pos), dev(mass)).cpu().numpy()
+            ref, _, _ = oracle.bh(pos, mass, 1.0, 0.01, 0.6)
+            assert np.array_equal(a, ref)
+            assert np.array_equal(ctx.tree(), oracle.Tree(pos, mass).records())

@@ -437,3 +437,29 @@ def test_energy_and_momentum_drift_plummer():
     e1 = oracle.energy(p1, v1, m, eps=eps)[2]
     assert abs(e1 - e0) / abs(e0) < 1e-4
     assert np.abs(oracle.momentum(v1, m) - p0).max() < 1e-14
+
+
+def test_moments_every_cell_is_mean_of_children():
+    """Algorithm 2 moments: each cell's mass is the sum of its children's, its centre of mass
+    their mass-weighted mean; a one-body leaf holds its body exactly."""
+    pos, _, _ = ics.plummer(3000, 33)
+    m = np.random.default_rng(2).uniform(0.5, 2.0, 3000)
+    t = oracle.Tree(pos, m)
+    rec, order = t.records(with_leaf_order=True)
+    mom = t.moments()
+    assert mom.shape == (len(rec), 4)
+    level = rec[:, 1]
+    for k in range(len(rec)):
+        first, count = int(rec[k, 3]), int(rec[k, 4])
+        bodies = order[first:first + count]
+        msum = math.fsum(m[bodies])
+        assert abs(mom[k, 0] - msum) <= 1e-13 * msum
+        for d in range(3):
+            com = math.fsum(m[bodies] * pos[d, bodies]) / msum
+            assert abs(mom[k, 1 + d] - com) <= 1e-12 * max(1.0, abs(com))
+        if count == 1:
+            b = bodies[0]
+            assert list(mom[k]) == [m[b], pos[0, b], pos[1, b], pos[2, b]]
+    # children of the root are the records at level 1
+    kids = np.nonzero(level == 1)[0]
+    assert abs(math.fsum(mom[kids, 0]) - mom[0, 0]) <= 1e-13 * mom[0, 0]
