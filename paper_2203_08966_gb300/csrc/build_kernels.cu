@@ -22,79 +22,103 @@ constexpr unsigned kFull = 0xffffffffu;
 // ------------------------------------------------------------------------------------------
 
 constexpr int kBoxThreads = 256;
+constexpr int kPart = 10;  // per-block partials: min x,y,z, max x,y,z, sum m, m x, m y, m z
 
-__device__ __forceinline__ void block_minmax6(double v[6], double *out)
+// Block reduction of v[0..2] (min), v[3..5] (max), v[6..9] (sum) -> out[0..9] by thread 0.  The
+// order of every operation is fixed by the launch shape, so the sums are deterministic.
+__device__ __forceinline__ void block_reduce10(double v[kPart], double *out)
 {
-    // v[0..2] minima, v[3..5] maxima -> out[0..5] written by thread 0
-    __shared__ double sh[6][kBoxThreads / 32];
+    __shared__ double sh[kPart][kBoxThreads / 32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
-    for (int k = 0; k < 6; ++k) {
+    for (int k = 0; k < kPart; ++k) {
         double x = v[k];
         for (int o = 16; o > 0; o >>= 1) {
-            double y = __shfl_xor_sync(kFull, x, o);
-            x = k < 3 ? fmin(x, y) : fmax(x, y);
+            const double y = __shfl_xor_sync(kFull, x, o);
+            x = k < 3 ? fmin(x, y) : (k < 6 ? fmax(x, y) : __dadd_rn(x, y));
         }
         if (lane == 0) sh[k][wid] = x;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        for (int k = 0; k < 6; ++k) {
+        for (int k = 0; k < kPart; ++k) {
             double x = sh[k][0];
-            for (int w = 1; w < kBoxThreads / 32; ++w) x = k < 3 ? fmin(x, sh[k][w]) : fmax(x, sh[k][w]);
+            for (int w = 1; w < kBoxThreads / 32; ++w)
+                x = k < 3 ? fmin(x, sh[k][w]) : (k < 6 ? fmax(x, sh[k][w]) : __dadd_rn(x, sh[k][w]));
             out[k] = x;
         }
     }
 }
 
+__device__ __forceinline__ void init10(double v[kPart])
+{
+    v[0] = v[1] = v[2] = DBL_MAX;
+    v[3] = v[4] = v[5] = -DBL_MAX;
+    v[6] = v[7] = v[8] = v[9] = 0.0;
+}
+
+__device__ __forceinline__ void add_body(double v[kPart], double x, double y, double z, double m)
+{
+    v[0] = fmin(v[0], x); v[3] = fmax(v[3], x);
+    v[1] = fmin(v[1], y); v[4] = fmax(v[4], y);
+    v[2] = fmin(v[2], z); v[5] = fmax(v[5], z);
+    v[6] = __dadd_rn(v[6], m);
+    v[7] = __fma_rn(m, x, v[7]);
+    v[8] = __fma_rn(m, y, v[8]);
+    v[9] = __fma_rn(m, z, v[9]);
+}
+
 __global__ void __launch_bounds__(kBoxThreads) bbox_partials_kernel(const double *__restrict__ pos,
+                                                                    const double *__restrict__ mass,
                                                                     int n, double *partials)
 {
-    double v[6] = {DBL_MAX, DBL_MAX, DBL_MAX, -DBL_MAX, -DBL_MAX, -DBL_MAX};
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            double x = pos[(size_t)d * n + i];
-            v[d] = fmin(v[d], x);
-            v[3 + d] = fmax(v[3 + d], x);
-        }
-    }
-    block_minmax6(v, partials + 6 * blockIdx.x);
+    double v[kPart];
+    init10(v);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        add_body(v, pos[i], pos[(size_t)n + i], pos[2 * (size_t)n + i], mass[i]);
+    block_reduce10(v, partials + kPart * blockIdx.x);
 }
 
 // Kick and drift of the leapfrog (eqs. leapkick1, leapdrift of §2.3), FP64 with separately
-// rounded products and sums, fused with the box partials of the new positions.
+// rounded products and sums, fused with the box and centre-of-mass partials of the new positions.
 __global__ void __launch_bounds__(kBoxThreads) kick_drift_bbox_kernel(
-    double *__restrict__ pos, double *__restrict__ vel, const double *__restrict__ acc, int n,
-    double h, double dt, double *partials)
+    double *__restrict__ pos, double *__restrict__ vel, const double *__restrict__ acc,
+    const double *__restrict__ mass, int n, double h, double dt, double *partials)
 {
-    double v[6] = {DBL_MAX, DBL_MAX, DBL_MAX, -DBL_MAX, -DBL_MAX, -DBL_MAX};
+    double v[kPart];
+    init10(v);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double x[3];
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
             const size_t k = (size_t)d * n + i;
-            double vh = __dadd_rn(vel[k], __dmul_rn(acc[k], h));
-            double x = __dadd_rn(pos[k], __dmul_rn(vh, dt));
+            const double vh = __dadd_rn(vel[k], __dmul_rn(acc[k], h));
+            x[d] = __dadd_rn(pos[k], __dmul_rn(vh, dt));
             vel[k] = vh;
-            pos[k] = x;
-            v[d] = fmin(v[d], x);
-            v[3 + d] = fmax(v[3 + d], x);
+            pos[k] = x[d];
         }
+        add_body(v, x[0], x[1], x[2], mass[i]);
     }
-    block_minmax6(v, partials + 6 * blockIdx.x);
+    block_reduce10(v, partials + kPart * blockIdx.x);
 }
 
+// Root cube (min corner, side = largest extent, 1 when all bodies coincide), the scale 2^21 / L,
+// the per-level tables, and the origin of the FP32 coordinates: the centre of mass, so that FP32
+// offsets stay small where the mass is (their absolute rounding error is 2^-24 of the offset).
 __global__ void __launch_bounds__(kBoxThreads) bbox_finalize_kernel(const double *partials,
                                                                     int nblk, Box *box,
                                                                     LevelTables *tab, double theta)
 {
-    double v[6] = {DBL_MAX, DBL_MAX, DBL_MAX, -DBL_MAX, -DBL_MAX, -DBL_MAX};
+    double v[kPart];
+    init10(v);
     for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
-        for (int k = 0; k < 3; ++k) v[k] = fmin(v[k], partials[6 * b + k]);
-        for (int k = 3; k < 6; ++k) v[k] = fmax(v[k], partials[6 * b + k]);
+        const double *p = partials + kPart * b;
+        for (int k = 0; k < 3; ++k) v[k] = fmin(v[k], p[k]);
+        for (int k = 3; k < 6; ++k) v[k] = fmax(v[k], p[k]);
+        for (int k = 6; k < kPart; ++k) v[k] = __dadd_rn(v[k], p[k]);
     }
-    __shared__ double r[6];
-    block_minmax6(v, r);
+    __shared__ double r[kPart];
+    block_reduce10(v, r);
     __syncthreads();
     if (threadIdx.x == 0) {
         double ext = 0.0;
@@ -105,7 +129,10 @@ __global__ void __launch_bounds__(kBoxThreads) bbox_finalize_kernel(const double
         if (!(ext > 0.0)) ext = 1.0;
         for (int d = 0; d < 3; ++d) {
             box->o[d] = r[d];
-            box->c[d] = __dadd_rn(r[d], __dmul_rn(ext, 0.5));
+            double c = r[6] > 0.0 ? r[7 + d] / r[6] : __dadd_rn(r[d], __dmul_rn(ext, 0.5));
+            // keep the origin inside the box (guards against a non-finite or stray quotient)
+            if (!(c >= r[d] && c <= r[3 + d])) c = __dadd_rn(r[d], __dmul_rn(ext, 0.5));
+            box->c[d] = c;
         }
         box->L = ext;
         box->s = __ddiv_rn(2097152.0, ext);
@@ -407,14 +434,21 @@ __device__ __forceinline__ uint32_t nodes_started(int lp, int la)
     return (uint32_t)(max(0, la - lp) + 1);
 }
 
-__global__ void count_nodes_kernel(const uint64_t *__restrict__ keys, int n, uint32_t *counts)
+// Nodes started by every body, and (atomic max into *max_level) the deepest node level.
+__global__ void count_nodes_kernel(const uint64_t *__restrict__ keys, int n, uint32_t *counts,
+                                   unsigned *max_level)
 {
+    unsigned deepest = 0;
     for (int a = blockIdx.x * blockDim.x + threadIdx.x; a <= n; a += gridDim.x * blockDim.x) {
         if (a == n) { counts[n] = 0; continue; }
         int lp, la;
         body_lcps(keys, n, a, lp, la);
         counts[a] = nodes_started(lp, la);
+        const int lv = (la == kMaxLevel || lp == kMaxLevel) ? kMaxLevel : max(lp, la) + 1;
+        deepest = max(deepest, (unsigned)lv);
     }
+    deepest = __reduce_max_sync(kFull, deepest);
+    if ((threadIdx.x & 31) == 0 && deepest > 0) atomicMax(max_level, deepest);
 }
 
 // First index c > lo (c <= n) whose key differs from keys[lo] above `shift`, given that
@@ -480,29 +514,6 @@ __global__ void emit_nodes_kernel(const uint64_t *__restrict__ keys, int n,
     }
 }
 
-// Parent links, child masks (octant digit of each child) and child counts of internal cells.
-__global__ void link_nodes_kernel(const uint64_t *__restrict__ keys, int n_nodes, NodeArrays na)
-{
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n_nodes; j += gridDim.x * blockDim.x) {
-        if (j == 0) na.parent[0] = -1;
-        na.arrive[j] = 0;
-        const WalkNode w = na.wn[j];
-        if (w.count != 0) { na.mask[j] = 0; na.nchild[j] = 0; continue; }
-        const int lev = na.level[j];
-        const int shift = 3 * (kMaxLevel - 1 - lev);
-        unsigned mask = 0, nc = 0;
-        // an internal cell has at most 8 children; the bound also ends the loop on a malformed
-        // skip chain
-        for (int c = j + 1; c < w.skip && nc < 8; c = max(na.wn[c].skip, c + 1)) {
-            na.parent[c] = j;
-            mask |= 1u << (unsigned)((keys[na.wn[c].first] >> shift) & 7u);
-            ++nc;
-        }
-        na.mask[j] = (uint8_t)mask;
-        na.nchild[j] = (uint8_t)nc;
-    }
-}
-
 __device__ __forceinline__ D4 ld_cg(const D4 *p)
 {
     const double2 *q = reinterpret_cast<const double2 *>(p);
@@ -512,72 +523,87 @@ __device__ __forceinline__ D4 ld_cg(const D4 *p)
     return r;
 }
 
-__device__ __forceinline__ void store_node(NodeArrays &na, int j, const D4 &m, const Box *box,
-                                           double G, float crit)
+__device__ __forceinline__ void store_node(NodeArrays &na, int j, const WalkNode &w0, const D4 &m,
+                                           const Box *box, double G, float crit)
 {
     na.com64[j] = m;
-    WalkNode w = na.wn[j];
+    WalkNode w = w0;
     w.c = make_float4((float)(m.x - box->c[0]), (float)(m.y - box->c[1]),
                       (float)(m.z - box->c[2]), (float)(G * m.w));
     w.crit = crit;
     na.wn[j] = w;
 }
 
-// Moments from the leaves to the root (Algorithm 2): a leaf takes its body (or the mass-
-// weighted mean of its bucket, bodies in Morton order); the last child to finish computes its
-// parent from all children in octant order: m = sum m_c, r = (sum m_c r_c) / m, every product
-// and sum separately rounded.  Counters only: nothing ever waits for another thread.
-__global__ void moments_kernel(int n_nodes, const D4 *__restrict__ sbody64,
-                               const Box *__restrict__ box, const LevelTables *__restrict__ tab,
-                               double G, NodeArrays na)
+// Child masks and node kinds, plus the moments of every leaf (Algorithm 2, moments from the
+// leaves up): a one-body leaf holds its body; a level-21 bucket the mass-weighted mean of its
+// bodies in Morton order, every product and sum separately rounded.
+__global__ void link_leaves_kernel(const uint64_t *__restrict__ keys, int n_nodes, NodeArrays na,
+                                   const D4 *__restrict__ sbody64, const Box *__restrict__ box,
+                                   double G)
 {
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n_nodes; j += gridDim.x * blockDim.x) {
         const WalkNode w = na.wn[j];
-        if (w.count == 0) continue;
+        const int lev = na.level[j];
+        if (w.count != 0) {
+            na.mask[j] = 0;
+            na.kind[j] = kLeafKind;
+            D4 m;
+            if (w.count == 1) {
+                m = sbody64[w.first];
+            } else {
+                double s = 0.0, sx = 0.0, sy = 0.0, sz = 0.0;
+                for (int b = w.first; b < w.first + w.count; ++b) {
+                    const D4 q = sbody64[b];
+                    s = __dadd_rn(s, q.w);
+                    sx = __dadd_rn(sx, __dmul_rn(q.w, q.x));
+                    sy = __dadd_rn(sy, __dmul_rn(q.w, q.y));
+                    sz = __dadd_rn(sz, __dmul_rn(q.w, q.z));
+                }
+                m.w = s;
+                m.x = __ddiv_rn(sx, s);
+                m.y = __ddiv_rn(sy, s);
+                m.z = __ddiv_rn(sz, s);
+            }
+            store_node(na, j, w, m, box, G, 0.f);
+            continue;
+        }
+        const int shift = 3 * (kMaxLevel - 1 - lev);
+        unsigned mask = 0;
+        int nc = 0;
+        // an internal cell has at most 8 children; the bound also ends the loop on a malformed
+        // skip chain
+        for (int c = j + 1; c < w.skip && nc < 8; c = max(na.wn[c].skip, c + 1), ++nc)
+            mask |= 1u << (unsigned)((keys[na.wn[c].first] >> shift) & 7u);
+        na.mask[j] = (uint8_t)mask;
+        na.kind[j] = (uint8_t)lev;
+    }
+}
+
+// Moments of the internal cells of one level, from their children (one level deeper, already
+// done): m = sum m_c, r = (sum m_c r_c) / m over the children in octant order, every product and
+// sum separately rounded.  Launched for the levels from the deepest up to the root.
+__global__ void moments_level_kernel(int level, int n_nodes, NodeArrays na,
+                                     const Box *__restrict__ box,
+                                     const LevelTables *__restrict__ tab, double G)
+{
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n_nodes; j += gridDim.x * blockDim.x) {
+        if (na.kind[j] != level) continue;
+        const WalkNode w = na.wn[j];
+        double s = 0.0, sx = 0.0, sy = 0.0, sz = 0.0;
+        int nc = 0;
+        for (int c = j + 1; c < w.skip && nc < 8; c = max(__ldcg(&na.wn[c].skip), c + 1), ++nc) {
+            const D4 q = ld_cg(&na.com64[c]);
+            s = __dadd_rn(s, q.w);
+            sx = __dadd_rn(sx, __dmul_rn(q.w, q.x));
+            sy = __dadd_rn(sy, __dmul_rn(q.w, q.y));
+            sz = __dadd_rn(sz, __dmul_rn(q.w, q.z));
+        }
         D4 m;
-        if (w.count == 1) {
-            m = sbody64[w.first];
-        } else {
-            double s = 0.0, sx = 0.0, sy = 0.0, sz = 0.0;
-            for (int b = w.first; b < w.first + w.count; ++b) {
-                const D4 q = sbody64[b];
-                s = __dadd_rn(s, q.w);
-                sx = __dadd_rn(sx, __dmul_rn(q.w, q.x));
-                sy = __dadd_rn(sy, __dmul_rn(q.w, q.y));
-                sz = __dadd_rn(sz, __dmul_rn(q.w, q.z));
-            }
-            m.w = s;
-            m.x = __ddiv_rn(sx, s);
-            m.y = __ddiv_rn(sy, s);
-            m.z = __ddiv_rn(sz, s);
-        }
-        store_node(na, j, m, box, G, 0.f);
-        int cur = j;
-        for (;;) {
-            const int p = na.parent[cur];
-            if (p < 0) break;
-            __threadfence();
-            const int seen = atomicAdd(&na.arrive[p], 1);
-            if (seen != (int)na.nchild[p] - 1) break;
-            __threadfence();
-            const int pskip = __ldcg(&na.wn[p].skip);
-            double s = 0.0, sx = 0.0, sy = 0.0, sz = 0.0;
-            int nc = 0;
-            for (int c = p + 1; c < pskip && nc < 8; c = max(__ldcg(&na.wn[c].skip), c + 1), ++nc) {
-                const D4 q = ld_cg(&na.com64[c]);
-                s = __dadd_rn(s, q.w);
-                sx = __dadd_rn(sx, __dmul_rn(q.w, q.x));
-                sy = __dadd_rn(sy, __dmul_rn(q.w, q.y));
-                sz = __dadd_rn(sz, __dmul_rn(q.w, q.z));
-            }
-            D4 pm;
-            pm.w = s;
-            pm.x = __ddiv_rn(sx, s);
-            pm.y = __ddiv_rn(sy, s);
-            pm.z = __ddiv_rn(sz, s);
-            store_node(na, p, pm, box, G, tab->crit32[na.level[p]]);
-            cur = p;
-        }
+        m.w = s;
+        m.x = __ddiv_rn(sx, s);
+        m.y = __ddiv_rn(sy, s);
+        m.z = __ddiv_rn(sz, s);
+        store_node(na, j, w, m, box, G, tab->crit32[level]);
     }
 }
 
@@ -672,17 +698,19 @@ void count_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed);
 int64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 int bbox_blocks(int64_t n) { return grid_for(n, kBoxThreads * 4, 152 * 8); }
+int bbox_partial_doubles() { return kPart; }
 
-void launch_bbox_partials(const double *pos, int n, double *partials, int nblk, cudaStream_t s)
+void launch_bbox_partials(const double *pos, const double *mass, int n, double *partials, int nblk,
+                          cudaStream_t s)
 {
-    bbox_partials_kernel<<<nblk, kBoxThreads, 0, s>>>(pos, n, partials);
+    bbox_partials_kernel<<<nblk, kBoxThreads, 0, s>>>(pos, mass, n, partials);
     count_launches(1);
 }
 
-void launch_kick_drift_bbox(double *pos, double *vel, const double *acc, int n, double h,
-                            double dt, double *partials, int nblk, cudaStream_t s)
+void launch_kick_drift_bbox(double *pos, double *vel, const double *acc, const double *mass, int n,
+                            double h, double dt, double *partials, int nblk, cudaStream_t s)
 {
-    kick_drift_bbox_kernel<<<nblk, kBoxThreads, 0, s>>>(pos, vel, acc, n, h, dt, partials);
+    kick_drift_bbox_kernel<<<nblk, kBoxThreads, 0, s>>>(pos, vel, acc, mass, n, h, dt, partials);
     count_launches(1);
 }
 
@@ -739,9 +767,11 @@ void launch_permute(const double *pos, const double *mass, const uint32_t *ids, 
 
 int scan_tiles(int len) { return (len + kScanTile - 1) / kScanTile; }
 
-void launch_count_nodes(const uint64_t *keys, int n, uint32_t *counts, cudaStream_t s)
+void launch_count_nodes(const uint64_t *keys, int n, uint32_t *counts, unsigned *max_level,
+                        cudaStream_t s)
 {
-    count_nodes_kernel<<<grid_for((int64_t)n + 1, 256, kMaxGrid), 256, 0, s>>>(keys, n, counts);
+    count_nodes_kernel<<<grid_for((int64_t)n + 1, 256, kMaxGrid), 256, 0, s>>>(keys, n, counts,
+                                                                              max_level);
     count_launches(1);
 }
 
@@ -762,18 +792,15 @@ void launch_emit_nodes(const uint64_t *keys, int n, const uint32_t *node_off, No
     count_launches(1);
 }
 
-void launch_link_nodes(const uint64_t *keys, int n_nodes, NodeArrays na, cudaStream_t s)
+void launch_moments(const uint64_t *keys, int n_nodes, int max_level, const D4 *sbody64,
+                    const Box *box, const LevelTables *tab, double G, NodeArrays na,
+                    cudaStream_t s)
 {
-    link_nodes_kernel<<<grid_for(n_nodes, 256, kMaxGrid * 4), 256, 0, s>>>(keys, n_nodes, na);
-    count_launches(1);
-}
-
-void launch_moments(int n_nodes, const D4 *sbody64, const Box *box, const LevelTables *tab,
-                    double G, NodeArrays na, cudaStream_t s)
-{
-    moments_kernel<<<grid_for(n_nodes, 256, kMaxGrid * 4), 256, 0, s>>>(n_nodes, sbody64, box, tab,
-                                                                       G, na);
-    count_launches(1);
+    const int grid = grid_for(n_nodes, 256, kMaxGrid * 4);
+    link_leaves_kernel<<<grid, 256, 0, s>>>(keys, n_nodes, na, sbody64, box, G);
+    for (int lev = min(max_level, kMaxLevel) - 1; lev >= 0; --lev)
+        moments_level_kernel<<<grid, 256, 0, s>>>(lev, n_nodes, na, box, tab, G);
+    count_launches(1 + max(0, min(max_level, kMaxLevel)));
 }
 
 }  // namespace nb

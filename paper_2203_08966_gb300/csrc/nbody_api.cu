@@ -29,14 +29,15 @@ struct nbody_ctx {
     uint32_t *hist = nullptr;       // 8 x 256
     uint32_t *counts = nullptr;     // 256 x sort tiles
     uint32_t *block_sums = nullptr; // scan tiles + 1
-    double *partials = nullptr;     // 6 x bbox blocks
+    double *partials = nullptr;     // bbox_partial_doubles() x bbox blocks
     int nblk = 0;
     Box *box = nullptr;             // [0] last build, [1] direct sum
     LevelTables *tab = nullptr;     // [0] last build, [1] direct sum
     double *acc = nullptr;          // 3 x cap: a^(k) kept between steps
     uint32_t *pp = nullptr, *pc = nullptr;
     int *err = nullptr;             // device error word
-    uint32_t *h_word = nullptr;     // pinned host word for the node count
+    uint32_t *h_word = nullptr;     // pinned host words: node count, deepest level
+    unsigned *info = nullptr;       // device word: deepest node level of the last build
 
     // octree
     NodeArrays na{};
@@ -115,9 +116,7 @@ void free_nodes(nbody_ctx *c)
     dfree(c->na.com64);
     dfree(c->na.level);
     dfree(c->na.mask);
-    dfree(c->na.nchild);
-    dfree(c->na.parent);
-    dfree(c->na.arrive);
+    dfree(c->na.kind);
     c->na.cap = 0;
 }
 
@@ -130,9 +129,7 @@ nbody_status ensure_nodes(nbody_ctx *c, int64_t need)
     CK(dalloc(&c->na.com64, cap));
     CK(dalloc(&c->na.level, cap));
     CK(dalloc(&c->na.mask, cap));
-    CK(dalloc(&c->na.nchild, cap));
-    CK(dalloc(&c->na.parent, cap));
-    CK(dalloc(&c->na.arrive, cap));
+    CK(dalloc(&c->na.kind, cap));
     c->na.cap = cap;
     return NBODY_OK;
 }
@@ -168,7 +165,7 @@ nbody_status build(nbody_ctx *c, const double *pos, const double *mass, int n,
         c->n_built = 0;
         return NBODY_OK;
     }
-    if (!have_partials) launch_bbox_partials(pos, n, c->partials, c->nblk, s);
+    if (!have_partials) launch_bbox_partials(pos, mass, n, c->partials, c->nblk, s);
     launch_bbox_finalize(c->partials, c->nblk, c->box, c->tab, c->p.theta, s);
     launch_keys(pos, n, c->box, c->keys, c->ids, s);
     record(c, 1);
@@ -176,20 +173,22 @@ nbody_status build(nbody_ctx *c, const double *pos, const double *mass, int n,
     launch_radix_sort(c->keys, c->ids, n, sc, s);
     record(c, 2);
     launch_permute(pos, mass, c->ids, n, c->box, c->p.G, c->sbody64, c->sbody32, s);
-    launch_count_nodes(c->keys, n, c->node_off, s);
+    CK(cudaMemsetAsync(c->info, 0, sizeof(unsigned), s));
+    launch_count_nodes(c->keys, n, c->node_off, c->info, s);
     ScanScratch ss{c->block_sums, scan_tiles((int)c->cap + 1)};
     launch_exclusive_scan(c->node_off, c->node_off, n + 1, ss, s);
     CKS(check_launch(c, "tree build"));
     CK(cudaMemcpyAsync(c->h_word, c->node_off + n, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(c->h_word + 1, c->info, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    const int64_t nn = (int64_t)*c->h_word;
+    const int64_t nn = (int64_t)c->h_word[0];
+    const int max_level = (int)c->h_word[1];
     if (nn < 1 || nn > 22 * (int64_t)n)
         return fail(c, NBODY_ECUDA, "node count %lld out of range for n = %d", (long long)nn, n);
     CKS(ensure_nodes(c, nn));
     c->n_nodes = nn;
     launch_emit_nodes(c->keys, n, c->node_off, c->na, s);
-    launch_link_nodes(c->keys, (int)nn, c->na, s);
-    launch_moments((int)nn, c->sbody64, c->box, c->tab, c->p.G, c->na, s);
+    launch_moments(c->keys, (int)nn, max_level, c->sbody64, c->box, c->tab, c->p.G, c->na, s);
     record(c, 3);
     CKS(check_launch(c, "node split / moments"));
     c->n_built = n;
@@ -274,7 +273,7 @@ nbody_status nbody_create(nbody_ctx **out, int64_t n_capacity, const nbody_param
         CK(dalloc(&c->counts, (size_t)256 * sort_tiles((int)cap)));
         CK(dalloc(&c->block_sums, (size_t)scan_tiles((int)cap + 1) + 1));
         c->nblk = bbox_blocks((int64_t)cap);
-        CK(dalloc(&c->partials, (size_t)6 * c->nblk));
+        CK(dalloc(&c->partials, (size_t)bbox_partial_doubles() * c->nblk));
         CK(dalloc(&c->box, 2));
         CK(dalloc(&c->tab, 2));
         CK(dalloc(&c->acc, 3 * cap));
@@ -282,7 +281,8 @@ nbody_status nbody_create(nbody_ctx **out, int64_t n_capacity, const nbody_param
         CK(dalloc(&c->pc, cap));
         CK(dalloc(&c->err, 1));
         CK(cudaMemset(c->err, 0, sizeof(int)));
-        CK(cudaMallocHost((void **)&c->h_word, sizeof(uint32_t)));
+        CK(cudaMallocHost((void **)&c->h_word, 2 * sizeof(uint32_t)));
+        CK(dalloc(&c->info, 1));
         for (int k = 0; k < 6; ++k) CK(cudaEventCreate(&c->ev[k]));
         return NBODY_OK;
     };
@@ -316,6 +316,7 @@ nbody_status nbody_destroy(nbody_ctx *c)
     dfree(c->pp);
     dfree(c->pc);
     dfree(c->err);
+    dfree(c->info);
     dfree(c->hpos);
     dfree(c->hvel);
     dfree(c->hmass);
@@ -374,8 +375,8 @@ nbody_status nbody_step(nbody_ctx *c, double *d_pos, double *d_vel, const double
     }
     for (int32_t k = 0; k < nsteps; ++k) {
         CKS(begin_timing(c));
-        launch_kick_drift_bbox(d_pos, d_vel, c->acc, (int)n, h, c->p.dt, c->partials, c->nblk,
-                               c->stream);
+        launch_kick_drift_bbox(d_pos, d_vel, c->acc, d_mass, (int)n, h, c->p.dt, c->partials,
+                               c->nblk, c->stream);
         CKS(check_launch(c, "kick/drift"));
         CKS(build(c, d_pos, d_mass, (int)n, true));
         CKS(walk(c, (int)n, c->acc, d_vel, h));
@@ -433,7 +434,7 @@ nbody_status nbody_direct_forces(nbody_ctx *c, const double *d_pos, const double
     if (nt < 0 || nt > ((int64_t)1 << 30)) return fail(c, NBODY_EINVAL, "bad target count");
     if (n > 0 && (!d_pos || !d_mass || !d_acc)) return fail(c, NBODY_EINVAL, "null pointer");
     if (n == 0 || nt == 0) return NBODY_OK;
-    launch_bbox_partials(d_pos, (int)n, c->partials, c->nblk, c->stream);
+    launch_bbox_partials(d_pos, d_mass, (int)n, c->partials, c->nblk, c->stream);
     launch_bbox_finalize(c->partials, c->nblk, c->box + 1, c->tab + 1, c->p.theta, c->stream);
     launch_direct(c->p.precision, d_pos, d_mass, (int)n, d_targets, (int)nt, c->p.G, c->p.eps,
                   c->box + 1, d_acc, c->stream);

@@ -37,7 +37,7 @@ struct Box {
     double o[3];      // min corner
     double L;         // cube side
     double s;         // 2^21 / L
-    double c[3];      // centre o + L/2 (origin of the FP32 coordinates)
+    double c[3];      // origin of the FP32 coordinates: the centre of mass
 };
 
 // Device error word bits.
@@ -55,9 +55,12 @@ int64_t launch_count();
 
 // ---------------------------------------------------------------- build_kernels.cu
 int bbox_blocks(int64_t n);
-void launch_bbox_partials(const double *pos, int n, double *partials, int nblk, cudaStream_t s);
-void launch_kick_drift_bbox(double *pos, double *vel, const double *acc, int n, double h,
-                            double dt, double *partials, int nblk, cudaStream_t s);
+int bbox_partial_doubles();  // doubles per block in the partials buffer
+void launch_bbox_partials(const double *pos, const double *mass, int n, double *partials,
+                          int nblk, cudaStream_t s);
+void launch_kick_drift_bbox(double *pos, double *vel, const double *acc, const double *mass,
+                            int n, double h, double dt, double *partials, int nblk,
+                            cudaStream_t s);
 void launch_bbox_finalize(const double *partials, int nblk, Box *box, LevelTables *tab,
                           double theta, cudaStream_t s);
 void launch_keys(const double *pos, int n, const Box *box, uint64_t *keys, uint32_t *ids,
@@ -83,25 +86,28 @@ struct ScanScratch {
     int max_tiles;
 };
 int scan_tiles(int len);
-void launch_count_nodes(const uint64_t *keys, int n, uint32_t *counts, cudaStream_t s);
+void launch_count_nodes(const uint64_t *keys, int n, uint32_t *counts, unsigned *max_level,
+                        cudaStream_t s);
 void launch_exclusive_scan(const uint32_t *in, uint32_t *out, int len, const ScanScratch &sc,
                            cudaStream_t s);
+
+// Node kind byte: the level of an internal cell, kLeafKind for a leaf.
+constexpr uint8_t kLeafKind = 0x80;
 
 struct NodeArrays {
     WalkNode *wn;
     D4 *com64;
     uint8_t *level;
     uint8_t *mask;
-    uint8_t *nchild;
-    int *parent;
-    int *arrive;
+    uint8_t *kind;
     int64_t cap;
 };
 void launch_emit_nodes(const uint64_t *keys, int n, const uint32_t *node_off, NodeArrays na,
                        cudaStream_t s);
-void launch_link_nodes(const uint64_t *keys, int n_nodes, NodeArrays na, cudaStream_t s);
-void launch_moments(int n_nodes, const D4 *sbody64, const Box *box, const LevelTables *tab,
-                    double G, NodeArrays na, cudaStream_t s);
+// Child masks, node kinds, leaf moments, then the internal cells level by level up to the root.
+void launch_moments(const uint64_t *keys, int n_nodes, int max_level, const D4 *sbody64,
+                    const Box *box, const LevelTables *tab, double G, NodeArrays na,
+                    cudaStream_t s);
 
 // ---------------------------------------------------------------- walk_kernels.cu
 struct WalkArgs {

@@ -57,27 +57,46 @@ __device__ __forceinline__ void pair64(double xj, double yj, double zj, double m
     }
 }
 
-// FP32 accumulator, plain or Kahan-compensated.
+// FP32 accumulator.  Plain: one running sum per component.  Compensated: the terms go into a
+// plain FP32 partial sum, which is folded into a Kahan-compensated total (Kahan 1965) every
+// kFold walk iterations and at the end, so the compensation costs a few operations per block of
+// terms instead of four per term; the error of the total is that of partials of at most kFold
+// terms plus a compensated sum over the partials.
 template <bool kKahan>
 struct Acc3 {
-    float x = 0.f, y = 0.f, z = 0.f;
-    float cx = 0.f, cy = 0.f, cz = 0.f;
+    static constexpr int kFold = 64;
+    float x = 0.f, y = 0.f, z = 0.f;     // plain sum, or the current partial
+    float sx = 0.f, sy = 0.f, sz = 0.f;  // compensated total
+    float cx = 0.f, cy = 0.f, cz = 0.f;  // its compensation
     __device__ __forceinline__ void add(float tx, float ty, float tz)
     {
+        x += tx;
+        y += ty;
+        z += tz;
+    }
+    __device__ __forceinline__ static void kahan(float &s, float &c, float t)
+    {
+        const float yv = t - c;
+        const float u = s + yv;
+        c = (u - s) - yv;
+        s = u;
+    }
+    __device__ __forceinline__ void fold()
+    {
         if (kKahan) {
-            const float yx = tx - cx, yy = ty - cy, yz = tz - cz;
-            const float sx = x + yx, sy = y + yy, sz = z + yz;
-            cx = (sx - x) - yx;
-            cy = (sy - y) - yy;
-            cz = (sz - z) - yz;
-            x = sx;
-            y = sy;
-            z = sz;
-        } else {
-            x += tx;
-            y += ty;
-            z += tz;
+            kahan(sx, cx, x);
+            kahan(sy, cy, y);
+            kahan(sz, cz, z);
+            x = y = z = 0.f;
         }
+    }
+    __device__ __forceinline__ float3 result()
+    {
+        if (kKahan) {
+            fold();
+            return make_float3(sx, sy, sz);
+        }
+        return make_float3(x, y, z);
     }
 };
 
@@ -118,9 +137,11 @@ __global__ void __launch_bounds__(kWalkThreads) walk32_kernel(WalkArgs a)
     // the root is never tested: a body starts at the root's first child (none when the root is a
     // leaf, i.e. a single body)
     int next = (!live || n_nodes < 2 || __ldg(&a.wn[0].count) != 0) ? n_nodes : 1;
+    unsigned it = 0;
     for (;;) {
         const int j = __reduce_min_sync(kFull, next);
         if (j >= n_nodes) break;
+        if (kKahan && (++it % Acc3<kKahan>::kFold) == 0) acc.fold();
         if (next != j) continue;
         const float4 c = ldg4(&a.wn[j].c);
         const int4 meta = __ldg(reinterpret_cast<const int4 *>(&a.wn[j].skip));
@@ -157,7 +178,8 @@ __global__ void __launch_bounds__(kWalkThreads) walk32_kernel(WalkArgs a)
         }
         next = max(next, j + 1);  // progress even on a malformed skip
     }
-    if (live) write_out(a, i, (double)acc.x, (double)acc.y, (double)acc.z, pp, pc);
+    const float3 r = acc.result();
+    if (live) write_out(a, i, (double)r.x, (double)r.y, (double)r.z, pp, pc);
 }
 
 // FP64 walk, operation for operation the plain per-particle definition: the MAC is
