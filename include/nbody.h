@@ -14,7 +14,7 @@
  *                  when l/d < theta, evaluated as l*l < theta*theta*d*d, else it is opened;
  *                  the root itself is never tested),
  *   softened pair kernel  (eq. `motion` of §2.1 with |r|^2 replaced by |r|^2 + eps^2),
- *   leapfrog      (kick-drift-kick, eqs. `leapkick1`, `leapdrift`, `leapkick2` of §2.3).
+ *   leapfrog      (kick-drift-kick, eqs. `leapkick1`, `leapdrift`, `leapkick2` of §2.4).
  *
  * Conventions shared by every entry point
  *   - Array layout is structure-of-arrays float64: pos = [x_0..x_{N-1} | y_0.. | z_0..] (3N
@@ -63,7 +63,7 @@ typedef enum {
 
 /* Physical and numerical parameters.  G: gravitational constant; eps: Plummer softening length
  * (§2.1); theta: opening angle of the acceptance test l/d < theta (§3); dt: leapfrog time step
- * (§2.3); precision: nbody_precision; flags: 0 (reserved, must be 0). */
+ * (§2.4); precision: nbody_precision; flags: 0 (reserved, must be 0). */
 typedef struct {
     double G;
     double eps;
@@ -111,7 +111,7 @@ nbody_status nbody_build_tree(nbody_ctx *c, const double *d_pos, const double *d
 nbody_status nbody_forces(nbody_ctx *c, const double *d_pos, const double *d_mass, int64_t n,
                           double *d_acc);
 
-/* Advances d_pos/d_vel in place by nsteps kick-drift-kick steps of the context's dt (§2.3):
+/* Advances d_pos/d_vel in place by nsteps kick-drift-kick steps of the context's dt (§2.4):
  * v += a dt/2; r += v dt; a = BH(r); v += a dt/2.  The acceleration at the current positions
  * is kept in the context between calls; the first call after create, set_params or a change
  * of n computes it first.  Synchronises once per step (node count).  nsteps >= 0. */
@@ -169,6 +169,33 @@ nbody_status nbody_get_timings(nbody_ctx *c, float *h_ms5);
 /* Number of kernel launches the library has made in this process (all contexts), so callers
  * can count the launches inside a timed region.  Errors: EINVAL when out == NULL. */
 nbody_status nbody_get_launch_count(int64_t *out);
+
+/* ---- allocation-free keys + sort ---- */
+
+/* Largest n accepted by nbody_sort_keys_noalloc. */
+#define NBODY_NOALLOC_MAX_N 262144
+
+/* The paper has no counterpart to this entry point: it exists for callers that cannot call
+ * cudaMalloc -- code running while a CUDA graph is being captured, runtimes that own a fixed
+ * device-memory budget or forbid allocation after start-up.  It computes what nbody_build_tree
+ * followed by nbody_get_keys returns (root box, Morton keys, stable sort by key then id) without
+ * a context and without allocating: its working memory is one file-scope device array of about
+ * 3.2 MB, which every GPU that loads the library holds until the process exits.
+ *   d_pos (3n doubles, SoA) and d_mass (n doubles): device inputs, caller-owned.
+ *   d_keys_sorted (n uint64) and d_ids_sorted (n uint32): device outputs, caller-owned; on
+ *   return (once the stream reaches the work) they hold the sorted Morton keys and the user
+ *   index of every sorted body.
+ *   cuda_stream: a cudaStream_t (NULL = the legacy default stream); the call is asynchronous.
+ * Errors: NBODY_EINVAL when n < 0, n > NBODY_NOALLOC_MAX_N or a pointer is NULL (n == 0 is a
+ * no-op); NBODY_ECUDA when a CUDA call fails.
+ * The first call on each device looks up the array's device address (cudaGetSymbolAddress) and
+ * sets a kernel attribute, so make that first call before any stream capture.  Every call on a
+ * device shares the one array and leaves its last contents there: calls whose work overlaps on
+ * the GPU (different streams, or host threads without ordering) race and must be serialised by
+ * the caller. */
+nbody_status nbody_sort_keys_noalloc(const double *d_pos, const double *d_mass, int64_t n,
+                                     uint64_t *d_keys_sorted, uint32_t *d_ids_sorted,
+                                     void *cuda_stream);
 
 /* Copies the last error message (NUL-terminated, truncated to cap bytes). */
 nbody_status nbody_last_error(nbody_ctx *c, char *buf, int64_t cap);

@@ -30,7 +30,7 @@ EXPORTS = ("nbody_create", "nbody_destroy", "nbody_set_params", "nbody_build_tre
            "nbody_forces", "nbody_step", "nbody_step_host", "nbody_direct_forces", "nbody_sync",
            "nbody_get_keys", "nbody_get_box", "nbody_get_tree", "nbody_get_moments",
            "nbody_get_counters", "nbody_enable_timing", "nbody_get_timings",
-           "nbody_last_error", "nbody_get_launch_count")
+           "nbody_last_error", "nbody_get_launch_count", "nbody_sort_keys_noalloc")
 
 
 class NBodyError(RuntimeError):
@@ -86,6 +86,7 @@ def load_library(path: str = LIB_PATH):
         "nbody_get_timings": [vp, vp],
         "nbody_last_error": [vp, ctypes.c_char_p, i64],
         "nbody_get_launch_count": [ctypes.POINTER(i64)],
+        "nbody_sort_keys_noalloc": [vp, vp, i64, vp, vp, vp],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
