@@ -261,7 +261,7 @@ def kdk(pos, vel, mass, acc, G=1.0, eps=0.0, theta=0.5, dt=1e-3, nsteps=1, metho
 
 
 def energy(pos, vel, mass, G=1.0, eps=0.0):
-    """(E_kin, E_pot, E_tot), §2.4 with the pair sum over i < j."""
+    """(E_kin, E_pot, E_tot), §2.3 with the pair sum over i < j."""
     pos = _soa(pos)
     vel = _soa(vel)
     mass = np.ascontiguousarray(mass, dtype=np.float64)

@@ -20,8 +20,8 @@
  *   - Morton keys: 21 bits per axis, bit interleave with x most significant (§4.4, Fig. `hot`).
  *   - Hashed-octree cell keys: root 1, child = parent << 3 | digit (§4.7).
  *   - Pre-order serialisation with an 8-bit child mask (§4.2).
- *   - Kick-drift-kick leapfrog, eqs. `leapkick1`, `leapdrift`, `leapkick2` (§2.3).
- *   - Energy, §2.4 (pair sum taken over i < j, softened like the force).
+ *   - Kick-drift-kick leapfrog, eqs. `leapkick1`, `leapdrift`, `leapkick2` (§2.4).
+ *   - Energy, §2.3 (pair sum taken over i < j, softened like the force).
  *
  * Readings where the paper is silent or garbled (all mirrored in the project's design notes):
  *   root box = tight FP64 min corner, side = largest extent (1 if all bodies coincide);
@@ -508,7 +508,7 @@ void orc_bh(const double *pos, const double *mass, int64_t n, double G, double e
 }
 
 /* ------------------------------------------------------------------ */
-/* Kick-drift-kick leapfrog (§2.3, eqs. leapkick1, leapdrift, leapkick2). */
+/* Kick-drift-kick leapfrog (§2.4, eqs. leapkick1, leapdrift, leapkick2). */
 /* ------------------------------------------------------------------ */
 
 /* Advances nsteps steps.  On entry acc holds a^(k) at the entry positions; on exit it holds the
@@ -528,7 +528,7 @@ void orc_kdk(double *pos, double *vel, const double *mass, int64_t n, double *ac
 }
 
 /* ------------------------------------------------------------------ */
-/* Energy (§2.4): E_kin = sum m v^2 / 2, E_pot = -sum_{i<j} G m_i m_j / sqrt(r_ij^2 + eps^2). */
+/* Energy (§2.3): E_kin = sum m v^2 / 2, E_pot = -sum_{i<j} G m_i m_j / sqrt(r_ij^2 + eps^2). */
 /* ------------------------------------------------------------------ */
 
 void orc_energy(const double *pos, const double *vel, const double *mass, int64_t n, double G,

@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(kBoxThreads) bbox_partials_kernel(const double
     block_reduce10(v, partials + kPart * blockIdx.x);
 }
 
-// Kick and drift of the leapfrog (eqs. leapkick1, leapdrift of §2.3), FP64 with separately
+// Kick and drift of the leapfrog (eqs. leapkick1, leapdrift of §2.4), FP64 with separately
 // rounded products and sums, fused with the box and centre-of-mass partials of the new positions.
 __global__ void __launch_bounds__(kBoxThreads) kick_drift_bbox_kernel(
     double *__restrict__ pos, double *__restrict__ vel, const double *__restrict__ acc,

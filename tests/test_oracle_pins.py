@@ -354,7 +354,7 @@ def test_bh_coincident_bodies_bucket():
         assert np.allclose(a, ad, rtol=1e-14, atol=0)
 
 
-# ---------------------------------------------------------------- KDK leapfrog (§2.3) and energy (§2.4)
+# ---------------------------------------------------------------- KDK leapfrog (§2.4) and energy (§2.3)
 
 def _circular_pair(eps, r=1.0, m1=0.5, m2=0.5):
     M = m1 + m2
@@ -426,7 +426,7 @@ def test_energy_two_body_closed_form():
 
 
 def test_energy_and_momentum_drift_plummer():
-    """The paper's validation criterion (§2.4, §5): total energy is conserved up to the
+    """The paper's validation criterion (§2.3, §5): total energy is conserved up to the
     integrator's truncation error; momentum to rounding (direct sum is antisymmetric)."""
     pos, vel, m = ics.plummer(1024, 81)
     eps, dt = 0.01, 1e-3
