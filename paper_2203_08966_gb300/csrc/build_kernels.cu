@@ -6,6 +6,7 @@
 // serialisation).  Every step here is integer or exact FP64 work, so keys, order and topology
 // are bit-identical to a plain CPU evaluation of the same definitions.
 #include <float.h>
+#include <algorithm>
 #include <atomic>
 #include <math.h>
 
@@ -539,8 +540,11 @@ __device__ __forceinline__ void store_node(NodeArrays &na, int j, const WalkNode
 // bodies in Morton order, every product and sum separately rounded.
 __global__ void link_leaves_kernel(const uint64_t *__restrict__ keys, int n_nodes, NodeArrays na,
                                    const D4 *__restrict__ sbody64, const Box *__restrict__ box,
-                                   double G)
+                                   double G, unsigned *level_count)
 {
+    __shared__ unsigned hist[kLevels];
+    if (threadIdx.x < kLevels) hist[threadIdx.x] = 0;
+    __syncthreads();
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n_nodes; j += gridDim.x * blockDim.x) {
         const WalkNode w = na.wn[j];
         const int lev = na.level[j];
@@ -576,18 +580,60 @@ __global__ void link_leaves_kernel(const uint64_t *__restrict__ keys, int n_node
             mask |= 1u << (unsigned)((keys[na.wn[c].first] >> shift) & 7u);
         na.mask[j] = (uint8_t)mask;
         na.kind[j] = (uint8_t)lev;
+        atomicAdd(&hist[lev], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x < kLevels && hist[threadIdx.x]) atomicAdd(&level_count[threadIdx.x], hist[threadIdx.x]);
+}
+
+// level_start[l] = number of internal cells at levels < l (exclusive scan of 22 counters); the
+// scatter cursors restart at zero.
+__global__ void level_scan_kernel(const unsigned *level_count, unsigned *level_start,
+                                  unsigned *cursor)
+{
+    if (threadIdx.x == 0) {
+        unsigned run = 0;
+        for (int l = 0; l < kLevels; ++l) {
+            level_start[l] = run;
+            run += level_count[l];
+            cursor[l] = 0;
+        }
+        level_start[kLevels] = run;
+    }
+}
+
+// Lists the internal cells of every level: list[level_start[l] ..] holds those at level l.
+__global__ void level_scatter_kernel(int n_nodes, const uint8_t *__restrict__ kind,
+                                     const unsigned *__restrict__ level_start, unsigned *cursor,
+                                     int *list)
+{
+    const int lane = threadIdx.x & 31;
+    for (int base = blockIdx.x * blockDim.x; base < n_nodes; base += gridDim.x * blockDim.x) {
+        const int j = base + threadIdx.x;
+        const unsigned k = j < n_nodes ? kind[j] : (unsigned)kLeafKind;
+        const unsigned peers = __match_any_sync(kFull, k);
+        if (k < (unsigned)kLevels) {
+            const int leader = __ffs(peers) - 1;
+            unsigned off = 0;
+            if (lane == leader) off = atomicAdd(&cursor[k], (unsigned)__popc(peers));
+            off = __shfl_sync(peers, off, leader);
+            const unsigned rank = __popc(peers & ((1u << lane) - 1u));
+            list[level_start[k] + off + rank] = j;
+        }
     }
 }
 
 // Moments of the internal cells of one level, from their children (one level deeper, already
 // done): m = sum m_c, r = (sum m_c r_c) / m over the children in octant order, every product and
 // sum separately rounded.  Launched for the levels from the deepest up to the root.
-__global__ void moments_level_kernel(int level, int n_nodes, NodeArrays na,
+__global__ void moments_level_kernel(int level, const unsigned *__restrict__ level_start,
+                                     const int *__restrict__ list, NodeArrays na,
                                      const Box *__restrict__ box,
                                      const LevelTables *__restrict__ tab, double G)
 {
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n_nodes; j += gridDim.x * blockDim.x) {
-        if (na.kind[j] != level) continue;
+    const int lo = (int)level_start[level], hi = (int)level_start[level + 1];
+    for (int t = lo + blockIdx.x * blockDim.x + threadIdx.x; t < hi; t += gridDim.x * blockDim.x) {
+        const int j = list[t];
         const WalkNode w = na.wn[j];
         double s = 0.0, sx = 0.0, sy = 0.0, sz = 0.0;
         int nc = 0;
@@ -797,10 +843,20 @@ void launch_moments(const uint64_t *keys, int n_nodes, int max_level, const D4 *
                     cudaStream_t s)
 {
     const int grid = grid_for(n_nodes, 256, kMaxGrid * 4);
-    link_leaves_kernel<<<grid, 256, 0, s>>>(keys, n_nodes, na, sbody64, box, G);
-    for (int lev = min(max_level, kMaxLevel) - 1; lev >= 0; --lev)
-        moments_level_kernel<<<grid, 256, 0, s>>>(lev, n_nodes, na, box, tab, G);
-    count_launches(1 + max(0, min(max_level, kMaxLevel)));
+    cudaMemsetAsync(na.level_count, 0, sizeof(unsigned) * kLevels, s);
+    link_leaves_kernel<<<grid, 256, 0, s>>>(keys, n_nodes, na, sbody64, box, G, na.level_count);
+    level_scan_kernel<<<1, 32, 0, s>>>(na.level_count, na.level_start, na.level_cursor);
+    level_scatter_kernel<<<grid, 256, 0, s>>>(n_nodes, na.kind, na.level_start, na.level_cursor,
+                                              na.level_list);
+    const int depth = min(max_level, kMaxLevel);
+    for (int lev = depth - 1; lev >= 0; --lev) {
+        // the node count of a level is only known on the device: a grid for the widest level
+        // (at most 8^lev cells) and a grid-stride loop over the level's list
+        const int64_t widest = lev < 10 ? ((int64_t)1 << (3 * lev)) : (int64_t)n_nodes;
+        const int g = grid_for(std::min<int64_t>(widest, n_nodes), 256, kMaxGrid * 2);
+        moments_level_kernel<<<g, 256, 0, s>>>(lev, na.level_start, na.level_list, na, box, tab, G);
+    }
+    count_launches(3 + max(0, depth));
 }
 
 }  // namespace nb

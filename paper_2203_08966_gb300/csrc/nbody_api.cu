@@ -38,6 +38,7 @@ struct nbody_ctx {
     int *err = nullptr;             // device error word
     uint32_t *h_word = nullptr;     // pinned host words: node count, deepest level
     unsigned *info = nullptr;       // device word: deepest node level of the last build
+    unsigned *levels = nullptr;     // per-level counters, offsets and cursors of the moments
 
     // octree
     NodeArrays na{};
@@ -117,6 +118,7 @@ void free_nodes(nbody_ctx *c)
     dfree(c->na.level);
     dfree(c->na.mask);
     dfree(c->na.kind);
+    dfree(c->na.level_list);
     c->na.cap = 0;
 }
 
@@ -130,6 +132,7 @@ nbody_status ensure_nodes(nbody_ctx *c, int64_t need)
     CK(dalloc(&c->na.level, cap));
     CK(dalloc(&c->na.mask, cap));
     CK(dalloc(&c->na.kind, cap));
+    CK(dalloc(&c->na.level_list, cap));
     c->na.cap = cap;
     return NBODY_OK;
 }
@@ -187,6 +190,9 @@ nbody_status build(nbody_ctx *c, const double *pos, const double *mass, int n,
         return fail(c, NBODY_ECUDA, "node count %lld out of range for n = %d", (long long)nn, n);
     CKS(ensure_nodes(c, nn));
     c->n_nodes = nn;
+    c->na.level_count = c->levels;
+    c->na.level_start = c->levels + kLevels;
+    c->na.level_cursor = c->levels + 2 * kLevels + 1;
     launch_emit_nodes(c->keys, n, c->node_off, c->na, s);
     launch_moments(c->keys, (int)nn, max_level, c->sbody64, c->box, c->tab, c->p.G, c->na, s);
     record(c, 3);
@@ -280,6 +286,7 @@ nbody_status nbody_create(nbody_ctx **out, int64_t n_capacity, const nbody_param
         CK(dalloc(&c->pp, cap));
         CK(dalloc(&c->pc, cap));
         CK(dalloc(&c->err, 1));
+        CK(dalloc(&c->levels, 3 * kLevels + 1));
         CK(cudaMemset(c->err, 0, sizeof(int)));
         CK(cudaMallocHost((void **)&c->h_word, 2 * sizeof(uint32_t)));
         CK(dalloc(&c->info, 1));
@@ -317,6 +324,7 @@ nbody_status nbody_destroy(nbody_ctx *c)
     dfree(c->pc);
     dfree(c->err);
     dfree(c->info);
+    dfree(c->levels);
     dfree(c->hpos);
     dfree(c->hvel);
     dfree(c->hmass);

@@ -100,6 +100,10 @@ struct NodeArrays {
     uint8_t *level;
     uint8_t *mask;
     uint8_t *kind;
+    int *level_list;          // internal cells grouped by level (cap entries)
+    unsigned *level_count;    // kLevels counters
+    unsigned *level_start;    // kLevels + 1 offsets into level_list
+    unsigned *level_cursor;   // kLevels scatter cursors
     int64_t cap;
 };
 void launch_emit_nodes(const uint64_t *keys, int n, const uint32_t *node_off, NodeArrays na,
