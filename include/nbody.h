@@ -50,7 +50,7 @@ typedef enum {
     NBODY_EINVAL = 1,    /* bad argument (null pointer, size, parameter) */
     NBODY_ENOMEM = 2,    /* device or host allocation failed */
     NBODY_ECUDA = 3,     /* a CUDA runtime call or kernel launch failed */
-    NBODY_ESTACK = 4,    /* reserved: a traversal exceeded its work bound */
+    NBODY_ESTACK = 4,    /* a traversal overran its node stack (reported by nbody_sync) */
     NBODY_ETIMEOUT = 5,  /* a bounded device-side wait gave up */
     NBODY_ESTATE = 6     /* call out of order (e.g. introspection before any build) */
 } nbody_status;
@@ -59,6 +59,10 @@ typedef enum {
     NBODY_FP64 = 0,        /* pair interactions, walk and accumulation in FP64 */
     NBODY_FP32 = 1,        /* FP32 pair interactions, MAC and accumulation */
     NBODY_FP32_KAHAN = 2   /* FP32 pair interactions with compensated (Kahan) accumulation */
+    /* FP64 sums each body's terms in the order of its own recursive walk.  The FP32 forms give
+     * every body the interaction list that the per-body FP32 acceptance test decides, but
+     * evaluate the walk for 32 Morton-consecutive bodies at a time and sum the terms in another
+     * order; their trees may hold at most 2^28 nodes (EINVAL beyond). */
 } nbody_precision;
 
 /* Physical and numerical parameters.  G: gravitational constant; eps: Plummer softening length

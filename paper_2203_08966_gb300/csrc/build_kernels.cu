@@ -654,6 +654,97 @@ __global__ void moments_level_kernel(int level, const unsigned *__restrict__ lev
 }
 
 // ------------------------------------------------------------------------------------------
+// Level-order copy of the tree for the group walk.  A stable partition of the pre-order nodes by
+// level: within a level the nodes keep their pre-order (Morton) order, so the children of a
+// cell, which are consecutive among the nodes of the next level, get consecutive indices.
+// ------------------------------------------------------------------------------------------
+
+constexpr int kLayThreads = 256;
+constexpr int kLayWarps = kLayThreads / 32;
+constexpr int kLayRounds = 16;
+constexpr int kLayTile = kLayThreads * kLayRounds;  // nodes per tile
+constexpr unsigned kNoLevel = 0xffu;
+
+// Per tile: the number of nodes of every level, stored level-major (counts[l * tiles + t]) so
+// that one exclusive scan gives every (level, tile) its first output index.
+__global__ void __launch_bounds__(kLayThreads) level_tile_count_kernel(
+    const uint8_t *__restrict__ level, int n_nodes, int tiles, uint32_t *counts)
+{
+    __shared__ unsigned h[kLevels];
+    if (threadIdx.x < kLevels) h[threadIdx.x] = 0;
+    __syncthreads();
+    const int base = blockIdx.x * kLayTile;
+    const int lane = threadIdx.x & 31;
+    for (int r = 0; r < kLayRounds; ++r) {
+        const int j = base + r * kLayThreads + threadIdx.x;
+        const unsigned l = j < n_nodes ? (unsigned)level[j] : kNoLevel;
+        const unsigned peers = __match_any_sync(kFull, l);
+        if (l < (unsigned)kLevels && lane == __ffs(peers) - 1) atomicAdd(&h[l], (unsigned)__popc(peers));
+    }
+    __syncthreads();
+    if (threadIdx.x < kLevels) counts[threadIdx.x * tiles + blockIdx.x] = h[threadIdx.x];
+}
+
+// Level-order index of every node: its (level, tile) offset plus its rank among the nodes of
+// the same level earlier in the tile.
+__global__ void __launch_bounds__(kLayThreads) level_tile_rank_kernel(
+    const uint8_t *__restrict__ level, int n_nodes, int tiles, const uint32_t *__restrict__ offs,
+    int *order)
+{
+    __shared__ unsigned run[kLevels];
+    __shared__ unsigned wc[kLayWarps][kLevels];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (threadIdx.x < kLevels) run[threadIdx.x] = offs[threadIdx.x * tiles + blockIdx.x];
+    const int base = blockIdx.x * kLayTile;
+    for (int r = 0; r < kLayRounds; ++r) {
+        if (threadIdx.x < kLayWarps * kLevels) (&wc[0][0])[threadIdx.x] = 0;
+        __syncthreads();
+        const int j = base + r * kLayThreads + threadIdx.x;
+        const unsigned l = j < n_nodes ? (unsigned)level[j] : kNoLevel;
+        const unsigned peers = __match_any_sync(kFull, l);
+        const unsigned rank = __popc(peers & ((1u << lane) - 1u));
+        if (l < (unsigned)kLevels && lane == __ffs(peers) - 1) wc[wid][l] = (unsigned)__popc(peers);
+        __syncthreads();
+        if (l < (unsigned)kLevels) {
+            unsigned o = run[l] + rank;
+            for (int w = 0; w < wid; ++w) o += wc[w][l];
+            order[j] = (int)o;
+        }
+        __syncthreads();
+        if (threadIdx.x < kLevels) {
+            unsigned t = 0;
+            for (int w = 0; w < kLayWarps; ++w) t += wc[w][threadIdx.x];
+            run[threadIdx.x] += t;
+        }
+        __syncthreads();
+    }
+}
+
+// GroupNode records at their level-order positions.  The first child of an internal cell is
+// the next node in pre-order; its children count is the population of the child mask.
+__global__ void group_nodes_kernel(int n_nodes, const WalkNode *__restrict__ wn,
+                                   const uint8_t *__restrict__ mask, const int *__restrict__ order,
+                                   GroupNode *gn)
+{
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n_nodes; j += gridDim.x * blockDim.x) {
+        const WalkNode w = wn[j];
+        GroupNode g;
+        g.c = w.c;
+        g.pre = j;
+        if (w.count != 0) {
+            g.child = w.first;
+            g.n = -w.count;
+            g.crit = 0.f;
+        } else {
+            g.child = order[j + 1];
+            g.n = __popc((unsigned)mask[j]);
+            g.crit = w.crit;
+        }
+        gn[order[j]] = g;
+    }
+}
+
+// ------------------------------------------------------------------------------------------
 // Generic exclusive scan of uint32 (reduce -> spine -> downsweep).
 // ------------------------------------------------------------------------------------------
 
@@ -857,6 +948,25 @@ void launch_moments(const uint64_t *keys, int n_nodes, int max_level, const D4 *
         moments_level_kernel<<<g, 256, 0, s>>>(lev, na.level_start, na.level_list, na, box, tab, G);
     }
     count_launches(3 + max(0, depth));
+}
+
+int layout_tiles(int64_t n_nodes) { return (int)((n_nodes + kLayTile - 1) / kLayTile); }
+int layout_scan_len(int64_t n_nodes) { return kLevels * layout_tiles(n_nodes); }
+
+void launch_level_order(const NodeArrays na, int n_nodes, const LayoutScratch &ls, GroupNode *gn,
+                        cudaStream_t s)
+{
+    const int tiles = layout_tiles(n_nodes);
+    const int len = kLevels * tiles;
+    level_tile_count_kernel<<<tiles, kLayThreads, 0, s>>>(na.level, n_nodes, tiles,
+                                                          ls.tile_offsets);
+    ScanScratch ss{ls.block_sums, scan_tiles(len)};
+    launch_exclusive_scan(ls.tile_offsets, ls.tile_offsets, len, ss, s);
+    level_tile_rank_kernel<<<tiles, kLayThreads, 0, s>>>(na.level, n_nodes, tiles,
+                                                         ls.tile_offsets, ls.order);
+    group_nodes_kernel<<<grid_for(n_nodes, 256, kMaxGrid * 4), 256, 0, s>>>(n_nodes, na.wn,
+                                                                           na.mask, ls.order, gn);
+    count_launches(3);
 }
 
 }  // namespace nb

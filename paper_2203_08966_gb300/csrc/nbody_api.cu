@@ -43,6 +43,9 @@ struct nbody_ctx {
     // octree
     NodeArrays na{};
     int64_t n_nodes = 0;
+    // level-order copy for the FP32 group walk (capacity na.cap)
+    GroupNode *gn = nullptr;
+    LayoutScratch ls{};
 
     // host-buffer stepping
     double *hpos = nullptr, *hvel = nullptr, *hmass = nullptr;
@@ -119,6 +122,10 @@ void free_nodes(nbody_ctx *c)
     dfree(c->na.mask);
     dfree(c->na.kind);
     dfree(c->na.level_list);
+    dfree(c->gn);
+    dfree(c->ls.tile_offsets);
+    dfree(c->ls.block_sums);
+    dfree(c->ls.order);
     c->na.cap = 0;
 }
 
@@ -133,6 +140,12 @@ nbody_status ensure_nodes(nbody_ctx *c, int64_t need)
     CK(dalloc(&c->na.mask, cap));
     CK(dalloc(&c->na.kind, cap));
     CK(dalloc(&c->na.level_list, cap));
+    CK(dalloc(&c->gn, cap));
+    CK(dalloc(&c->ls.order, cap));
+    const int len = layout_scan_len(cap);
+    CK(dalloc(&c->ls.tile_offsets, (size_t)len + 1));
+    CK(dalloc(&c->ls.block_sums, (size_t)scan_tiles(len) + 1));
+    c->ls.max_tiles = layout_tiles(cap);
     c->na.cap = cap;
     return NBODY_OK;
 }
@@ -188,6 +201,10 @@ nbody_status build(nbody_ctx *c, const double *pos, const double *mass, int n,
     const int max_level = (int)c->h_word[1];
     if (nn < 1 || nn > 22 * (int64_t)n)
         return fail(c, NBODY_ECUDA, "node count %lld out of range for n = %d", (long long)nn, n);
+    const bool group = c->p.precision != NBODY_FP64;
+    if (group && nn > (int64_t)kMaxGroupNodes)
+        return fail(c, NBODY_EINVAL, "%lld tree nodes: the FP32 walk indexes at most %lld",
+                    (long long)nn, (long long)kMaxGroupNodes);
     CKS(ensure_nodes(c, nn));
     c->n_nodes = nn;
     c->na.level_count = c->levels;
@@ -195,6 +212,7 @@ nbody_status build(nbody_ctx *c, const double *pos, const double *mass, int n,
     c->na.level_cursor = c->levels + 2 * kLevels + 1;
     launch_emit_nodes(c->keys, n, c->node_off, c->na, s);
     launch_moments(c->keys, (int)nn, max_level, c->sbody64, c->box, c->tab, c->p.G, c->na, s);
+    if (group) launch_level_order(c->na, (int)nn, c->ls, c->gn, s);
     record(c, 3);
     CKS(check_launch(c, "node split / moments"));
     c->n_built = n;
@@ -222,6 +240,8 @@ nbody_status walk(nbody_ctx *c, int n, double *acc, double *vel, double h)
     a.h = h;
     a.pp = c->pp;
     a.pc = c->pc;
+    a.gn = c->gn;
+    a.err = c->err;
     launch_walk(c->p.precision, a, c->stream);
     record(c, 4);
     CKS(check_launch(c, "walk"));
@@ -457,6 +477,7 @@ nbody_status nbody_sync(nbody_ctx *c)
     CK(cudaMemcpy(&e, c->err, sizeof(int), cudaMemcpyDeviceToHost));
     if (e & kErrTimeout) return fail(c, NBODY_ETIMEOUT, "a device-side wait gave up");
     if (e & kErrNodeCap) return fail(c, NBODY_ENOMEM, "node capacity exceeded on the device");
+    if (e & kErrStack) return fail(c, NBODY_ESTACK, "a group walk overran its node stack");
     return NBODY_OK;
 }
 

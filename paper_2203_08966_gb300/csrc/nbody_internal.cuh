@@ -41,7 +41,7 @@ struct Box {
 };
 
 // Device error word bits.
-enum : int { kErrNodeCap = 1, kErrTimeout = 2 };
+enum : int { kErrNodeCap = 1, kErrTimeout = 2, kErrStack = 4 };
 
 // Per-level tables written with the box.
 struct LevelTables {
@@ -113,6 +113,37 @@ void launch_moments(const uint64_t *keys, int n_nodes, int max_level, const D4 *
                     const Box *box, const LevelTables *tab, double G, NodeArrays na,
                     cudaStream_t s);
 
+// Level-order copy of the octree read by the FP32 group walk.  Nodes are ordered by level, and
+// within a level in pre-order (= Morton order), so the children of a cell are contiguous:
+// children of node b are child .. child + n - 1.
+//   c      as WalkNode::c
+//   child  internal: level-order index of the first child; leaf: sorted index of its first body
+//   n      internal: number of children (1..8); leaf: -(number of bodies)
+//   crit   internal: l^2 / theta^2 as FP32 (+inf when theta == 0); leaf: 0
+//   pre    pre-order index of the same node
+struct alignas(16) GroupNode {
+    float4 c;
+    int child;
+    int n;
+    float crit;
+    int pre;
+};
+
+// Node indices of the group walk's stack entries have 28 bits.
+constexpr int64_t kMaxGroupNodes = (int64_t)1 << 28;
+
+struct LayoutScratch {
+    uint32_t *tile_offsets;  // kLevels x tiles (+1), level-major
+    uint32_t *block_sums;    // scan scratch for the tile offsets
+    int *order;              // pre-order index -> level-order index
+    int max_tiles;
+};
+int layout_tiles(int64_t n_nodes);
+int layout_scan_len(int64_t n_nodes);
+// Stable partition of the nodes by level, then the GroupNode records.
+void launch_level_order(const NodeArrays na, int n_nodes, const LayoutScratch &ls,
+                        GroupNode *gn, cudaStream_t s);
+
 // ---------------------------------------------------------------- walk_kernels.cu
 struct WalkArgs {
     const WalkNode *wn;
@@ -129,6 +160,8 @@ struct WalkArgs {
     double *vel;          // 3n, user order, kicked by acc*h when non-null
     double h;
     uint32_t *pp, *pc;    // n, sorted order
+    const GroupNode *gn;  // level-order tree (FP32 walks)
+    int *err;             // device error word (kErrStack)
 };
 void launch_walk(int precision, const WalkArgs &a, cudaStream_t s);
 

@@ -1,14 +1,16 @@
 // Force kernels: the Barnes-Hut walk (Algorithm 2, "Compute Cell Force") and the direct sum
 // (Algorithm 1), both with the softened pair kernel of eq. `motion` (§2.1).
 //
-// Walk.  The nodes are stored in pre-order, each with `skip` = the index of the first node after
-// its subtree.  A body's recursive walk over the children of every opened cell then becomes a
-// monotone scan over node indices: at node j the body either opens j (next node j + 1, its first
-// child) or is done with j's subtree (next node skip[j]: a leaf, or a cell accepted by l/d <
-// theta).  One warp owns 32 Morton-consecutive bodies; every lane keeps its own `next`, and the
-// warp visits the minimum `next` over its lanes, so each lane sees exactly its own sequence of
-// nodes in its own order.  The per-body result (interaction list and summation order) is that of
-// the per-particle recursive walk; only lanes whose `next` equals the visited node do work there.
+// FP64 walk.  The nodes are stored in pre-order, each with `skip` = the index of the first node
+// after its subtree.  A body's recursive walk over the children of every opened cell then
+// becomes a monotone scan over node indices: at node j the body either opens j (next node j + 1,
+// its first child) or is done with j's subtree (next node skip[j]: a leaf, or a cell accepted by
+// l/d < theta).  One warp owns 32 Morton-consecutive bodies; every lane keeps its own `next`, and
+// the warp visits the minimum `next` over its lanes, so each lane sees exactly its own sequence
+// of nodes in its own order: interaction list and summation order are those of the per-particle
+// recursive walk.
+//
+// FP32 walk: the group walk below (same interaction lists, terms summed in another order).
 #include <math.h>
 
 #include "nbody_internal.cuh"
@@ -120,66 +122,342 @@ __device__ __forceinline__ void write_out(const WalkArgs &a, int i, double ax, d
     }
 }
 
-// FP32 walk.  MAC: accept a cell when d^2 > l^2 / theta^2 (the node's `crit`), i.e. l/d < theta.
-template <bool kKahan, bool kGuard>
-__global__ void __launch_bounds__(kWalkThreads) walk32_kernel(WalkArgs a)
+// ------------------------------------------------------------------------------------------
+// FP32 group walk.  One warp owns a group of 32 Morton-consecutive bodies and walks the
+// level-order tree for all of them at once, 32 nodes per step (one node per lane).  Each node is
+// tested against the group's bounding box first.  Per body the acceptance test is
+// d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) > crit with dx = c.x - x in FP32 (MAC l/d < theta of
+// §3, crit = l^2 / theta^2); every step of that expression is monotone in |dx|, |dy|, |dz|, so
+// the same expression over the per-axis distances from c to the box gives a lower bound of every
+// body's d2, and over the farthest box corner an upper bound.  Hence:
+//   lower bound > crit  -> every body of the group accepts the cell,
+//   upper bound <= crit -> every body opens it,
+// both exactly as the per-body test decides; only the cells in between ("mixed") are tested body
+// by body (one lane per body).  A node on the stack carries the mask of the bodies that opened
+// all its ancestors, so each body ends up with exactly the interaction list of its own walk
+// (Algorithm 2, "Compute Cell Force"): the same cells accepted, the same leaves, itself left
+// out.  Only the order of the terms differs.
+//
+// Interactions are collected per warp in shared memory, full-group ones (every live body of
+// the group) and partial ones (with a body mask), and evaluated in a dense loop with one lane per
+// body reading each source by broadcast.
+// ------------------------------------------------------------------------------------------
+
+constexpr int kGWarps = 4;
+constexpr int kGThreads = kGWarps * 32;
+// Stack of child ranges.  Every step pops <= 32 nodes and pushes <= 1 range per popped node, all
+// one level deeper than the shallowest popped node; so the ranges pushed by one step lie
+// strictly deeper than everything left below them, and at most 21 such groups (levels 1..21) of
+// <= 32 ranges are ever on the stack.
+constexpr int kStackCap = 22 * 32;
+constexpr int kFCap = 128;   // full-group interaction buffer
+constexpr int kPCap = 64;    // partial interaction buffer
+constexpr uint32_t kIdxMask = 0x0fffffffu;  // node index bits of a stack entry; 3 bits count - 1
+
+struct GroupSmem {
+    uint32_t st_node[kStackCap];  // first node | (count - 1) << 28
+    uint32_t st_mask[kStackCap];  // bodies of the group that still need these nodes
+    float4 f[kFCap];
+    float4 p[kPCap];
+    uint2 pm[kPCap];              // (body mask, 1 for a leaf body / 0 for a cell)
+};
+
+enum : int { kNone = 0, kFullLeaf, kFullCell, kPartLeaf, kPartCell, kOpen, kMixed, kBucket };
+
+__device__ __forceinline__ unsigned lanemask_lt_w()
 {
-    const int lane = threadIdx.x & 31;
-    const int warp = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
-    const int i = warp * 32 + lane;
-    if (warp * 32 >= a.n) return;  // whole warp out of range (uniform per warp)
-    const bool live = i < a.n;
-    const int n_nodes = a.n_nodes;
-    const float eps2 = (float)(a.eps * a.eps);
-    const float4 me = live ? ldg4(a.sbody32 + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+    unsigned r;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ float warp_fmin(float v)
+{
+    for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(kFull, v, o));
+    return v;
+}
+
+__device__ __forceinline__ float warp_fmax(float v)
+{
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(kFull, v, o));
+    return v;
+}
+
+// Distance along one axis from c to [lo, hi], as the per-body expression rounds it: the smallest
+// |c - x| (0 inside) and the largest.
+__device__ __forceinline__ void axis_bounds(float c, float lo, float hi, float &dmin, float &dmax)
+{
+    const float a = c - lo, b = c - hi;   // a >= b
+    dmin = b > 0.f ? b : (a < 0.f ? a : 0.f);
+    dmax = fmaxf(fabsf(a), fabsf(b));
+}
+
+template <bool kKahan, bool kGuard>
+struct GroupEval {
     Acc3<kKahan> acc;
-    uint32_t pp = 0, pc = 0;
-    // the root is never tested: a body starts at the root's first child (none when the root is a
-    // leaf, i.e. a single body)
-    int next = (!live || n_nodes < 2 || __ldg(&a.wn[0].count) != 0) ? n_nodes : 1;
-    unsigned it = 0;
-    for (;;) {
-        const int j = __reduce_min_sync(kFull, next);
-        if (j >= n_nodes) break;
-        if (kKahan && (++it % Acc3<kKahan>::kFold) == 0) acc.fold();
-        if (next != j) continue;
-        const float4 c = ldg4(&a.wn[j].c);
-        const int4 meta = __ldg(reinterpret_cast<const int4 *>(&a.wn[j].skip));
-        const int skip = meta.x, first = meta.y, count = meta.z;
-        const float crit = __int_as_float(meta.w);
-        float tx, ty, tz;
-        if (count == 1) {
-            if (first != i) {
-                pair32<kGuard>(c, me.x, me.y, me.z, eps2, tx, ty, tz);
-                acc.add(tx, ty, tz);
-                ++pp;
+    uint32_t pp = 0, pc = 0;      // partial-entry counts of this lane's body
+    __device__ __forceinline__ void full(const GroupSmem &S, int cnt, const float4 &me, float eps2)
+    {
+        __syncwarp();
+#pragma unroll 4
+        for (int e = 0; e < cnt; ++e) {
+            float tx, ty, tz;
+            pair32<kGuard>(S.f[e], me.x, me.y, me.z, eps2, tx, ty, tz);
+            acc.add(tx, ty, tz);
+        }
+        acc.fold();
+        __syncwarp();
+    }
+    __device__ __forceinline__ void part(const GroupSmem &S, int cnt, const float4 &me, float eps2,
+                                         int lane)
+    {
+        __syncwarp();
+#pragma unroll 2
+        for (int e = 0; e < cnt; ++e) {
+            float4 s = S.p[e];
+            const uint2 q = S.pm[e];
+            const uint32_t on = (q.x >> lane) & 1u;
+            const uint32_t leaf = q.y;
+            s.w = on ? s.w : 0.f;
+            float tx, ty, tz;
+            pair32<kGuard>(s, me.x, me.y, me.z, eps2, tx, ty, tz);
+            acc.add(tx, ty, tz);
+            pp += on & leaf;
+            pc += on & (leaf ^ 1u);
+        }
+        acc.fold();
+        __syncwarp();
+    }
+};
+
+template <bool kKahan, bool kGuard>
+__global__ void __launch_bounds__(kGThreads) group_walk32_kernel(WalkArgs a)
+{
+    __shared__ GroupSmem smem[kGWarps];
+    GroupSmem &S = smem[threadIdx.x >> 5];
+    const int lane = threadIdx.x & 31;
+    const int g0 = (blockIdx.x * kGWarps + (threadIdx.x >> 5)) * 32;
+    if (g0 >= a.n) return;  // uniform per warp
+    const int i = g0 + lane;
+    const bool live = i < a.n;
+    const unsigned lt = lanemask_lt_w();
+    const unsigned live_mask = __ballot_sync(kFull, live);
+    // lanes past the end stand on the last body so that they do not widen the group box
+    const float4 me = ldg4(a.sbody32 + min(i, a.n - 1));
+    const float lox = warp_fmin(me.x), loy = warp_fmin(me.y), loz = warp_fmin(me.z);
+    const float hix = warp_fmax(me.x), hiy = warp_fmax(me.y), hiz = warp_fmax(me.z);
+    const float eps2 = (float)(a.eps * a.eps);
+
+    GroupEval<kKahan, kGuard> ev;
+    uint32_t upp = 0, upc = 0;    // full-entry counts (the same for every live body)
+    int sp = 0, fn = 0, pn = 0;   // stack depth and buffer fills (warp-uniform)
+
+    // the root is never tested: the walk starts with the root's children (none when the root
+    // is a leaf, i.e. a single body)
+    if (a.n_nodes >= 2) {
+        const int4 r = __ldg(reinterpret_cast<const int4 *>(&a.gn[0].child));
+        if (r.y > 0) {
+            if (lane == 0) {
+                S.st_node[0] = (uint32_t)r.x | ((uint32_t)(r.y - 1) << 28);
+                S.st_mask[0] = live_mask;
             }
-            next = skip;
-        } else if (count > 1) {
-            const int end = min(first + count, a.n);
-            for (int b = first; b < end; ++b) {
-                if (b == i) continue;
-                pair32<kGuard>(ldg4(a.sbody32 + b), me.x, me.y, me.z, eps2, tx, ty, tz);
-                acc.add(tx, ty, tz);
-                ++pp;
-            }
-            next = skip;
+            sp = 1;
+        }
+    }
+
+    // appends the entries of the lanes whose kind says so to the two buffers
+    auto emit = [&](int kind, const float4 &c, unsigned m) {
+        const bool isf = kind == kFullLeaf || kind == kFullCell;
+        const unsigned fb = __ballot_sync(kFull, isf);
+        if (isf) S.f[fn + __popc(fb & lt)] = c;
+        fn += __popc(fb);
+        const unsigned fl = __ballot_sync(kFull, kind == kFullLeaf);
+        upp += __popc(fl);
+        upc += __popc(fb & ~fl);
+        const bool isp = kind == kPartLeaf || kind == kPartCell;
+        const unsigned pb = __ballot_sync(kFull, isp);
+        if (isp) {
+            const int o = pn + __popc(pb & lt);
+            S.p[o] = c;
+            S.pm[o] = make_uint2(m, kind == kPartLeaf ? 1u : 0u);
+        }
+        pn += __popc(pb);
+    };
+    auto flush = [&]() {
+        if (fn > kFCap - 32) {
+            ev.full(S, fn, me, eps2);
+            fn = 0;
+        }
+        if (pn > kPCap - 32) {
+            ev.part(S, pn, me, eps2, lane);
+            pn = 0;
+        }
+    };
+
+    // every node is popped at most once per group, so more steps than nodes means a malformed
+    // tree: stop with the error word set rather than loop
+    int steps_left = a.n_nodes;
+    while (sp > 0) {
+        flush();
+        if (sp > kStackCap - 32 || --steps_left < 0) {  // cannot happen (see kStackCap)
+            if (lane == 0) atomicOr(a.err, kErrStack);
+            break;
+        }
+        __syncwarp();
+        // ---- pop up to 32 nodes from the top ranges
+        const int ne = min(sp, 32);
+        uint32_t pk = 0, pmk = 0;
+        int cnt = 0;
+        if (lane < ne) {
+            pk = S.st_node[sp - 1 - lane];
+            pmk = S.st_mask[sp - 1 - lane];
+            cnt = (int)(pk >> 28) + 1;
+        }
+        int incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += t;
+        }
+        const int excl = incl - cnt;
+        const bool touched = lane < ne && excl < 32;
+        const int nt = __popc(__ballot_sync(kFull, touched));       // ranges touched: 0 .. nt-1
+        const int last_incl = __shfl_sync(kFull, incl, nt - 1);
+        const int last_excl = __shfl_sync(kFull, excl, nt - 1);
+        const uint32_t last_pk = __shfl_sync(kFull, pk, nt - 1);
+        const int items = min(last_incl, 32);
+        const unsigned starts = __reduce_or_sync(kFull, touched ? (1u << excl) : 0u);
+        const unsigned le = starts & (lane == 31 ? kFull : ((2u << lane) - 1u));
+        const int k = __popc(le) - 1;
+        const int off = lane - (31 - __clz(le));
+        const uint32_t ek = __shfl_sync(kFull, pk, k & 31);
+        const uint32_t em = __shfl_sync(kFull, pmk, k & 31);
+        __syncwarp();  // every popped entry is read before the stack is written again
+        if (last_incl > 32) {
+            // the deepest touched range is split: its first (32 - last_excl) nodes are taken
+            const int taken = 32 - last_excl;
+            sp -= nt - 1;
+            if (lane == 0)
+                S.st_node[sp - 1] = ((last_pk & kIdxMask) + (uint32_t)taken) |
+                                    ((uint32_t)((int)(last_pk >> 28) - taken) << 28);
         } else {
-            const float dx = c.x - me.x, dy = c.y - me.y, dz = c.z - me.z;
-            const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            if (d2 > crit) {
-                pair32<kGuard>(c, me.x, me.y, me.z, eps2, tx, ty, tz);
-                acc.add(tx, ty, tz);
-                ++pc;
-                next = skip;
+            sp -= nt;
+        }
+
+        // ---- classify the popped nodes, one per lane
+        const int node0 = (int)(ek & kIdxMask) + off;
+        const bool bad = lane < items && node0 >= a.n_nodes;
+        if (bad) atomicOr(a.err, kErrStack);
+        const bool has = lane < items && !bad;
+        const int node = has ? node0 : 0;
+        const unsigned m = has ? em : 0u;
+        float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
+        int4 meta = make_int4(0, 0, 0, 0);
+        if (has) {
+            c = ldg4(&a.gn[node].c);
+            meta = __ldg(reinterpret_cast<const int4 *>(&a.gn[node].child));
+        }
+        int kind = kNone;
+        unsigned mm = m;
+        if (has) {
+            if (meta.y < 0) {
+                if (meta.y == -1) {
+                    const unsigned d = (unsigned)(meta.x - g0);
+                    if (d < 32u) mm &= ~(1u << d);   // the body itself
+                    kind = mm == 0u ? kNone : (mm == live_mask ? kFullLeaf : kPartLeaf);
+                } else {
+                    kind = kBucket;
+                }
             } else {
-                next = j + 1;
+                const float crit = __int_as_float(meta.z);
+                float nx, ny, nz, fx, fy, fz;
+                axis_bounds(c.x, lox, hix, nx, fx);
+                axis_bounds(c.y, loy, hiy, ny, fy);
+                axis_bounds(c.z, loz, hiz, nz, fz);
+                const float dmin2 = fmaf(nx, nx, fmaf(ny, ny, nz * nz));
+                const float dmax2 = fmaf(fx, fx, fmaf(fy, fy, fz * fz));
+                if (dmin2 > crit) kind = m == live_mask ? kFullCell : kPartCell;
+                else if (dmax2 <= crit) kind = kOpen;
+                else kind = kMixed;
             }
         }
-        next = max(next, j + 1);  // progress even on a malformed skip
+        emit(kind, c, mm);
+        {
+            const bool iso = kind == kOpen;
+            const unsigned ob = __ballot_sync(kFull, iso);
+            if (iso) {
+                const int o = sp + __popc(ob & lt);
+                S.st_node[o] = (uint32_t)meta.x | ((uint32_t)(meta.y - 1) << 28);
+                S.st_mask[o] = m;
+            }
+            sp += __popc(ob);
+        }
+
+        // ---- mixed cells: every body tests its own acceptance
+        unsigned mx = __ballot_sync(kFull, kind == kMixed);
+        while (mx) {
+            const int src = __ffs(mx) - 1;
+            mx &= mx - 1u;
+            float4 sc;
+            sc.x = __shfl_sync(kFull, c.x, src);
+            sc.y = __shfl_sync(kFull, c.y, src);
+            sc.z = __shfl_sync(kFull, c.z, src);
+            sc.w = __shfl_sync(kFull, c.w, src);
+            const float crit = __int_as_float(__shfl_sync(kFull, meta.z, src));
+            const unsigned sm = __shfl_sync(kFull, m, src);
+            const float dx = sc.x - me.x, dy = sc.y - me.y, dz = sc.z - me.z;
+            const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            const unsigned A = __ballot_sync(kFull, d2 > crit) & sm;
+            const unsigned O = sm & ~A;
+            if (A) {
+                if (A == live_mask) {
+                    if (lane == 0) S.f[fn] = sc;
+                    ++fn;
+                    ++upc;
+                } else {
+                    if (lane == 0) {
+                        S.p[pn] = sc;
+                        S.pm[pn] = make_uint2(A, 0u);
+                    }
+                    ++pn;
+                }
+            }
+            if (O) {
+                const int cx = __shfl_sync(kFull, meta.x, src);
+                const int cn = __shfl_sync(kFull, meta.y, src);
+                if (lane == 0) {
+                    S.st_node[sp] = (uint32_t)cx | ((uint32_t)(cn - 1) << 28);
+                    S.st_mask[sp] = O;
+                }
+                ++sp;
+            }
+        }
+
+        // ---- level-21 buckets (rare): every member but the body itself, 32 members at a time
+        unsigned bk = __ballot_sync(kFull, kind == kBucket);
+        while (bk) {
+            const int src = __ffs(bk) - 1;
+            bk &= bk - 1u;
+            const int b0 = __shfl_sync(kFull, meta.x, src);
+            const int nb = -__shfl_sync(kFull, meta.y, src);
+            const unsigned sm = __shfl_sync(kFull, m, src);
+            for (int base = 0; base < nb; base += 32) {
+                flush();
+                const bool h = base + lane < nb;
+                const int b = min(b0 + base + lane, a.n - 1);
+                const float4 s = h ? ldg4(a.sbody32 + b) : make_float4(0.f, 0.f, 0.f, 0.f);
+                unsigned mb = sm;
+                const unsigned d = (unsigned)(b - g0);
+                if (d < 32u) mb &= ~(1u << d);
+                const int kb = (!h || mb == 0u) ? kNone : (mb == live_mask ? kFullLeaf : kPartLeaf);
+                emit(kb, s, mb);
+            }
+        }
     }
-    const float3 r = acc.result();
-    if (live) write_out(a, i, (double)r.x, (double)r.y, (double)r.z, pp, pc);
+    if (fn > 0) ev.full(S, fn, me, eps2);
+    if (pn > 0) ev.part(S, pn, me, eps2, lane);
+    const float3 r = ev.acc.result();
+    if (live) write_out(a, i, (double)r.x, (double)r.y, (double)r.z, ev.pp + upp, ev.pc + upc);
 }
 
 // FP64 walk, operation for operation the plain per-particle definition: the MAC is
@@ -347,17 +625,21 @@ __global__ void __launch_bounds__(kDirectThreads) direct64_kernel(
 void launch_walk(int precision, const WalkArgs &a, cudaStream_t s)
 {
     if (a.n <= 0) return;
-    const int64_t threads = ((int64_t)a.n + 31) / 32 * 32;
-    const int blocks = (int)((threads + kWalkThreads - 1) / kWalkThreads);
     const bool guard = !(a.eps > 0.0);
     if (precision == NBODY_FP64) {
+        const int64_t threads = ((int64_t)a.n + 31) / 32 * 32;
+        const int blocks = (int)((threads + kWalkThreads - 1) / kWalkThreads);
         walk64_kernel<<<blocks, kWalkThreads, 0, s>>>(a);
-    } else if (precision == NBODY_FP32_KAHAN) {
-        if (guard) walk32_kernel<true, true><<<blocks, kWalkThreads, 0, s>>>(a);
-        else walk32_kernel<true, false><<<blocks, kWalkThreads, 0, s>>>(a);
     } else {
-        if (guard) walk32_kernel<false, true><<<blocks, kWalkThreads, 0, s>>>(a);
-        else walk32_kernel<false, false><<<blocks, kWalkThreads, 0, s>>>(a);
+        const int64_t groups = ((int64_t)a.n + 31) / 32;
+        const int blocks = (int)((groups + kGWarps - 1) / kGWarps);
+        if (precision == NBODY_FP32_KAHAN) {
+            if (guard) group_walk32_kernel<true, true><<<blocks, kGThreads, 0, s>>>(a);
+            else group_walk32_kernel<true, false><<<blocks, kGThreads, 0, s>>>(a);
+        } else {
+            if (guard) group_walk32_kernel<false, true><<<blocks, kGThreads, 0, s>>>(a);
+            else group_walk32_kernel<false, false><<<blocks, kGThreads, 0, s>>>(a);
+        }
     }
     count_launches(1);
 }

@@ -110,6 +110,7 @@ def test_fp32_forces_within_tolerance(name, prec):
     ref, rpp, rpc = oracle.bh(pos, mass, 1.0, eps, theta)
     with nb.Context(n, 1.0, eps, theta, 1e-3, prec) as ctx:
         a = ctx.forces(dev(pos), dev(mass)).cpu().numpy()
+        ctx.sync()  # the walk's device error word is clear
         pp, pc = ctx.counters(n)
     assert np.isfinite(a).all()
     if name == "colinear_257":
