@@ -150,7 +150,7 @@ constexpr int kGThreads = kGWarps * 32;
 // strictly deeper than everything left below them, and at most 21 such groups (levels 1..21) of
 // <= 32 ranges are ever on the stack.
 constexpr int kStackCap = 22 * 32;
-constexpr int kFCap = 128;   // full-group interaction buffer
+constexpr int kFCap = 64;    // full-group interaction buffer
 constexpr int kPCap = 64;    // partial interaction buffer
 constexpr uint32_t kIdxMask = 0x0fffffffu;  // node index bits of a stack entry; 3 bits count - 1
 
@@ -195,38 +195,42 @@ __device__ __forceinline__ void axis_bounds(float c, float lo, float hi, float &
 template <bool kKahan, bool kGuard>
 struct GroupEval {
     Acc3<kKahan> acc;
-    uint32_t pp = 0, pc = 0;      // partial-entry counts of this lane's body
+    uint32_t pp = 0, pc = 0;      // partial entries of this lane's body: leaves, all
+    int terms = 0;                // terms in the current partial (warp-uniform)
+    __device__ __forceinline__ void settle(int cnt)
+    {
+        terms += cnt;
+        if (terms >= Acc3<kKahan>::kFold) {
+            acc.fold();
+            terms = 0;
+        }
+    }
     __device__ __forceinline__ void full(const GroupSmem &S, int cnt, const float4 &me, float eps2)
     {
-        __syncwarp();
 #pragma unroll 4
         for (int e = 0; e < cnt; ++e) {
             float tx, ty, tz;
             pair32<kGuard>(S.f[e], me.x, me.y, me.z, eps2, tx, ty, tz);
             acc.add(tx, ty, tz);
         }
-        acc.fold();
-        __syncwarp();
+        settle(cnt);
     }
     __device__ __forceinline__ void part(const GroupSmem &S, int cnt, const float4 &me, float eps2,
                                          int lane)
     {
-        __syncwarp();
 #pragma unroll 2
         for (int e = 0; e < cnt; ++e) {
             float4 s = S.p[e];
             const uint2 q = S.pm[e];
             const uint32_t on = (q.x >> lane) & 1u;
-            const uint32_t leaf = q.y;
             s.w = on ? s.w : 0.f;
             float tx, ty, tz;
             pair32<kGuard>(s, me.x, me.y, me.z, eps2, tx, ty, tz);
             acc.add(tx, ty, tz);
-            pp += on & leaf;
-            pc += on & (leaf ^ 1u);
+            pp += on & q.y;   // leaf bodies
+            pc += on;         // all partial entries; the cells are pc - pp
         }
-        acc.fold();
-        __syncwarp();
+        settle(cnt);
     }
 };
 
@@ -265,7 +269,7 @@ __global__ void __launch_bounds__(kGThreads) group_walk32_kernel(WalkArgs a)
         }
     }
 
-    // appends the entries of the lanes whose kind says so to the two buffers
+    // appends one entry per lane whose kind says so: full-group entries to f, others to p
     auto emit = [&](int kind, const float4 &c, unsigned m) {
         const bool isf = kind == kFullLeaf || kind == kFullCell;
         const unsigned fb = __ballot_sync(kFull, isf);
@@ -283,49 +287,45 @@ __global__ void __launch_bounds__(kGThreads) group_walk32_kernel(WalkArgs a)
         }
         pn += __popc(pb);
     };
-    auto flush = [&]() {
-        if (fn > kFCap - 32) {
-            ev.full(S, fn, me, eps2);
-            fn = 0;
-        }
-        if (pn > kPCap - 32) {
-            ev.part(S, pn, me, eps2, lane);
-            pn = 0;
-        }
+    // evaluates and empties both buffers
+    auto drain = [&]() {
+        __syncwarp();
+        if (fn > 0) ev.full(S, fn, me, eps2);
+        if (pn > 0) ev.part(S, pn, me, eps2, lane);
+        fn = pn = 0;
+        __syncwarp();
     };
 
     // every node is popped at most once per group, so more steps than nodes means a malformed
     // tree: stop with the error word set rather than loop
     int steps_left = a.n_nodes;
     while (sp > 0) {
-        flush();
         if (sp > kStackCap - 32 || --steps_left < 0) {  // cannot happen (see kStackCap)
             if (lane == 0) atomicOr(a.err, kErrStack);
             break;
         }
         __syncwarp();
-        // ---- pop up to 32 nodes from the top ranges
+        // ---- pop up to 32 nodes from the top ranges (lane k reads the k-th range from the top)
         const int ne = min(sp, 32);
         uint32_t pk = 0, pmk = 0;
-        int cnt = 0;
+        unsigned cnt = 0;
         if (lane < ne) {
             pk = S.st_node[sp - 1 - lane];
             pmk = S.st_mask[sp - 1 - lane];
-            cnt = (int)(pk >> 28) + 1;
+            cnt = (pk >> 28) + 1u;
         }
-        int incl = cnt;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int t = __shfl_up_sync(kFull, incl, o);
-            if (lane >= o) incl += t;
-        }
-        const int excl = incl - cnt;
+        // exclusive prefix sum of the range sizes (1..8) from their bits, one ballot per bit
+        const unsigned b0 = __ballot_sync(kFull, cnt & 1u), b1 = __ballot_sync(kFull, cnt & 2u);
+        const unsigned b2 = __ballot_sync(kFull, cnt & 4u), b3 = __ballot_sync(kFull, cnt & 8u);
+        const int excl = __popc(b0 & lt) + 2 * __popc(b1 & lt) + 4 * __popc(b2 & lt) +
+                         8 * __popc(b3 & lt);
+        const int total = __popc(b0) + 2 * __popc(b1) + 4 * __popc(b2) + 8 * __popc(b3);
         const bool touched = lane < ne && excl < 32;
         const int nt = __popc(__ballot_sync(kFull, touched));       // ranges touched: 0 .. nt-1
-        const int last_incl = __shfl_sync(kFull, incl, nt - 1);
         const int last_excl = __shfl_sync(kFull, excl, nt - 1);
         const uint32_t last_pk = __shfl_sync(kFull, pk, nt - 1);
-        const int items = min(last_incl, 32);
+        const int last_incl = last_excl + (int)(last_pk >> 28) + 1;
+        const int items = min(total, 32);
         const unsigned starts = __reduce_or_sync(kFull, touched ? (1u << excl) : 0u);
         const unsigned le = starts & (lane == 31 ? kFull : ((2u << lane) - 1u));
         const int k = __popc(le) - 1;
@@ -344,7 +344,7 @@ __global__ void __launch_bounds__(kGThreads) group_walk32_kernel(WalkArgs a)
             sp -= nt;
         }
 
-        // ---- classify the popped nodes, one per lane
+        // ---- load the popped nodes (one per lane)
         const int node0 = (int)(ek & kIdxMask) + off;
         const bool bad = lane < items && node0 >= a.n_nodes;
         if (bad) atomicOr(a.err, kErrStack);
@@ -357,14 +357,19 @@ __global__ void __launch_bounds__(kGThreads) group_walk32_kernel(WalkArgs a)
             c = ldg4(&a.gn[node].c);
             meta = __ldg(reinterpret_cast<const int4 *>(&a.gn[node].child));
         }
+
+        // ---- while the loads are in flight: evaluate what the previous step buffered
+        drain();
+
+        // ---- classify
         int kind = kNone;
-        unsigned mm = m;
+        unsigned emask = m;     // bodies that take this node's entry
         if (has) {
             if (meta.y < 0) {
                 if (meta.y == -1) {
                     const unsigned d = (unsigned)(meta.x - g0);
-                    if (d < 32u) mm &= ~(1u << d);   // the body itself
-                    kind = mm == 0u ? kNone : (mm == live_mask ? kFullLeaf : kPartLeaf);
+                    if (d < 32u) emask &= ~(1u << d);   // the body itself
+                    kind = emask == 0u ? kNone : (emask == live_mask ? kFullLeaf : kPartLeaf);
                 } else {
                     kind = kBucket;
                 }
@@ -381,56 +386,47 @@ __global__ void __launch_bounds__(kGThreads) group_walk32_kernel(WalkArgs a)
                 else kind = kMixed;
             }
         }
-        emit(kind, c, mm);
-        {
-            const bool iso = kind == kOpen;
-            const unsigned ob = __ballot_sync(kFull, iso);
-            if (iso) {
-                const int o = sp + __popc(ob & lt);
-                S.st_node[o] = (uint32_t)meta.x | ((uint32_t)(meta.y - 1) << 28);
-                S.st_mask[o] = m;
-            }
-            sp += __popc(ob);
+
+        // ---- mixed cells: every body tests its own acceptance, two cells per pass
+        unsigned mx = __ballot_sync(kFull, kind == kMixed);
+        unsigned myA = 0u;
+        const float crit_l = __int_as_float(meta.z);
+        while (mx) {
+            const int s1 = __ffs(mx) - 1;
+            mx &= mx - 1u;
+            const int s2 = mx ? __ffs(mx) - 1 : s1;
+            mx &= mx - 1u;
+            const float x1 = __shfl_sync(kFull, c.x, s1), x2 = __shfl_sync(kFull, c.x, s2);
+            const float y1 = __shfl_sync(kFull, c.y, s1), y2 = __shfl_sync(kFull, c.y, s2);
+            const float z1 = __shfl_sync(kFull, c.z, s1), z2 = __shfl_sync(kFull, c.z, s2);
+            const float k1 = __shfl_sync(kFull, crit_l, s1), k2 = __shfl_sync(kFull, crit_l, s2);
+            const float dx1 = x1 - me.x, dy1 = y1 - me.y, dz1 = z1 - me.z;
+            const float dx2 = x2 - me.x, dy2 = y2 - me.y, dz2 = z2 - me.z;
+            const float q1 = fmaf(dx1, dx1, fmaf(dy1, dy1, dz1 * dz1));
+            const float q2 = fmaf(dx2, dx2, fmaf(dy2, dy2, dz2 * dz2));
+            const unsigned A1 = __ballot_sync(kFull, q1 > k1);
+            const unsigned A2 = __ballot_sync(kFull, q2 > k2);
+            if (lane == s1) myA = A1;
+            if (lane == s2) myA = A2;
+        }
+        unsigned pmask = kind == kOpen ? m : 0u;   // bodies that need this cell's children
+        if (kind == kMixed) {
+            emask = myA & m;
+            pmask = m & ~emask;
+            kind = emask == 0u ? kNone : (emask == live_mask ? kFullCell : kPartCell);
         }
 
-        // ---- mixed cells: every body tests its own acceptance
-        unsigned mx = __ballot_sync(kFull, kind == kMixed);
-        while (mx) {
-            const int src = __ffs(mx) - 1;
-            mx &= mx - 1u;
-            float4 sc;
-            sc.x = __shfl_sync(kFull, c.x, src);
-            sc.y = __shfl_sync(kFull, c.y, src);
-            sc.z = __shfl_sync(kFull, c.z, src);
-            sc.w = __shfl_sync(kFull, c.w, src);
-            const float crit = __int_as_float(__shfl_sync(kFull, meta.z, src));
-            const unsigned sm = __shfl_sync(kFull, m, src);
-            const float dx = sc.x - me.x, dy = sc.y - me.y, dz = sc.z - me.z;
-            const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            const unsigned A = __ballot_sync(kFull, d2 > crit) & sm;
-            const unsigned O = sm & ~A;
-            if (A) {
-                if (A == live_mask) {
-                    if (lane == 0) S.f[fn] = sc;
-                    ++fn;
-                    ++upc;
-                } else {
-                    if (lane == 0) {
-                        S.p[pn] = sc;
-                        S.pm[pn] = make_uint2(A, 0u);
-                    }
-                    ++pn;
-                }
+        // ---- buffer the entries, push the children
+        emit(kind, c, emask);
+        {
+            const bool isp = pmask != 0u;
+            const unsigned ob = __ballot_sync(kFull, isp);
+            if (isp) {
+                const int o = sp + __popc(ob & lt);
+                S.st_node[o] = (uint32_t)meta.x | ((uint32_t)(meta.y - 1) << 28);
+                S.st_mask[o] = pmask;
             }
-            if (O) {
-                const int cx = __shfl_sync(kFull, meta.x, src);
-                const int cn = __shfl_sync(kFull, meta.y, src);
-                if (lane == 0) {
-                    S.st_node[sp] = (uint32_t)cx | ((uint32_t)(cn - 1) << 28);
-                    S.st_mask[sp] = O;
-                }
-                ++sp;
-            }
+            sp += __popc(ob);
         }
 
         // ---- level-21 buckets (rare): every member but the body itself, 32 members at a time
@@ -438,13 +434,13 @@ __global__ void __launch_bounds__(kGThreads) group_walk32_kernel(WalkArgs a)
         while (bk) {
             const int src = __ffs(bk) - 1;
             bk &= bk - 1u;
-            const int b0 = __shfl_sync(kFull, meta.x, src);
+            const int b0i = __shfl_sync(kFull, meta.x, src);
             const int nb = -__shfl_sync(kFull, meta.y, src);
             const unsigned sm = __shfl_sync(kFull, m, src);
             for (int base = 0; base < nb; base += 32) {
-                flush();
+                if (fn > kFCap - 32 || pn > kPCap - 32) drain();
                 const bool h = base + lane < nb;
-                const int b = min(b0 + base + lane, a.n - 1);
+                const int b = min(b0i + base + lane, a.n - 1);
                 const float4 s = h ? ldg4(a.sbody32 + b) : make_float4(0.f, 0.f, 0.f, 0.f);
                 unsigned mb = sm;
                 const unsigned d = (unsigned)(b - g0);
@@ -454,10 +450,9 @@ __global__ void __launch_bounds__(kGThreads) group_walk32_kernel(WalkArgs a)
             }
         }
     }
-    if (fn > 0) ev.full(S, fn, me, eps2);
-    if (pn > 0) ev.part(S, pn, me, eps2, lane);
+    drain();
     const float3 r = ev.acc.result();
-    if (live) write_out(a, i, (double)r.x, (double)r.y, (double)r.z, ev.pp + upp, ev.pc + upc);
+    if (live) write_out(a, i, (double)r.x, (double)r.y, (double)r.z, ev.pp + upp, ev.pc - ev.pp + upc);
 }
 
 // FP64 walk, operation for operation the plain per-particle definition: the MAC is
