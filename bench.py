@@ -39,7 +39,8 @@ METRIC = "Barnes-Hut bodies/s per step at N=16M theta=0.5"
 FLOP_PER_INTERACTION = 20          # softened monopole pair term, counting rsqrt as 2 flops
 FP32_LANES_PER_SM = 128            # FP32 FMA lanes per SM (Blackwell)
 CPU_SAMPLE_N = 1 << 20             # bodies in the CPU-baseline sample
-REF_SAMPLE_N = 1 << 19             # bodies per step of the reference arm
+CPU_SAMPLE_STEPS = 3               # timed oracle steps on that sample (about 10-15 s on 16 cores)
+REF_SAMPLE_N = 1 << 20             # bodies per step of the reference arm
 
 
 def parse():
@@ -54,6 +55,8 @@ def parse():
     ap.add_argument("--theta", type=float, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 512-system forest line")
+    ap.add_argument("--no-accuracy", action="store_true", help="skip the per-theta error report")
     return ap.parse_args()
 
 
@@ -196,6 +199,126 @@ def run_reference(args):
 
 # ------------------------------------------------------------------ GPU arm
 
+def measure_batch(nb, torch, dev, stream, steps=100):
+    """The batched forest (512 Plummer systems, N_s log-uniform in [1024, 65536], eps 0.01,
+    theta 0.6, dt 1e-3, FP32-Kahan forces): `steps` leapfrog steps replayed from one captured
+    CUDA graph, timed with CUDA events on the context stream; plus the same steps launched
+    kernel by kernel for comparison."""
+    w = ics.WORKLOADS["forest_512"]
+    pos, vel, mass, off = ics.forest(w["systems"], w["seed"])
+    n = int(off[-1])
+    tp = torch.from_numpy(pos).to(dev)
+    tv = torch.from_numpy(vel).to(dev)
+    tm = torch.from_numpy(mass).to(dev)
+    ctx = nb.Context.forest(off, 1.0, w["eps"], w["theta"], w["dt"], nb.FP32_KAHAN, stream=stream)
+    ctx.forest_step(tp, tv, tm, 4, use_graph=True)     # a^(0), capture, warm-up replays
+    ctx.forest_step(tp, tv, tm, 3, use_graph=False)    # warm-up of the launched form
+    ctx.sync()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    l0 = nb.launch_count()
+    ev[0].record(stream)
+    ctx.forest_step(tp, tv, tm, steps, use_graph=True)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    launches = nb.launch_count() - l0
+    k = max(1, steps // 10)
+    ev[2].record(stream)
+    ctx.forest_step(tp, tv, tm, k, use_graph=False)
+    ev[3].record(stream)
+    torch.cuda.synchronize()
+    ctx.sync()
+    ctx.close()
+    ms = ev[0].elapsed_time(ev[1])
+    ms_launched = ev[2].elapsed_time(ev[3]) / k
+    return {"metric": "batch steps/s", "value": steps / (ms * 1e-3), "unit": "steps/s",
+            "workload": "forest_512", "systems": int(w["systems"]), "bodies": n,
+            "bodies_per_s": n * steps / (ms * 1e-3), "ms_per_step": ms / steps,
+            "ms_per_step_launched": ms_launched, "steps": steps, "graph": True,
+            "gpu_launches": int(launches), "precision": "fp32_kahan",
+            "theta": w["theta"], "eps": w["eps"], "dt": w["dt"]}
+
+
+def measure_accuracy(nb, torch, dev, stream, n_targets=16384):
+    """Force errors on the 1,048,576-body Plummer sphere (eps 0.005) against the FP64 direct
+    sum on 16,384 sampled targets, per theta, for the plain FP64 path and the FP32-Kahan path,
+    with the walk time of each on this GPU."""
+    w = ics.WORKLOADS["plummer_1m"]
+    pos, _, mass = ics.plummer(w["n"], w["seed"])
+    n = w["n"]
+    tp = torch.from_numpy(pos).to(dev)
+    tm = torch.from_numpy(mass).to(dev)
+    rng = np.random.Generator(np.random.PCG64(3))
+    tgt = np.sort(rng.choice(n, n_targets, replace=False)).astype(np.int64)
+    tt = torch.from_numpy(tgt).to(dev)
+
+    def rel(a, ref):
+        num = ((a - ref) ** 2).sum(axis=0)
+        den = (ref ** 2).sum(axis=0)
+        return {"rms": float(np.sqrt(np.mean(num / den))),
+                "global": float(np.sqrt(num.sum() / den.sum())),
+                "p99": float(np.sqrt(np.quantile(num / den, 0.99)))}
+
+    out = {"workload": "plummer_1m", "n": n, "eps": w["eps"], "targets": n_targets,
+           "reference": "FP64 direct sum (nbody_direct_forces) on the sampled targets",
+           "theta": {}}
+    with nb.Context(n, 1.0, w["eps"], 0.5, w["dt"], nb.FP64, stream=stream) as ctx:
+        direct = ctx.direct_forces(tp, tm, tt).cpu().numpy()
+    for theta in (0.3, 0.5, 0.7):
+        row = {}
+        res = {}
+        for name, prec in (("fp64", nb.FP64), ("fp32_kahan", nb.FP32_KAHAN)):
+            with nb.Context(n, 1.0, w["eps"], theta, w["dt"], prec, stream=stream) as ctx:
+                ctx.enable_timing(True)
+                a = ctx.forces(tp, tm)
+                t = ctx.timings()
+                a = a.cpu().numpy()
+                pp, pc = ctx.counters(n)
+            res[name] = a
+            row[name] = {"vs_direct": rel(a[:, tgt], direct), "walk_ms": float(t[3]),
+                         "interactions_per_body": float((pp.astype(np.float64).sum() +
+                                                         pc.astype(np.float64).sum()) / n)}
+        row["fp32_kahan_vs_fp64_bh"] = rel(res["fp32_kahan"], res["fp64"])
+        out["theta"][str(theta)] = row
+    return out
+
+
+WALK_SOURCES = ("paper_2203_08966_gb300/csrc/walk_kernels.cu",
+                "paper_2203_08966_gb300/csrc/nbody_internal.cuh")
+WALK_PROFILE = "profiles/group_walk32_two_plummer_16m.md"
+
+
+def walk_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for rel in WALK_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def committed_traffic():
+    """DRAM bytes per walk launch (dram__bytes_read.sum + dram__bytes_write.sum) from the
+    committed ncu summary of the benchmark workload, or None when that summary is missing or
+    was taken on other walk sources than the ones built now."""
+    try:
+        with open(os.path.join(ROOT, WALK_PROFILE)) as f:
+            text = f.read()
+    except OSError:
+        return None
+    vals = {}
+    for line in text.splitlines():
+        line = line.strip().strip("`")
+        for key in ("traffic_bytes_per_launch:", "walk_sources_sha256:"):
+            if line.startswith(key):
+                vals[key] = line[len(key):].strip()
+    if vals.get("walk_sources_sha256:") != walk_source_hash():
+        return None
+    try:
+        return float(vals["traffic_bytes_per_launch:"])
+    except (KeyError, ValueError):
+        return None
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -276,6 +399,13 @@ def run_ours(args):
     peak_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     peak_tf = sms * FP32_LANES_PER_SM * 2 * peak_mhz * 1e6 / 1e12
 
+    batch = None
+    accuracy = None
+    if ws == 1 and not args.no_batch:
+        batch = measure_batch(nb, torch, dev, stream)
+    if ws == 1 and not args.no_accuracy:
+        accuracy = measure_accuracy(nb, torch, dev, stream)
+
     # end to end through the host-buffer entry point: pinned inputs copied in, result read back
     e2e = None
     if not args.no_e2e:
@@ -308,10 +438,10 @@ def run_ours(args):
 
     cpu = None
     if not args.no_cpu_baseline and ws == 1:
-        rate, secs, cores = oracle_step_rate(args.workload, w, CPU_SAMPLE_N)
+        rate, secs, cores = oracle_step_rate(args.workload, w, CPU_SAMPLE_N, CPU_SAMPLE_STEPS)
         cpu = {"value": rate, "unit": "bodies/s", "cores": cores, "kind": "oracle",
-               "sample": f"one KDK step of the FP64 CPU oracle on {CPU_SAMPLE_N} bodies drawn "
-                         f"with the same recipe ({secs:.1f} s)"}
+               "sample": f"{CPU_SAMPLE_STEPS} KDK steps of the FP64 CPU oracle on {CPU_SAMPLE_N} "
+                         f"bodies drawn with the same recipe ({secs:.1f} s)"}
 
     line = {
         "metric": METRIC, "value": value, "unit": "bodies/s", "n_gpus": ws,
@@ -330,7 +460,11 @@ def run_ours(args):
         "roofline": {"kernel": "walk32 (Kahan)" if args.precision == "fp32_kahan" else
                      ("walk32" if args.precision == "fp32" else "walk64"),
                      "bound": "alu", "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
-                     "frac": achieved / peak_tf, "traffic": None,
+                     "frac": achieved / peak_tf,
+                     "traffic": committed_traffic() if args.precision == "fp32_kahan" and
+                     args.workload == "two_plummer_16m" and not args.n else None,
+                     "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + "
+                                     "dram__bytes_write.sum)",
                      "peak_source": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x "
                                     f"{peak_mhz:.0f} MHz ({peak_src} max SM clock)",
                      "walk_ms": walk_avg},
@@ -338,6 +472,8 @@ def run_ours(args):
         "gpu_launches": int(launches),
         "e2e": e2e,
         "cpu_baseline": cpu,
+        "batch": batch,
+        "accuracy": accuracy,
     }
     print(json.dumps(line), flush=True)
     if ws > 1:

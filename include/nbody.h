@@ -174,6 +174,38 @@ nbody_status nbody_get_timings(nbody_ctx *c, float *h_ms5);
  * can count the launches inside a timed region.  Errors: EINVAL when out == NULL. */
 nbody_status nbody_get_launch_count(int64_t *out);
 
+/* ---- forest: many independent systems advanced together ---- */
+
+/* Creates a context for n_systems independent systems packed into one set of arrays: system k
+ * owns bodies h_offsets[k] .. h_offsets[k+1] - 1 of every SoA row (h_offsets: HOST array of
+ * n_systems + 1 entries, h_offsets[0] == 0, non-decreasing; empty systems are allowed).  Bodies
+ * of different systems never interact; each system gets its own root box, octree and walk
+ * (§3, Algorithm 2), with the shared parameters p.  All systems are handled by the same kernel
+ * launches, and a step synchronises nothing on the host, so it can be replayed as a CUDA graph.
+ * The node arrays are sized here for 4 nodes per body plus 22 per system; a step whose trees
+ * need more reports ENOMEM at the next nbody_sync.  Errors: EINVAL (bad offsets, n_systems
+ * outside 1..65535, total bodies outside 1..2^30, bad params), ENOMEM, ECUDA.  Destroy with
+ * nbody_destroy.  The single-system entry points (build_tree, forces, step, step_host,
+ * direct_forces, get_tree, get_moments) return ESTATE on a forest context. */
+nbody_status nbody_forest_create(nbody_ctx **out, int32_t n_systems, const int64_t *h_offsets,
+                                 const nbody_params *p, void *cuda_stream);
+
+/* Barnes-Hut accelerations of every system (d_pos 3N, d_mass N, d_acc 3N doubles, device, user
+ * order, N = h_offsets[n_systems]).  Per-body counters and sorted keys are available through
+ * nbody_get_counters / nbody_get_keys (keys sorted by system, then key, then index). */
+nbody_status nbody_forest_forces(nbody_ctx *c, const double *d_pos, const double *d_mass,
+                                 double *d_acc);
+
+/* nsteps kick-drift-kick steps of every system (§2.4), in place on d_pos / d_vel.  The first
+ * call (and the first after nbody_set_params) computes the starting accelerations.  use_graph:
+ * 0 launches every kernel of every step; 1 captures one step as a CUDA graph on a stream the
+ * context owns (again whenever d_pos, d_vel or d_mass differ from the captured ones, or after
+ * nbody_set_params) and replays it nsteps times, ordered after the work already on the
+ * context stream, with the context stream waiting for the replays.  Timing events are not
+ * recorded by replayed steps. */
+nbody_status nbody_forest_step(nbody_ctx *c, double *d_pos, double *d_vel, const double *d_mass,
+                               int32_t nsteps, int32_t use_graph);
+
 /* ---- allocation-free keys + sort ---- */
 
 /* Largest n accepted by nbody_sort_keys_noalloc. */

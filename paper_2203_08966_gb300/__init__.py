@@ -30,7 +30,8 @@ EXPORTS = ("nbody_create", "nbody_destroy", "nbody_set_params", "nbody_build_tre
            "nbody_forces", "nbody_step", "nbody_step_host", "nbody_direct_forces", "nbody_sync",
            "nbody_get_keys", "nbody_get_box", "nbody_get_tree", "nbody_get_moments",
            "nbody_get_counters", "nbody_enable_timing", "nbody_get_timings",
-           "nbody_last_error", "nbody_get_launch_count", "nbody_sort_keys_noalloc")
+           "nbody_last_error", "nbody_get_launch_count", "nbody_sort_keys_noalloc",
+           "nbody_forest_create", "nbody_forest_forces", "nbody_forest_step")
 
 
 class NBodyError(RuntimeError):
@@ -87,6 +88,9 @@ def load_library(path: str = LIB_PATH):
         "nbody_last_error": [vp, ctypes.c_char_p, i64],
         "nbody_get_launch_count": [ctypes.POINTER(i64)],
         "nbody_sort_keys_noalloc": [vp, vp, i64, vp, vp, vp],
+        "nbody_forest_create": [ctypes.POINTER(vp), i32, vp, P, vp],
+        "nbody_forest_forces": [vp, vp, vp, vp],
+        "nbody_forest_step": [vp, vp, vp, vp, i32, i32],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -125,7 +129,7 @@ class Context:
     ``stream``, a torch.cuda.Stream)."""
 
     def __init__(self, capacity, G=1.0, eps=0.0, theta=0.5, dt=1e-3, precision=FP32,
-                 stream=None):
+                 stream=None, offsets=None):
         import torch
         self._lib = load_library()
         if isinstance(precision, str):
@@ -135,12 +139,29 @@ class Context:
             stream = torch.cuda.current_stream()
         self.stream = stream
         h = ctypes.c_void_p()
-        st = self._lib.nbody_create(ctypes.byref(h), int(capacity), ctypes.byref(self.params),
-                                    ctypes.c_void_p(stream.cuda_stream))
+        sp = ctypes.c_void_p(stream.cuda_stream)
+        if offsets is None:
+            st = self._lib.nbody_create(ctypes.byref(h), int(capacity), ctypes.byref(self.params),
+                                        sp)
+            what = "nbody_create"
+        else:
+            off = np.ascontiguousarray(offsets, dtype=np.int64)
+            st = self._lib.nbody_forest_create(ctypes.byref(h), int(off.shape[0]) - 1,
+                                               off.ctypes.data_as(ctypes.c_void_p),
+                                               ctypes.byref(self.params), sp)
+            what = "nbody_forest_create"
+            capacity = int(off[-1])
+            self.offsets = off
         if st != 0:
-            raise NBodyError(st, "nbody_create")
+            raise NBodyError(st, what)
         self._h = h
         self.capacity = int(capacity)
+
+    @classmethod
+    def forest(cls, offsets, G=1.0, eps=0.0, theta=0.5, dt=1e-3, precision=FP32, stream=None):
+        """A context for independent systems packed into one set of arrays: system k owns
+        bodies offsets[k] .. offsets[k+1] - 1 (nbody_forest_create)."""
+        return cls(0, G, eps, theta, dt, precision, stream, offsets=offsets)
 
     # ---------------------------------------------------------------- plumbing
     def _check(self, st, what):
@@ -228,6 +249,28 @@ class Context:
                                                   _dptr(acc, torch.float64, (3, nt), "acc")),
                     "nbody_direct_forces")
         return acc
+
+    def forest_forces(self, pos, mass, acc=None):
+        import torch
+        n = self.capacity
+        if acc is None:
+            acc = torch.empty((3, n), dtype=torch.float64, device=pos.device)
+        self._check(self._lib.nbody_forest_forces(self._h,
+                                                  _dptr(pos, torch.float64, (3, n), "pos"),
+                                                  _dptr(mass, torch.float64, (n,), "mass"),
+                                                  _dptr(acc, torch.float64, (3, n), "acc")),
+                    "nbody_forest_forces")
+        return acc
+
+    def forest_step(self, pos, vel, mass, nsteps=1, use_graph=False):
+        import torch
+        n = self.capacity
+        self._check(self._lib.nbody_forest_step(self._h,
+                                                _dptr(pos, torch.float64, (3, n), "pos"),
+                                                _dptr(vel, torch.float64, (3, n), "vel"),
+                                                _dptr(mass, torch.float64, (n,), "mass"),
+                                                int(nsteps), 1 if use_graph else 0),
+                    "nbody_forest_step")
 
     def sync(self):
         self._check(self._lib.nbody_sync(self._h), "nbody_sync")

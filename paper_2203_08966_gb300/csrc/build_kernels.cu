@@ -106,6 +106,33 @@ __global__ void __launch_bounds__(kBoxThreads) kick_drift_bbox_kernel(
 // Root cube (min corner, side = largest extent, 1 when all bodies coincide), the scale 2^21 / L,
 // the per-level tables, and the origin of the FP32 coordinates: the centre of mass, so that FP32
 // offsets stay small where the mass is (their absolute rounding error is 2^-24 of the offset).
+// r: min x,y,z, max x,y,z, sum m, sum m x, m y, m z.
+__device__ void finalize_box(const double r[kPart], double theta, Box *box, LevelTables *tab)
+{
+    double ext = 0.0;
+    for (int d = 0; d < 3; ++d) {
+        double e = __dsub_rn(r[3 + d], r[d]);
+        if (e > ext) ext = e;
+    }
+    if (!(ext > 0.0)) ext = 1.0;
+    for (int d = 0; d < 3; ++d) {
+        box->o[d] = r[d];
+        double c = r[6] > 0.0 ? r[7 + d] / r[6] : __dadd_rn(r[d], __dmul_rn(ext, 0.5));
+        // keep the origin inside the box (guards against a non-finite or stray quotient)
+        if (!(c >= r[d] && c <= r[3 + d])) c = __dadd_rn(r[d], __dmul_rn(ext, 0.5));
+        box->c[d] = c;
+    }
+    box->L = ext;
+    box->s = __ddiv_rn(2097152.0, ext);
+    const double th2 = __dmul_rn(theta, theta);
+    for (int lev = 0; lev < kLevels; ++lev) {
+        double l = ldexp(ext, -lev);
+        double l2 = __dmul_rn(l, l);
+        tab->l2[lev] = l2;
+        tab->crit32[lev] = th2 > 0.0 ? (float)__ddiv_rn(l2, th2) : __int_as_float(0x7f800000);
+    }
+}
+
 __global__ void __launch_bounds__(kBoxThreads) bbox_finalize_kernel(const double *partials,
                                                                     int nblk, Box *box,
                                                                     LevelTables *tab, double theta)
@@ -121,30 +148,38 @@ __global__ void __launch_bounds__(kBoxThreads) bbox_finalize_kernel(const double
     __shared__ double r[kPart];
     block_reduce10(v, r);
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double ext = 0.0;
+    if (threadIdx.x == 0) finalize_box(r, theta, box, tab);
+}
+
+// Forest: leapfrog kick and drift of every body (eqs. leapkick1, leapdrift of §2.4).
+__global__ void kick_drift_kernel(double *__restrict__ pos, double *__restrict__ vel,
+                                  const double *__restrict__ acc, int n, double h, double dt)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+#pragma unroll
         for (int d = 0; d < 3; ++d) {
-            double e = __dsub_rn(r[3 + d], r[d]);
-            if (e > ext) ext = e;
-        }
-        if (!(ext > 0.0)) ext = 1.0;
-        for (int d = 0; d < 3; ++d) {
-            box->o[d] = r[d];
-            double c = r[6] > 0.0 ? r[7 + d] / r[6] : __dadd_rn(r[d], __dmul_rn(ext, 0.5));
-            // keep the origin inside the box (guards against a non-finite or stray quotient)
-            if (!(c >= r[d] && c <= r[3 + d])) c = __dadd_rn(r[d], __dmul_rn(ext, 0.5));
-            box->c[d] = c;
-        }
-        box->L = ext;
-        box->s = __ddiv_rn(2097152.0, ext);
-        const double th2 = __dmul_rn(theta, theta);
-        for (int lev = 0; lev < kLevels; ++lev) {
-            double l = ldexp(ext, -lev);
-            double l2 = __dmul_rn(l, l);
-            tab->l2[lev] = l2;
-            tab->crit32[lev] = th2 > 0.0 ? (float)__ddiv_rn(l2, th2) : __int_as_float(0x7f800000);
+            const size_t k = (size_t)d * n + i;
+            const double vh = __dadd_rn(vel[k], __dmul_rn(acc[k], h));
+            vel[k] = vh;
+            pos[k] = __dadd_rn(pos[k], __dmul_rn(vh, dt));
         }
     }
+}
+
+// Forest: one block per system reduces its bodies and writes its root box and level tables.
+__global__ void __launch_bounds__(kBoxThreads) system_box_kernel(
+    const double *__restrict__ pos, const double *__restrict__ mass, int n, Systems ss, Box *box,
+    LevelTables *tab, double theta)
+{
+    const int k = blockIdx.x;
+    double v[kPart];
+    init10(v);
+    for (int i = ss.start[k] + threadIdx.x; i < ss.start[k + 1]; i += blockDim.x)
+        add_body(v, pos[i], pos[(size_t)n + i], pos[2 * (size_t)n + i], mass[i]);
+    __shared__ double r[kPart];
+    block_reduce10(v, r);
+    __syncthreads();
+    if (threadIdx.x == 0) finalize_box(r, theta, box + k, tab + k);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -173,14 +208,20 @@ __device__ __forceinline__ uint64_t spread3(uint64_t v)
     return v;
 }
 
-__global__ void keys_kernel(const double *__restrict__ pos, int n, const Box *__restrict__ box,
-                            uint64_t *__restrict__ keys, uint32_t *__restrict__ ids)
+__device__ __forceinline__ int system_of(const Systems &ss, int i)
 {
-    const double ox = box->o[0], oy = box->o[1], oz = box->o[2], s = box->s;
+    return ss.sys ? (int)ss.sys[i] : 0;
+}
+
+__global__ void keys_kernel(const double *__restrict__ pos, int n, const Box *__restrict__ box,
+                            Systems ss, uint64_t *__restrict__ keys, uint32_t *__restrict__ ids)
+{
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        uint32_t qx = quantise(pos[i], ox, s);
-        uint32_t qy = quantise(pos[(size_t)n + i], oy, s);
-        uint32_t qz = quantise(pos[2 * (size_t)n + i], oz, s);
+        const Box *b = box + system_of(ss, i);
+        const double s = b->s;
+        uint32_t qx = quantise(pos[i], b->o[0], s);
+        uint32_t qy = quantise(pos[(size_t)n + i], b->o[1], s);
+        uint32_t qz = quantise(pos[2 * (size_t)n + i], b->o[2], s);
         keys[i] = (spread3(qx) << 2) | (spread3(qy) << 1) | spread3(qz);
         ids[i] = (uint32_t)i;
     }
@@ -197,7 +238,8 @@ constexpr int kSortThreads = 256;
 constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kSortItems = 16;                         // per thread
 constexpr int kSortTile = kSortThreads * kSortItems;   // 4096 keys per tile
-constexpr int kPasses = 8;
+constexpr int kPasses = 8;       // key passes
+constexpr int kSysPasses = 2;    // forest: system passes (systems < 2^16)
 constexpr size_t kDownSmem = (size_t)kSortTile * 8 + (size_t)kSortTile * 4 +
                              (size_t)kSortWarps * 256 * 4 + 256 * 4 + 256 * 4;
 
@@ -234,9 +276,22 @@ __global__ void __launch_bounds__(kSortThreads) radix_hist_kernel(const uint64_t
     }
 }
 
+// Digit of an element: a byte of its key, or (forest system passes) a byte of the system of its
+// id.
+template <bool kSys>
+__device__ __forceinline__ unsigned sort_digit(uint64_t key, uint32_t id, int shift,
+                                               const uint16_t *sys)
+{
+    if (kSys) return ((unsigned)sys[id] >> shift) & 255u;
+    return (unsigned)((key >> shift) & 255u);
+}
+
+template <bool kSys>
 __global__ void __launch_bounds__(kSortThreads) radix_upsweep_kernel(const uint64_t *__restrict__ keys,
+                                                                    const uint32_t *__restrict__ ids,
                                                                     int n, int shift,
-                                                                    uint32_t *counts, int tiles)
+                                                                    uint32_t *counts, int tiles,
+                                                                    const uint16_t *__restrict__ sys)
 {
     __shared__ uint32_t sh[256];
     sh[threadIdx.x] = 0;
@@ -247,7 +302,8 @@ __global__ void __launch_bounds__(kSortThreads) radix_upsweep_kernel(const uint6
     for (int r = 0; r < kSortItems; ++r) {
         const int i = tile0 + r * 32 + lane;
         const bool ok = i < n;
-        const unsigned d = ok ? (unsigned)((keys[i] >> shift) & 255u) : 256u;
+        const unsigned d = ok ? sort_digit<kSys>(kSys ? 0ull : keys[i], kSys ? ids[i] : 0u, shift, sys)
+                              : 256u;
         const unsigned peers = __match_any_sync(kFull, d);
         if (ok && (__ffs(peers) - 1) == lane) atomicAdd(&sh[d], __popc(peers));
     }
@@ -306,10 +362,11 @@ __global__ void __launch_bounds__(kSortThreads) radix_rowscan_kernel(uint32_t *c
     }
 }
 
+template <bool kSys>
 __global__ void __launch_bounds__(kSortThreads) radix_downsweep_kernel(
     const uint64_t *__restrict__ keys_in, const uint32_t *__restrict__ ids_in,
     uint64_t *__restrict__ keys_out, uint32_t *__restrict__ ids_out, int n, int shift,
-    const uint32_t *__restrict__ offsets, int tiles)
+    const uint32_t *__restrict__ offsets, int tiles, const uint16_t *__restrict__ sys)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     uint64_t *s_keys = reinterpret_cast<uint64_t *>(smem);
@@ -336,7 +393,7 @@ __global__ void __launch_bounds__(kSortThreads) radix_downsweep_kernel(
         const bool ok = i < n;
         k[r] = ok ? keys_in[i] : 0ull;
         id[r] = ok ? ids_in[i] : 0u;
-        const unsigned d = ok ? (unsigned)((k[r] >> shift) & 255u) : 256u;
+        const unsigned d = ok ? sort_digit<kSys>(k[r], id[r], shift, sys) : 256u;
         const unsigned peers = __match_any_sync(kFull, d);
         const uint32_t before = ok ? hist[d] : 0u;
         __syncwarp();
@@ -364,7 +421,7 @@ __global__ void __launch_bounds__(kSortThreads) radix_downsweep_kernel(
     for (int r = 0; r < kSortItems; ++r) {
         const int i = w0 + r * 32 + lane;
         if (i < n) {
-            const unsigned d = (unsigned)((k[r] >> shift) & 255u);
+            const unsigned d = sort_digit<kSys>(k[r], id[r], shift, sys);
             const uint32_t p = s_start[d] + s_warp[wid * 256 + d] + rank[r];
             s_keys[p] = k[r];
             s_ids[p] = id[r];
@@ -373,7 +430,7 @@ __global__ void __launch_bounds__(kSortThreads) radix_downsweep_kernel(
     __syncthreads();
     for (int i = threadIdx.x; i < tile_n; i += blockDim.x) {
         const uint64_t kk = s_keys[i];
-        const unsigned d = (unsigned)((kk >> shift) & 255u);
+        const unsigned d = sort_digit<kSys>(kk, s_ids[i], shift, sys);
         const int o = s_gofs[d] + i;
         keys_out[o] = kk;
         ids_out[o] = s_ids[i];
@@ -387,10 +444,12 @@ __global__ void __launch_bounds__(kSortThreads) radix_downsweep_kernel(
 
 __global__ void permute_kernel(const double *__restrict__ pos, const double *__restrict__ mass,
                                const uint32_t *__restrict__ ids, int n, const Box *__restrict__ box,
-                               double G, D4 *__restrict__ sbody64, float4 *__restrict__ sbody32)
+                               Systems ss, double G, D4 *__restrict__ sbody64,
+                               float4 *__restrict__ sbody32)
 {
-    const double cx = box->c[0], cy = box->c[1], cz = box->c[2];
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const Box *bx = box + system_of(ss, i);
+        const double cx = bx->c[0], cy = bx->c[1], cz = bx->c[2];
         const uint32_t id = ids[i];
         D4 b;
         b.x = pos[id];
@@ -421,11 +480,26 @@ __device__ __forceinline__ int lcp_digits(uint64_t a, uint64_t b)
     return (__clzll((long long)x) - 1) / 3;
 }
 
-__device__ __forceinline__ void body_lcps(const uint64_t *keys, int n, int a, int &lp, int &la)
+// Body a's system spans sorted indices lo .. hi - 1 (0 .. n - 1 for a single system).
+__device__ __forceinline__ void system_range(const Systems &ss, int n, int a, int &lo, int &hi)
+{
+    if (ss.sys) {
+        const int k = ss.sys[a];
+        lo = ss.start[k];
+        hi = ss.start[k + 1];
+    } else {
+        lo = 0;
+        hi = n;
+    }
+}
+
+// lcp with the previous and the next body of the same system (-1 past either end).
+__device__ __forceinline__ void body_lcps(const uint64_t *keys, int lo, int hi, int a, int &lp,
+                                          int &la)
 {
     const uint64_t ka = keys[a];
-    lp = a > 0 ? lcp_digits(keys[a - 1], ka) : -1;
-    la = a + 1 < n ? lcp_digits(ka, keys[a + 1]) : -1;
+    lp = a > lo ? lcp_digits(keys[a - 1], ka) : -1;
+    la = a + 1 < hi ? lcp_digits(ka, keys[a + 1]) : -1;
 }
 
 __device__ __forceinline__ uint32_t nodes_started(int lp, int la)
@@ -436,14 +510,15 @@ __device__ __forceinline__ uint32_t nodes_started(int lp, int la)
 }
 
 // Nodes started by every body, and (atomic max into *max_level) the deepest node level.
-__global__ void count_nodes_kernel(const uint64_t *__restrict__ keys, int n, uint32_t *counts,
-                                   unsigned *max_level)
+__global__ void count_nodes_kernel(const uint64_t *__restrict__ keys, int n, Systems ss,
+                                   uint32_t *counts, unsigned *max_level)
 {
     unsigned deepest = 0;
     for (int a = blockIdx.x * blockDim.x + threadIdx.x; a <= n; a += gridDim.x * blockDim.x) {
         if (a == n) { counts[n] = 0; continue; }
-        int lp, la;
-        body_lcps(keys, n, a, lp, la);
+        int lo, hi, lp, la;
+        system_range(ss, n, a, lo, hi);
+        body_lcps(keys, lo, hi, a, lp, la);
         counts[a] = nodes_started(lp, la);
         const int lv = (la == kMaxLevel || lp == kMaxLevel) ? kMaxLevel : max(lp, la) + 1;
         deepest = max(deepest, (unsigned)lv);
@@ -471,15 +546,21 @@ __device__ int run_end(const uint64_t *keys, int n, int lo, uint64_t prefix, int
     return hi;
 }
 
-__global__ void emit_nodes_kernel(const uint64_t *__restrict__ keys, int n,
-                                  const uint32_t *__restrict__ node_off, NodeArrays na)
+__global__ void emit_nodes_kernel(const uint64_t *__restrict__ keys, int n, Systems ss,
+                                  const uint32_t *__restrict__ node_off, NodeArrays na, int *err)
 {
+    if (*na.d_nn == 0u) return;  // the tree did not fit: no node is written (see clamp_count)
     for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < n; a += gridDim.x * blockDim.x) {
-        int lp, la;
-        body_lcps(keys, n, a, lp, la);
+        int lo, hi, lp, la;
+        system_range(ss, n, a, lo, hi);
+        body_lcps(keys, lo, hi, a, lp, la);
         const uint32_t k = nodes_started(lp, la);
         if (k == 0) continue;
         const int base = (int)node_off[a];
+        if ((int64_t)base + k > na.cap) {   // more nodes than the arrays hold: write none
+            atomicOr(err, kErrNodeCap);
+            continue;
+        }
         const uint64_t ka = keys[a];
         // levels of the cells (internal or bucket) that start at body a, deepest first so each
         // search starts from the end of the nested deeper run.
@@ -489,7 +570,7 @@ __global__ void emit_nodes_kernel(const uint64_t *__restrict__ keys, int n,
         for (int l = deepest_run; l >= top; --l) {
             const int shift = 3 * (kMaxLevel - l);
             const uint64_t prefix = shift >= 64 ? 0ull : (ka >> shift);
-            end = run_end(keys, n, max(a + 1, end - 1), prefix, shift);
+            end = run_end(keys, hi, max(a + 1, end - 1), prefix, shift);
             const int idx = base + (l - top);
             WalkNode w;
             w.c = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -538,13 +619,11 @@ __device__ __forceinline__ void store_node(NodeArrays &na, int j, const WalkNode
 // Child masks and node kinds, plus the moments of every leaf (Algorithm 2, moments from the
 // leaves up): a one-body leaf holds its body; a level-21 bucket the mass-weighted mean of its
 // bodies in Morton order, every product and sum separately rounded.
-__global__ void link_leaves_kernel(const uint64_t *__restrict__ keys, int n_nodes, NodeArrays na,
+__global__ void link_leaves_kernel(const uint64_t *__restrict__ keys, NodeArrays na,
                                    const D4 *__restrict__ sbody64, const Box *__restrict__ box,
-                                   double G, unsigned *level_count)
+                                   Systems ss, double G)
 {
-    __shared__ unsigned hist[kLevels];
-    if (threadIdx.x < kLevels) hist[threadIdx.x] = 0;
-    __syncthreads();
+    const int n_nodes = (int)min((int64_t)*na.d_nn, na.cap);
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n_nodes; j += gridDim.x * blockDim.x) {
         const WalkNode w = na.wn[j];
         const int lev = na.level[j];
@@ -568,7 +647,7 @@ __global__ void link_leaves_kernel(const uint64_t *__restrict__ keys, int n_node
                 m.y = __ddiv_rn(sy, s);
                 m.z = __ddiv_rn(sz, s);
             }
-            store_node(na, j, w, m, box, G, 0.f);
+            store_node(na, j, w, m, box + system_of(ss, w.first), G, 0.f);
             continue;
         }
         const int shift = 3 * (kMaxLevel - 1 - lev);
@@ -580,60 +659,21 @@ __global__ void link_leaves_kernel(const uint64_t *__restrict__ keys, int n_node
             mask |= 1u << (unsigned)((keys[na.wn[c].first] >> shift) & 7u);
         na.mask[j] = (uint8_t)mask;
         na.kind[j] = (uint8_t)lev;
-        atomicAdd(&hist[lev], 1u);
-    }
-    __syncthreads();
-    if (threadIdx.x < kLevels && hist[threadIdx.x]) atomicAdd(&level_count[threadIdx.x], hist[threadIdx.x]);
-}
-
-// level_start[l] = number of internal cells at levels < l (exclusive scan of 22 counters); the
-// scatter cursors restart at zero.
-__global__ void level_scan_kernel(const unsigned *level_count, unsigned *level_start,
-                                  unsigned *cursor)
-{
-    if (threadIdx.x == 0) {
-        unsigned run = 0;
-        for (int l = 0; l < kLevels; ++l) {
-            level_start[l] = run;
-            run += level_count[l];
-            cursor[l] = 0;
-        }
-        level_start[kLevels] = run;
-    }
-}
-
-// Lists the internal cells of every level: list[level_start[l] ..] holds those at level l.
-__global__ void level_scatter_kernel(int n_nodes, const uint8_t *__restrict__ kind,
-                                     const unsigned *__restrict__ level_start, unsigned *cursor,
-                                     int *list)
-{
-    const int lane = threadIdx.x & 31;
-    for (int base = blockIdx.x * blockDim.x; base < n_nodes; base += gridDim.x * blockDim.x) {
-        const int j = base + threadIdx.x;
-        const unsigned k = j < n_nodes ? kind[j] : (unsigned)kLeafKind;
-        const unsigned peers = __match_any_sync(kFull, k);
-        if (k < (unsigned)kLevels) {
-            const int leader = __ffs(peers) - 1;
-            unsigned off = 0;
-            if (lane == leader) off = atomicAdd(&cursor[k], (unsigned)__popc(peers));
-            off = __shfl_sync(peers, off, leader);
-            const unsigned rank = __popc(peers & ((1u << lane) - 1u));
-            list[level_start[k] + off + rank] = j;
-        }
     }
 }
 
 // Moments of the internal cells of one level, from their children (one level deeper, already
 // done): m = sum m_c, r = (sum m_c r_c) / m over the children in octant order, every product and
 // sum separately rounded.  Launched for the levels from the deepest up to the root.
-__global__ void moments_level_kernel(int level, const unsigned *__restrict__ level_start,
-                                     const int *__restrict__ list, NodeArrays na,
-                                     const Box *__restrict__ box,
-                                     const LevelTables *__restrict__ tab, double G)
+__global__ void moments_level_kernel(int level, NodeArrays na, const Box *__restrict__ box,
+                                     const LevelTables *__restrict__ tab, Systems ss, double G)
 {
-    const int lo = (int)level_start[level], hi = (int)level_start[level + 1];
+    // the nodes of this level are level-order indices [start(level), start(level + 1))
+    const int lo = (int)na.tile_offsets[level * na.tiles];
+    const int hi = (int)na.tile_offsets[(level + 1) * na.tiles];
     for (int t = lo + blockIdx.x * blockDim.x + threadIdx.x; t < hi; t += gridDim.x * blockDim.x) {
-        const int j = list[t];
+        const int j = na.inv[t];
+        if (na.kind[j] == kLeafKind) continue;
         const WalkNode w = na.wn[j];
         double s = 0.0, sx = 0.0, sy = 0.0, sz = 0.0;
         int nc = 0;
@@ -649,7 +689,8 @@ __global__ void moments_level_kernel(int level, const unsigned *__restrict__ lev
         m.x = __ddiv_rn(sx, s);
         m.y = __ddiv_rn(sy, s);
         m.z = __ddiv_rn(sz, s);
-        store_node(na, j, w, m, box, G, tab->crit32[level]);
+        const int k = system_of(ss, w.first);
+        store_node(na, j, w, m, box + k, G, tab[k].crit32[level]);
     }
 }
 
@@ -668,8 +709,10 @@ constexpr unsigned kNoLevel = 0xffu;
 // Per tile: the number of nodes of every level, stored level-major (counts[l * tiles + t]) so
 // that one exclusive scan gives every (level, tile) its first output index.
 __global__ void __launch_bounds__(kLayThreads) level_tile_count_kernel(
-    const uint8_t *__restrict__ level, int n_nodes, int tiles, uint32_t *counts)
+    const uint8_t *__restrict__ level, const uint32_t *__restrict__ d_nn, int64_t cap, int tiles,
+    uint32_t *counts)
 {
+    const int n_nodes = (int)min((int64_t)*d_nn, cap);
     __shared__ unsigned h[kLevels];
     if (threadIdx.x < kLevels) h[threadIdx.x] = 0;
     __syncthreads();
@@ -683,14 +726,16 @@ __global__ void __launch_bounds__(kLayThreads) level_tile_count_kernel(
     }
     __syncthreads();
     if (threadIdx.x < kLevels) counts[threadIdx.x * tiles + blockIdx.x] = h[threadIdx.x];
+    if (blockIdx.x == 0 && threadIdx.x == 0) counts[kLevels * tiles] = 0;  // scans to the total
 }
 
 // Level-order index of every node: its (level, tile) offset plus its rank among the nodes of
 // the same level earlier in the tile.
 __global__ void __launch_bounds__(kLayThreads) level_tile_rank_kernel(
-    const uint8_t *__restrict__ level, int n_nodes, int tiles, const uint32_t *__restrict__ offs,
-    int *order)
+    const uint8_t *__restrict__ level, const uint32_t *__restrict__ d_nn, int64_t cap, int tiles,
+    const uint32_t *__restrict__ offs, int *order, int *inv)
 {
+    const int n_nodes = (int)min((int64_t)*d_nn, cap);
     __shared__ unsigned run[kLevels];
     __shared__ unsigned wc[kLayWarps][kLevels];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -709,6 +754,7 @@ __global__ void __launch_bounds__(kLayThreads) level_tile_rank_kernel(
             unsigned o = run[l] + rank;
             for (int w = 0; w < wid; ++w) o += wc[w][l];
             order[j] = (int)o;
+            inv[o] = j;
         }
         __syncthreads();
         if (threadIdx.x < kLevels) {
@@ -722,10 +768,12 @@ __global__ void __launch_bounds__(kLayThreads) level_tile_rank_kernel(
 
 // GroupNode records at their level-order positions.  The first child of an internal cell is
 // the next node in pre-order; its children count is the population of the child mask.
-__global__ void group_nodes_kernel(int n_nodes, const WalkNode *__restrict__ wn,
+__global__ void group_nodes_kernel(const uint32_t *__restrict__ d_nn, int64_t cap,
+                                   const WalkNode *__restrict__ wn,
                                    const uint8_t *__restrict__ mask, const int *__restrict__ order,
                                    GroupNode *gn)
 {
+    const int n_nodes = (int)min((int64_t)*d_nn, cap);
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n_nodes; j += gridDim.x * blockDim.x) {
         const WalkNode w = wn[j];
         GroupNode g;
@@ -736,11 +784,37 @@ __global__ void group_nodes_kernel(int n_nodes, const WalkNode *__restrict__ wn,
             g.n = -w.count;
             g.crit = 0.f;
         } else {
-            g.child = order[j + 1];
-            g.n = __popc((unsigned)mask[j]);
+            g.child = j + 1 < n_nodes ? order[j + 1] : n_nodes;  // out of range: the walk refuses it
+            g.n = max(1, __popc((unsigned)mask[j]));
             g.crit = w.crit;
         }
         gn[order[j]] = g;
+    }
+}
+
+// Forest: level-order index of the root of every non-empty system (its first pre-order node).
+__global__ void roots_kernel(const uint32_t *__restrict__ node_off, Systems ss,
+                             const uint32_t *__restrict__ d_nn, const int *__restrict__ order,
+                             int *roots)
+{
+    const uint32_t nn = *d_nn;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < ss.count; k += gridDim.x * blockDim.x) {
+        const uint32_t r = node_off[ss.start[k]];
+        roots[k] = (ss.start[k + 1] > ss.start[k] && r < nn) ? order[r] : -1;
+    }
+}
+
+// Forest: the node count the other kernels use.  A tree larger than the node arrays is not
+// built at all (count 0, kErrNodeCap), so no kernel ever reads or writes past them.
+__global__ void clamp_count_kernel(const uint32_t *__restrict__ total, int64_t cap, uint32_t *nn,
+                                   int *err)
+{
+    const uint32_t t = *total;
+    if ((int64_t)t > cap) {
+        *nn = 0u;
+        atomicOr(err, kErrNodeCap);
+    } else {
+        *nn = t;
     }
 }
 
@@ -858,10 +932,24 @@ void launch_bbox_finalize(const double *partials, int nblk, Box *box, LevelTable
     count_launches(1);
 }
 
-void launch_keys(const double *pos, int n, const Box *box, uint64_t *keys, uint32_t *ids,
-                 cudaStream_t s)
+void launch_kick_drift(double *pos, double *vel, const double *acc, int n, double h, double dt,
+                       cudaStream_t s)
 {
-    keys_kernel<<<grid_for(n, 256, kMaxGrid), 256, 0, s>>>(pos, n, box, keys, ids);
+    kick_drift_kernel<<<grid_for(n, 256, kMaxGrid), 256, 0, s>>>(pos, vel, acc, n, h, dt);
+    count_launches(1);
+}
+
+void launch_system_boxes(const double *pos, const double *mass, int n, const Systems &ss,
+                         Box *box, LevelTables *tab, double theta, cudaStream_t s)
+{
+    system_box_kernel<<<ss.count, kBoxThreads, 0, s>>>(pos, mass, n, ss, box, tab, theta);
+    count_launches(1);
+}
+
+void launch_keys(const double *pos, int n, const Box *box, const Systems &ss, uint64_t *keys,
+                 uint32_t *ids, cudaStream_t s)
+{
+    keys_kernel<<<grid_for(n, 256, kMaxGrid), 256, 0, s>>>(pos, n, box, ss, keys, ids);
     count_launches(1);
 }
 
@@ -869,8 +957,12 @@ int sort_tiles(int n) { return (n + kSortTile - 1) / kSortTile; }
 
 cudaError_t sort_prepare()
 {
-    return cudaFuncSetAttribute(radix_downsweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)kDownSmem);
+    cudaError_t e = cudaFuncSetAttribute(radix_downsweep_kernel<false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kDownSmem);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(radix_downsweep_kernel<true>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDownSmem);
 }
 
 void launch_radix_sort(uint64_t *keys, uint32_t *ids, int n, const SortScratch &sc, cudaStream_t s)
@@ -881,33 +973,46 @@ void launch_radix_sort(uint64_t *keys, uint32_t *ids, int n, const SortScratch &
     radix_hist_kernel<<<grid_for(n, kSortThreads * 8, 152 * 4), kSortThreads, 0, s>>>(keys, n, sc.hist);
     uint64_t *kin = keys, *kout = sc.keys_alt;
     uint32_t *iin = ids, *iout = sc.ids_alt;
-    for (int p = 0; p < kPasses; ++p) {
-        const int shift = 8 * p;
-        radix_upsweep_kernel<<<tiles, kSortThreads, 0, s>>>(kin, n, shift, sc.counts, tiles);
-        radix_rowscan_kernel<<<256, kSortThreads, 0, s>>>(sc.counts, tiles, sc.hist + 256 * p);
-        radix_downsweep_kernel<<<tiles, kSortThreads, kDownSmem, s>>>(kin, iin, kout, iout, n, shift,
-                                                                     sc.counts, tiles);
+    const int passes = kPasses + (sc.sys ? kSysPasses : 0);
+    for (int p = 0; p < passes; ++p) {
+        const bool sys_pass = p >= kPasses;
+        const int shift = sys_pass ? 8 * (p - kPasses) : 8 * p;
+        const uint32_t *hist = sys_pass ? sc.sys_hist + 256 * (p - kPasses) : sc.hist + 256 * p;
+        if (sys_pass)
+            radix_upsweep_kernel<true><<<tiles, kSortThreads, 0, s>>>(kin, iin, n, shift, sc.counts,
+                                                                     tiles, sc.sys);
+        else
+            radix_upsweep_kernel<false><<<tiles, kSortThreads, 0, s>>>(kin, iin, n, shift,
+                                                                      sc.counts, tiles, nullptr);
+        radix_rowscan_kernel<<<256, kSortThreads, 0, s>>>(sc.counts, tiles, hist);
+        if (sys_pass)
+            radix_downsweep_kernel<true><<<tiles, kSortThreads, kDownSmem, s>>>(
+                kin, iin, kout, iout, n, shift, sc.counts, tiles, sc.sys);
+        else
+            radix_downsweep_kernel<false><<<tiles, kSortThreads, kDownSmem, s>>>(
+                kin, iin, kout, iout, n, shift, sc.counts, tiles, nullptr);
         uint64_t *tk = kin; kin = kout; kout = tk;
         uint32_t *ti = iin; iin = iout; iout = ti;
     }
-    count_launches(1 + 3 * kPasses);
-    // an even number of passes leaves the result in the caller's buffers
+    count_launches(1 + 3 * passes);
+    // an even number of passes (8, or 8 + 2) leaves the result in the caller's buffers
 }
 
 void launch_permute(const double *pos, const double *mass, const uint32_t *ids, int n,
-                    const Box *box, double G, D4 *sbody64, float4 *sbody32, cudaStream_t s)
+                    const Box *box, const Systems &ss, double G, D4 *sbody64, float4 *sbody32,
+                    cudaStream_t s)
 {
-    permute_kernel<<<grid_for(n, 256, kMaxGrid), 256, 0, s>>>(pos, mass, ids, n, box, G, sbody64,
-                                                              sbody32);
+    permute_kernel<<<grid_for(n, 256, kMaxGrid), 256, 0, s>>>(pos, mass, ids, n, box, ss, G,
+                                                              sbody64, sbody32);
     count_launches(1);
 }
 
 int scan_tiles(int len) { return (len + kScanTile - 1) / kScanTile; }
 
-void launch_count_nodes(const uint64_t *keys, int n, uint32_t *counts, unsigned *max_level,
-                        cudaStream_t s)
+void launch_count_nodes(const uint64_t *keys, int n, const Systems &ss, uint32_t *counts,
+                        unsigned *max_level, cudaStream_t s)
 {
-    count_nodes_kernel<<<grid_for((int64_t)n + 1, 256, kMaxGrid), 256, 0, s>>>(keys, n, counts,
+    count_nodes_kernel<<<grid_for((int64_t)n + 1, 256, kMaxGrid), 256, 0, s>>>(keys, n, ss, counts,
                                                                               max_level);
     count_launches(1);
 }
@@ -922,51 +1027,67 @@ void launch_exclusive_scan(const uint32_t *in, uint32_t *out, int len, const Sca
     count_launches(3);
 }
 
-void launch_emit_nodes(const uint64_t *keys, int n, const uint32_t *node_off, NodeArrays na,
-                       cudaStream_t s)
+void launch_emit_nodes(const uint64_t *keys, int n, const Systems &ss, const uint32_t *node_off,
+                       NodeArrays na, int *err, cudaStream_t s)
 {
-    emit_nodes_kernel<<<grid_for(n, 128, kMaxGrid * 4), 128, 0, s>>>(keys, n, node_off, na);
+    emit_nodes_kernel<<<grid_for(n, 128, kMaxGrid * 4), 128, 0, s>>>(keys, n, ss, node_off, na,
+                                                                     err);
     count_launches(1);
 }
 
-void launch_moments(const uint64_t *keys, int n_nodes, int max_level, const D4 *sbody64,
-                    const Box *box, const LevelTables *tab, double G, NodeArrays na,
-                    cudaStream_t s)
+int layout_tiles(int64_t n_nodes) { return (int)((n_nodes + kLayTile - 1) / kLayTile); }
+int layout_scan_len(int64_t n_nodes) { return kLevels * layout_tiles(n_nodes) + 1; }
+
+void launch_level_order(const NodeArrays &na, cudaStream_t s)
 {
-    const int grid = grid_for(n_nodes, 256, kMaxGrid * 4);
-    cudaMemsetAsync(na.level_count, 0, sizeof(unsigned) * kLevels, s);
-    link_leaves_kernel<<<grid, 256, 0, s>>>(keys, n_nodes, na, sbody64, box, G, na.level_count);
-    level_scan_kernel<<<1, 32, 0, s>>>(na.level_count, na.level_start, na.level_cursor);
-    level_scatter_kernel<<<grid, 256, 0, s>>>(n_nodes, na.kind, na.level_start, na.level_cursor,
-                                              na.level_list);
-    const int depth = min(max_level, kMaxLevel);
-    for (int lev = depth - 1; lev >= 0; --lev) {
-        // the node count of a level is only known on the device: a grid for the widest level
-        // (at most 8^lev cells) and a grid-stride loop over the level's list
-        const int64_t widest = lev < 10 ? ((int64_t)1 << (3 * lev)) : (int64_t)n_nodes;
-        const int g = grid_for(std::min<int64_t>(widest, n_nodes), 256, kMaxGrid * 2);
-        moments_level_kernel<<<g, 256, 0, s>>>(lev, na.level_start, na.level_list, na, box, tab, G);
-    }
-    count_launches(3 + max(0, depth));
+    const int tiles = na.tiles;
+    const int len = kLevels * tiles + 1;
+    level_tile_count_kernel<<<tiles, kLayThreads, 0, s>>>(na.level, na.d_nn, na.cap, tiles,
+                                                          na.tile_offsets);
+    ScanScratch ss{na.block_sums, scan_tiles(len)};
+    launch_exclusive_scan(na.tile_offsets, na.tile_offsets, len, ss, s);
+    level_tile_rank_kernel<<<tiles, kLayThreads, 0, s>>>(na.level, na.d_nn, na.cap, tiles,
+                                                         na.tile_offsets, na.order, na.inv);
+    count_launches(2);
 }
 
-int layout_tiles(int64_t n_nodes) { return (int)((n_nodes + kLayTile - 1) / kLayTile); }
-int layout_scan_len(int64_t n_nodes) { return kLevels * layout_tiles(n_nodes); }
-
-void launch_level_order(const NodeArrays na, int n_nodes, const LayoutScratch &ls, GroupNode *gn,
-                        cudaStream_t s)
+void launch_moments(const uint64_t *keys, int max_level, const D4 *sbody64, const Box *box,
+                    const LevelTables *tab, const Systems &ss, double G, NodeArrays na,
+                    cudaStream_t s)
 {
-    const int tiles = layout_tiles(n_nodes);
-    const int len = kLevels * tiles;
-    level_tile_count_kernel<<<tiles, kLayThreads, 0, s>>>(na.level, n_nodes, tiles,
-                                                          ls.tile_offsets);
-    ScanScratch ss{ls.block_sums, scan_tiles(len)};
-    launch_exclusive_scan(ls.tile_offsets, ls.tile_offsets, len, ss, s);
-    level_tile_rank_kernel<<<tiles, kLayThreads, 0, s>>>(na.level, n_nodes, tiles,
-                                                         ls.tile_offsets, ls.order);
-    group_nodes_kernel<<<grid_for(n_nodes, 256, kMaxGrid * 4), 256, 0, s>>>(n_nodes, na.wn,
-                                                                           na.mask, ls.order, gn);
-    count_launches(3);
+    const int64_t cap = na.cap;
+    link_leaves_kernel<<<grid_for(cap, 256, kMaxGrid * 4), 256, 0, s>>>(keys, na, sbody64, box, ss,
+                                                                       G);
+    const int depth = min(max_level, kMaxLevel);
+    for (int lev = depth - 1; lev >= 0; --lev) {
+        // a level's node count is only known on the device: a grid for the widest level it can
+        // have (8^lev cells per system) and a grid-stride loop over the level's range
+        const int64_t widest = lev < 10 ? ((int64_t)ss.count << (3 * lev)) : cap;
+        const int g = grid_for(std::min<int64_t>(widest, cap), 256, kMaxGrid * 2);
+        moments_level_kernel<<<g, 256, 0, s>>>(lev, na, box, tab, ss, G);
+    }
+    count_launches(1 + max(0, depth));
+}
+
+void launch_group_nodes(const NodeArrays &na, GroupNode *gn, cudaStream_t s)
+{
+    group_nodes_kernel<<<grid_for(na.cap, 256, kMaxGrid * 4), 256, 0, s>>>(na.d_nn, na.cap, na.wn,
+                                                                          na.mask, na.order, gn);
+    count_launches(1);
+}
+
+void launch_roots(const NodeArrays &na, const uint32_t *node_off, const Systems &ss, int *roots,
+                  cudaStream_t s)
+{
+    roots_kernel<<<grid_for(ss.count, 256, kMaxGrid), 256, 0, s>>>(node_off, ss, na.d_nn, na.order,
+                                                                   roots);
+    count_launches(1);
+}
+
+void launch_clamp_count(const uint32_t *total, int64_t cap, uint32_t *nn, int *err, cudaStream_t s)
+{
+    clamp_count_kernel<<<1, 1, 0, s>>>(total, cap, nn, err);
+    count_launches(1);
 }
 
 }  // namespace nb

@@ -38,14 +38,27 @@ struct nbody_ctx {
     int *err = nullptr;             // device error word
     uint32_t *h_word = nullptr;     // pinned host words: node count, deepest level
     unsigned *info = nullptr;       // device word: deepest node level of the last build
-    unsigned *levels = nullptr;     // per-level counters, offsets and cursors of the moments
 
     // octree
     NodeArrays na{};
     int64_t n_nodes = 0;
-    // level-order copy for the FP32 group walk (capacity na.cap)
-    GroupNode *gn = nullptr;
-    LayoutScratch ls{};
+    GroupNode *gn = nullptr;        // level-order copy for the FP32 group walk (capacity na.cap)
+
+    // forest (n_sys > 0): systems packed in one set of arrays
+    int n_sys = 0;
+    uint16_t *sys = nullptr;        // system of every body
+    int *sys_start = nullptr;       // n_sys + 1 body offsets
+    uint32_t *sys_hist = nullptr;   // digit totals of the two system sort passes
+    int4 *groups = nullptr;         // walk groups: (first body, count, system, 0)
+    int n_groups = 0;
+    int *roots = nullptr;           // level-order root of every system
+    uint32_t *nn = nullptr;         // node count the forest's kernels use (device)
+    // one forest step captured as a CUDA graph, replayed on its own stream
+    cudaStream_t gstream = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    const void *gkey[3] = {nullptr, nullptr, nullptr};
+    int64_t glaunches = 0;          // kernels per replayed step
+    cudaEvent_t gev[2] = {};
 
     // host-buffer stepping
     double *hpos = nullptr, *hvel = nullptr, *hmass = nullptr;
@@ -121,11 +134,11 @@ void free_nodes(nbody_ctx *c)
     dfree(c->na.level);
     dfree(c->na.mask);
     dfree(c->na.kind);
-    dfree(c->na.level_list);
+    dfree(c->na.order);
+    dfree(c->na.inv);
+    dfree(c->na.tile_offsets);
+    dfree(c->na.block_sums);
     dfree(c->gn);
-    dfree(c->ls.tile_offsets);
-    dfree(c->ls.block_sums);
-    dfree(c->ls.order);
     c->na.cap = 0;
 }
 
@@ -139,13 +152,13 @@ nbody_status ensure_nodes(nbody_ctx *c, int64_t need)
     CK(dalloc(&c->na.level, cap));
     CK(dalloc(&c->na.mask, cap));
     CK(dalloc(&c->na.kind, cap));
-    CK(dalloc(&c->na.level_list, cap));
-    CK(dalloc(&c->gn, cap));
-    CK(dalloc(&c->ls.order, cap));
+    CK(dalloc(&c->na.order, cap));
+    CK(dalloc(&c->na.inv, cap));
     const int len = layout_scan_len(cap);
-    CK(dalloc(&c->ls.tile_offsets, (size_t)len + 1));
-    CK(dalloc(&c->ls.block_sums, (size_t)scan_tiles(len) + 1));
-    c->ls.max_tiles = layout_tiles(cap);
+    CK(dalloc(&c->na.tile_offsets, (size_t)len));
+    CK(dalloc(&c->na.block_sums, (size_t)scan_tiles(len) + 1));
+    c->na.tiles = layout_tiles(cap);
+    CK(dalloc(&c->gn, cap));
     c->na.cap = cap;
     return NBODY_OK;
 }
@@ -181,16 +194,18 @@ nbody_status build(nbody_ctx *c, const double *pos, const double *mass, int n,
         c->n_built = 0;
         return NBODY_OK;
     }
+    const Systems one{nullptr, nullptr, 1};
     if (!have_partials) launch_bbox_partials(pos, mass, n, c->partials, c->nblk, s);
     launch_bbox_finalize(c->partials, c->nblk, c->box, c->tab, c->p.theta, s);
-    launch_keys(pos, n, c->box, c->keys, c->ids, s);
+    launch_keys(pos, n, c->box, one, c->keys, c->ids, s);
     record(c, 1);
-    SortScratch sc{c->keys_alt, c->ids_alt, c->hist, c->counts, sort_tiles((int)c->cap)};
+    SortScratch sc{c->keys_alt, c->ids_alt, c->hist, c->counts, sort_tiles((int)c->cap), nullptr,
+                   nullptr};
     launch_radix_sort(c->keys, c->ids, n, sc, s);
     record(c, 2);
-    launch_permute(pos, mass, c->ids, n, c->box, c->p.G, c->sbody64, c->sbody32, s);
+    launch_permute(pos, mass, c->ids, n, c->box, one, c->p.G, c->sbody64, c->sbody32, s);
     CK(cudaMemsetAsync(c->info, 0, sizeof(unsigned), s));
-    launch_count_nodes(c->keys, n, c->node_off, c->info, s);
+    launch_count_nodes(c->keys, n, one, c->node_off, c->info, s);
     ScanScratch ss{c->block_sums, scan_tiles((int)c->cap + 1)};
     launch_exclusive_scan(c->node_off, c->node_off, n + 1, ss, s);
     CKS(check_launch(c, "tree build"));
@@ -207,12 +222,11 @@ nbody_status build(nbody_ctx *c, const double *pos, const double *mass, int n,
                     (long long)nn, (long long)kMaxGroupNodes);
     CKS(ensure_nodes(c, nn));
     c->n_nodes = nn;
-    c->na.level_count = c->levels;
-    c->na.level_start = c->levels + kLevels;
-    c->na.level_cursor = c->levels + 2 * kLevels + 1;
-    launch_emit_nodes(c->keys, n, c->node_off, c->na, s);
-    launch_moments(c->keys, (int)nn, max_level, c->sbody64, c->box, c->tab, c->p.G, c->na, s);
-    if (group) launch_level_order(c->na, (int)nn, c->ls, c->gn, s);
+    c->na.d_nn = c->node_off + n;
+    launch_emit_nodes(c->keys, n, one, c->node_off, c->na, c->err, s);
+    launch_level_order(c->na, s);
+    launch_moments(c->keys, max_level, c->sbody64, c->box, c->tab, one, c->p.G, c->na, s);
+    if (group) launch_group_nodes(c->na, c->gn, s);
     record(c, 3);
     CKS(check_launch(c, "node split / moments"));
     c->n_built = n;
@@ -227,7 +241,6 @@ nbody_status walk(nbody_ctx *c, int n, double *acc, double *vel, double h)
     a.com64 = c->na.com64;
     a.level = c->na.level;
     a.tab = c->tab;
-    a.n_nodes = (int)c->n_nodes;
     a.sbody64 = c->sbody64;
     a.sbody32 = c->sbody32;
     a.ids = c->ids;
@@ -242,11 +255,62 @@ nbody_status walk(nbody_ctx *c, int n, double *acc, double *vel, double h)
     a.pc = c->pc;
     a.gn = c->gn;
     a.err = c->err;
+    a.d_nn = c->na.d_nn;
+    a.groups = c->groups;
+    a.n_groups = c->n_groups;
+    a.roots = c->roots;
+    a.node_off = c->node_off;
+    a.start = c->sys_start;
     launch_walk(c->p.precision, a, c->stream);
     record(c, 4);
     CKS(check_launch(c, "walk"));
     c->n_forces = n;
     return NBODY_OK;
+}
+
+// ---------------------------------------------------------------- forest
+// Every step of a forest runs over all systems at once, with no host synchronisation: the node
+// count stays on the device (the node arrays are sized at creation), so a step can be captured
+// as a CUDA graph.
+
+Systems systems(const nbody_ctx *c) { return Systems{c->sys, c->sys_start, c->n_sys}; }
+
+nbody_status forest_build(nbody_ctx *c, const double *pos, const double *mass)
+{
+    cudaStream_t s = c->stream;
+    const int n = (int)c->cap;
+    const Systems ss = systems(c);
+    launch_system_boxes(pos, mass, n, ss, c->box, c->tab, c->p.theta, s);
+    launch_keys(pos, n, c->box, ss, c->keys, c->ids, s);
+    SortScratch sc{c->keys_alt, c->ids_alt, c->hist, c->counts, sort_tiles(n), c->sys,
+                   c->sys_hist};
+    launch_radix_sort(c->keys, c->ids, n, sc, s);
+    launch_permute(pos, mass, c->ids, n, c->box, ss, c->p.G, c->sbody64, c->sbody32, s);
+    CK(cudaMemsetAsync(c->info, 0, sizeof(unsigned), s));
+    launch_count_nodes(c->keys, n, ss, c->node_off, c->info, s);
+    ScanScratch sn{c->block_sums, scan_tiles(n + 1)};
+    launch_exclusive_scan(c->node_off, c->node_off, n + 1, sn, s);
+    launch_clamp_count(c->node_off + n, c->na.cap, c->nn, c->err, s);
+    c->na.d_nn = c->nn;
+    launch_emit_nodes(c->keys, n, ss, c->node_off, c->na, c->err, s);
+    launch_level_order(c->na, s);
+    launch_moments(c->keys, kMaxLevel, c->sbody64, c->box, c->tab, ss, c->p.G, c->na, s);
+    if (c->p.precision != NBODY_FP64) launch_group_nodes(c->na, c->gn, s);
+    launch_roots(c->na, c->node_off, ss, c->roots, s);
+    CKS(check_launch(c, "forest build"));
+    c->n_built = n;
+    c->n_nodes = -1;  // on the device only
+    return NBODY_OK;
+}
+
+nbody_status forest_step_once(nbody_ctx *c, double *pos, double *vel, const double *mass)
+{
+    const int n = (int)c->cap;
+    const double h = 0.5 * c->p.dt;
+    launch_kick_drift(pos, vel, c->acc, n, h, c->p.dt, c->stream);
+    CKS(check_launch(c, "kick/drift"));
+    CKS(forest_build(c, pos, mass));
+    return walk(c, n, c->acc, vel, h);
 }
 
 nbody_status begin_timing(nbody_ctx *c)
@@ -306,7 +370,6 @@ nbody_status nbody_create(nbody_ctx **out, int64_t n_capacity, const nbody_param
         CK(dalloc(&c->pp, cap));
         CK(dalloc(&c->pc, cap));
         CK(dalloc(&c->err, 1));
-        CK(dalloc(&c->levels, 3 * kLevels + 1));
         CK(cudaMemset(c->err, 0, sizeof(int)));
         CK(cudaMallocHost((void **)&c->h_word, 2 * sizeof(uint32_t)));
         CK(dalloc(&c->info, 1));
@@ -344,7 +407,16 @@ nbody_status nbody_destroy(nbody_ctx *c)
     dfree(c->pc);
     dfree(c->err);
     dfree(c->info);
-    dfree(c->levels);
+    dfree(c->sys);
+    dfree(c->sys_start);
+    dfree(c->sys_hist);
+    dfree(c->groups);
+    dfree(c->roots);
+    dfree(c->nn);
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->gstream) cudaStreamDestroy(c->gstream);
+    for (int k = 0; k < 2; ++k)
+        if (c->gev[k]) cudaEventDestroy(c->gev[k]);
     dfree(c->hpos);
     dfree(c->hvel);
     dfree(c->hmass);
@@ -362,12 +434,17 @@ nbody_status nbody_set_params(nbody_ctx *c, const nbody_params *p)
     if (!params_ok(p)) return fail(c, NBODY_EINVAL, "invalid parameters");
     c->p = *p;
     c->acc_n = -1;
+    if (c->gexec) {  // the captured step holds the old parameters
+        cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+    }
     return NBODY_OK;
 }
 
 nbody_status nbody_build_tree(nbody_ctx *c, const double *d_pos, const double *d_mass, int64_t n)
 {
     if (!c) return NBODY_EINVAL;
+    if (c->n_sys) return fail(c, NBODY_ESTATE, "a forest context takes the forest entry points");
     CKS(check_n(c, n));
     if (n > 0 && (!d_pos || !d_mass)) return fail(c, NBODY_EINVAL, "null pointer");
     CKS(begin_timing(c));
@@ -379,6 +456,7 @@ nbody_status nbody_forces(nbody_ctx *c, const double *d_pos, const double *d_mas
                           double *d_acc)
 {
     if (!c) return NBODY_EINVAL;
+    if (c->n_sys) return fail(c, NBODY_ESTATE, "a forest context takes the forest entry points");
     CKS(check_n(c, n));
     if (n > 0 && (!d_pos || !d_mass || !d_acc)) return fail(c, NBODY_EINVAL, "null pointer");
     CKS(begin_timing(c));
@@ -391,6 +469,7 @@ nbody_status nbody_step(nbody_ctx *c, double *d_pos, double *d_vel, const double
                         int64_t n, int32_t nsteps)
 {
     if (!c) return NBODY_EINVAL;
+    if (c->n_sys) return fail(c, NBODY_ESTATE, "a forest context takes the forest entry points");
     CKS(check_n(c, n));
     if (nsteps < 0) return fail(c, NBODY_EINVAL, "nsteps < 0");
     if (n > 0 && (!d_pos || !d_vel || !d_mass)) return fail(c, NBODY_EINVAL, "null pointer");
@@ -417,6 +496,7 @@ nbody_status nbody_step_host(nbody_ctx *c, double *h_pos, double *h_vel, double 
                              const double *h_mass, int64_t n, int32_t nsteps)
 {
     if (!c) return NBODY_EINVAL;
+    if (c->n_sys) return fail(c, NBODY_ESTATE, "a forest context takes the forest entry points");
     CKS(check_n(c, n));
     if (nsteps < 0) return fail(c, NBODY_EINVAL, "nsteps < 0");
     if (n > 0 && (!h_pos || !h_vel || !h_mass)) return fail(c, NBODY_EINVAL, "null pointer");
@@ -457,6 +537,7 @@ nbody_status nbody_direct_forces(nbody_ctx *c, const double *d_pos, const double
                                  int64_t n, const int64_t *d_targets, int64_t nt, double *d_acc)
 {
     if (!c) return NBODY_EINVAL;
+    if (c->n_sys) return fail(c, NBODY_ESTATE, "a forest context takes the forest entry points");
     CKS(check_n(c, n));
     if (!d_targets) nt = n;
     if (nt < 0 || nt > ((int64_t)1 << 30)) return fail(c, NBODY_EINVAL, "bad target count");
@@ -512,6 +593,7 @@ nbody_status nbody_get_tree(nbody_ctx *c, int64_t *n_nodes, nbody_tree_record *h
 {
     if (!c || !n_nodes) return NBODY_EINVAL;
     if (c->n_built < 0) return fail(c, NBODY_ESTATE, "no tree built yet");
+    if (c->n_sys) return fail(c, NBODY_ESTATE, "a forest's trees stay on the device");
     const int64_t nn = c->n_nodes, n = c->n_built;
     *n_nodes = nn;
     if (!h_records || cap < nn || nn == 0) return NBODY_OK;
@@ -546,6 +628,7 @@ nbody_status nbody_get_moments(nbody_ctx *c, double *h_out, int64_t cap_nodes)
 {
     if (!c || !h_out) return NBODY_EINVAL;
     if (c->n_built < 0) return fail(c, NBODY_ESTATE, "no tree built yet");
+    if (c->n_sys) return fail(c, NBODY_ESTATE, "a forest's trees stay on the device");
     const int64_t nn = c->n_nodes;
     if (cap_nodes < nn) return fail(c, NBODY_EINVAL, "cap_nodes < node count %lld", (long long)nn);
     if (nn == 0) return NBODY_OK;
@@ -610,6 +693,160 @@ nbody_status nbody_last_error(nbody_ctx *c, char *buf, int64_t cap)
 {
     if (!c || !buf || cap <= 0) return NBODY_EINVAL;
     snprintf(buf, (size_t)cap, "%s", c->msg);
+    return NBODY_OK;
+}
+
+// ---------------------------------------------------------------- forest
+
+nbody_status nbody_forest_create(nbody_ctx **out, int32_t n_systems, const int64_t *h_offsets,
+                                 const nbody_params *p, void *cuda_stream)
+{
+    if (!out) return NBODY_EINVAL;
+    *out = nullptr;
+    if (n_systems < 1 || n_systems > kMaxSystems || !h_offsets || !params_ok(p)) return NBODY_EINVAL;
+    if (h_offsets[0] != 0) return NBODY_EINVAL;
+    for (int32_t k = 0; k < n_systems; ++k)
+        if (h_offsets[k + 1] < h_offsets[k]) return NBODY_EINVAL;
+    const int64_t n = h_offsets[n_systems];
+    if (n < 1 || n > ((int64_t)1 << 30)) return NBODY_EINVAL;
+    nbody_status st = nbody_create(out, n, p, cuda_stream);
+    if (st != NBODY_OK) return st;
+    nbody_ctx *c = *out;
+    auto body = [&]() -> nbody_status {
+        const int S = n_systems;
+        c->n_sys = S;
+        std::vector<uint16_t> sys((size_t)n);
+        std::vector<int> start((size_t)S + 1);
+        std::vector<uint32_t> hist(2 * 256, 0u);
+        std::vector<int4> groups;
+        for (int k = 0; k < S; ++k) {
+            const int64_t lo = h_offsets[k], hi = h_offsets[k + 1];
+            start[k] = (int)lo;
+            for (int64_t i = lo; i < hi; ++i) sys[(size_t)i] = (uint16_t)k;
+            hist[k & 255] += (uint32_t)(hi - lo);
+            hist[256 + ((k >> 8) & 255)] += (uint32_t)(hi - lo);
+            for (int64_t b = lo; b < hi; b += 32)
+                groups.push_back(make_int4((int)b, (int)std::min<int64_t>(32, hi - b), k, 0));
+        }
+        start[S] = (int)n;
+        c->n_groups = (int)groups.size();
+        CK(dalloc(&c->sys, (size_t)n));
+        CK(dalloc(&c->sys_start, (size_t)S + 1));
+        CK(dalloc(&c->sys_hist, 2 * 256));
+        CK(dalloc(&c->groups, groups.size()));
+        CK(dalloc(&c->roots, (size_t)S));
+        CK(dalloc(&c->nn, 1));
+        CK(cudaMemcpy(c->sys, sys.data(), sizeof(uint16_t) * n, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(c->sys_start, start.data(), sizeof(int) * (S + 1), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(c->sys_hist, hist.data(), sizeof(uint32_t) * 512, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(c->groups, groups.data(), sizeof(int4) * groups.size(),
+                      cudaMemcpyHostToDevice));
+        // one root box and level table per system
+        dfree(c->box);
+        dfree(c->tab);
+        CK(dalloc(&c->box, (size_t)std::max(2, S)));
+        CK(dalloc(&c->tab, (size_t)std::max(2, S)));
+        // the node count is only known on the device during a step: room for 4 nodes per body
+        // (Plummer-like systems need about 1.5) plus a full chain of 22 levels per system
+        CKS(ensure_nodes(c, 4 * n + 22 * (int64_t)S + 1024));
+        if (c->na.cap > kMaxGroupNodes)
+            return fail(c, NBODY_EINVAL, "forest of %lld bodies exceeds the node index range",
+                        (long long)n);
+        return NBODY_OK;
+    };
+    st = body();
+    if (st != NBODY_OK) {
+        nbody_destroy(c);
+        *out = nullptr;
+        return st;
+    }
+    return NBODY_OK;
+}
+
+nbody_status nbody_forest_forces(nbody_ctx *c, const double *d_pos, const double *d_mass,
+                                 double *d_acc)
+{
+    if (!c) return NBODY_EINVAL;
+    if (c->n_sys == 0) return fail(c, NBODY_ESTATE, "not a forest context");
+    if (!d_pos || !d_mass || !d_acc) return fail(c, NBODY_EINVAL, "null pointer");
+    CKS(begin_timing(c));
+    CKS(forest_build(c, d_pos, d_mass));
+    CKS(walk(c, (int)c->cap, d_acc, nullptr, 0.0));
+    return end_timing(c);
+}
+
+nbody_status nbody_forest_step(nbody_ctx *c, double *d_pos, double *d_vel, const double *d_mass,
+                               int32_t nsteps, int32_t use_graph)
+{
+    if (!c) return NBODY_EINVAL;
+    if (c->n_sys == 0) return fail(c, NBODY_ESTATE, "not a forest context");
+    if (nsteps < 0) return fail(c, NBODY_EINVAL, "nsteps < 0");
+    if (!d_pos || !d_vel || !d_mass) return fail(c, NBODY_EINVAL, "null pointer");
+    if (nsteps == 0) return NBODY_OK;
+    const int64_t n = c->cap;
+    if (c->acc_n != n) {
+        CKS(forest_build(c, d_pos, d_mass));
+        CKS(walk(c, (int)n, c->acc, nullptr, 0.0));
+        c->acc_n = n;
+    }
+    if (!use_graph) {
+        for (int32_t k = 0; k < nsteps; ++k) {
+            CKS(begin_timing(c));
+            CKS(forest_step_once(c, d_pos, d_vel, d_mass));
+            CKS(end_timing(c));
+        }
+        return NBODY_OK;
+    }
+    if (!c->gstream) {
+        CK(cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking));
+        for (int k = 0; k < 2; ++k) CK(cudaEventCreateWithFlags(&c->gev[k], cudaEventDisableTiming));
+    }
+    const void *key[3] = {d_pos, d_vel, d_mass};
+    if (!c->gexec || memcmp(key, c->gkey, sizeof(key)) != 0) {
+        if (c->gexec) {
+            cudaGraphExecDestroy(c->gexec);
+            c->gexec = nullptr;
+        }
+        // the caller's stream must reach this point before the captured work may run
+        CK(cudaEventRecord(c->gev[0], c->stream));
+        CK(cudaStreamWaitEvent(c->gstream, c->gev[0], 0));
+        CK(cudaStreamSynchronize(c->gstream));
+        cudaStream_t user = c->stream;
+        const bool timing = c->timing;
+        c->stream = c->gstream;
+        c->timing = false;
+        const int64_t l0 = launch_count();
+        CK(cudaStreamBeginCapture(c->gstream, cudaStreamCaptureModeThreadLocal));
+        const nbody_status st = forest_step_once(c, d_pos, d_vel, d_mass);
+        cudaGraph_t g = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(c->gstream, &g);
+        c->stream = user;
+        c->timing = timing;
+        const int64_t k = launch_count() - l0;  // recorded, not launched
+        count_launches((int)-k);
+        if (st != NBODY_OK || e != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            if (st != NBODY_OK) return st;
+            return fail(c, NBODY_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+        }
+        const cudaError_t ei = cudaGraphInstantiate(&c->gexec, g, 0);
+        cudaGraphDestroy(g);
+        if (ei != cudaSuccess) {
+            c->gexec = nullptr;
+            return fail(c, NBODY_ECUDA, "graph instantiate: %s", cudaGetErrorString(ei));
+        }
+        c->glaunches = k;
+        memcpy(c->gkey, key, sizeof(key));
+    }
+    CK(cudaEventRecord(c->gev[0], c->stream));
+    CK(cudaStreamWaitEvent(c->gstream, c->gev[0], 0));
+    for (int32_t s = 0; s < nsteps; ++s) {
+        CK(cudaGraphLaunch(c->gexec, c->gstream));
+        count_launches((int)c->glaunches);
+    }
+    CK(cudaEventRecord(c->gev[1], c->gstream));
+    CK(cudaStreamWaitEvent(c->stream, c->gev[1], 0));
+    c->n_forces = n;
     return NBODY_OK;
 }
 

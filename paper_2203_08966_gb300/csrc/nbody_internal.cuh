@@ -49,6 +49,16 @@ struct LevelTables {
     float crit32[kLevels];   // l2 / theta^2 as FP32 (+inf when theta == 0)
 };
 
+// The systems of a forest.  sys[i] is the system of body i; the bodies of system k are
+// start[k] .. start[k+1] - 1, both in the caller's order and in sorted order (the sort keeps every
+// body inside its system's range).  A single system is {nullptr, nullptr, 1}.
+struct Systems {
+    const uint16_t *sys;
+    const int *start;
+    int count;
+};
+constexpr int kMaxSystems = 65535;
+
 // Process-wide count of kernel launches made by the library (every launcher adds its launches).
 void count_launches(int k);
 int64_t launch_count();
@@ -63,15 +73,22 @@ void launch_kick_drift_bbox(double *pos, double *vel, const double *acc, const d
                             cudaStream_t s);
 void launch_bbox_finalize(const double *partials, int nblk, Box *box, LevelTables *tab,
                           double theta, cudaStream_t s);
-void launch_keys(const double *pos, int n, const Box *box, uint64_t *keys, uint32_t *ids,
-                 cudaStream_t s);
+// Forest: kick + drift of all bodies, then one box (and level tables) per system.
+void launch_kick_drift(double *pos, double *vel, const double *acc, int n, double h, double dt,
+                       cudaStream_t s);
+void launch_system_boxes(const double *pos, const double *mass, int n, const Systems &ss,
+                         Box *box, LevelTables *tab, double theta, cudaStream_t s);
+void launch_keys(const double *pos, int n, const Box *box, const Systems &ss, uint64_t *keys,
+                 uint32_t *ids, cudaStream_t s);
 
 struct SortScratch {
     uint64_t *keys_alt;
     uint32_t *ids_alt;
-    uint32_t *hist;       // 8 x 256 digit totals
+    uint32_t *hist;       // 10 x 256 digit totals (8 key passes, 2 system passes)
     uint32_t *counts;     // 256 x tiles
     int max_tiles;
+    const uint16_t *sys;  // forest: two more stable passes on the system of every id
+    const uint32_t *sys_hist;  // their digit totals (2 x 256, fixed per forest)
 };
 int sort_tiles(int n);
 cudaError_t sort_prepare(); // one-time function attributes
@@ -79,38 +96,47 @@ void launch_radix_sort(uint64_t *keys, uint32_t *ids, int n, const SortScratch &
                        cudaStream_t s);
 
 void launch_permute(const double *pos, const double *mass, const uint32_t *ids, int n,
-                    const Box *box, double G, D4 *sbody64, float4 *sbody32, cudaStream_t s);
+                    const Box *box, const Systems &ss, double G, D4 *sbody64, float4 *sbody32,
+                    cudaStream_t s);
 
 struct ScanScratch {
     uint32_t *block_sums;  // tiles + 1
     int max_tiles;
 };
 int scan_tiles(int len);
-void launch_count_nodes(const uint64_t *keys, int n, uint32_t *counts, unsigned *max_level,
-                        cudaStream_t s);
+void launch_count_nodes(const uint64_t *keys, int n, const Systems &ss, uint32_t *counts,
+                        unsigned *max_level, cudaStream_t s);
 void launch_exclusive_scan(const uint32_t *in, uint32_t *out, int len, const ScanScratch &sc,
                            cudaStream_t s);
 
 // Node kind byte: the level of an internal cell, kLeafKind for a leaf.
 constexpr uint8_t kLeafKind = 0x80;
 
+// Nodes in pre-order (capacity `cap`).  The node count lives on the device (d_nn, the last
+// entry of the node offsets); kernels that loop over nodes read it there.
 struct NodeArrays {
     WalkNode *wn;
     D4 *com64;
     uint8_t *level;
     uint8_t *mask;
     uint8_t *kind;
-    int *level_list;          // internal cells grouped by level (cap entries)
-    unsigned *level_count;    // kLevels counters
-    unsigned *level_start;    // kLevels + 1 offsets into level_list
-    unsigned *level_cursor;   // kLevels scatter cursors
+    int *order;               // pre-order index -> level-order index
+    int *inv;                 // level-order index -> pre-order index
+    uint32_t *tile_offsets;   // level-major (level, tile) offsets; level l starts at [l * tiles]
+    uint32_t *block_sums;     // scan scratch for tile_offsets
+    const uint32_t *d_nn;     // node count (device)
+    int tiles;                // layout tiles for `cap` nodes
     int64_t cap;
 };
-void launch_emit_nodes(const uint64_t *keys, int n, const uint32_t *node_off, NodeArrays na,
-                       cudaStream_t s);
-// Child masks, node kinds, leaf moments, then the internal cells level by level up to the root.
-void launch_moments(const uint64_t *keys, int n_nodes, int max_level, const D4 *sbody64,
-                    const Box *box, const LevelTables *tab, double G, NodeArrays na,
+// Node split; nodes past `cap` are not written and set kErrNodeCap in *err.
+void launch_emit_nodes(const uint64_t *keys, int n, const Systems &ss, const uint32_t *node_off,
+                       NodeArrays na, int *err, cudaStream_t s);
+// Stable partition of the nodes by level (order, inv, per-level starts).
+void launch_level_order(const NodeArrays &na, cudaStream_t s);
+// Child masks, node kinds, leaf moments, then the internal cells level by level (levels
+// max_level - 1 .. 0) up to the roots.
+void launch_moments(const uint64_t *keys, int max_level, const D4 *sbody64, const Box *box,
+                    const LevelTables *tab, const Systems &ss, double G, NodeArrays na,
                     cudaStream_t s);
 
 // Level-order copy of the octree read by the FP32 group walk.  Nodes are ordered by level, and
@@ -132,17 +158,16 @@ struct alignas(16) GroupNode {
 // Node indices of the group walk's stack entries have 28 bits.
 constexpr int64_t kMaxGroupNodes = (int64_t)1 << 28;
 
-struct LayoutScratch {
-    uint32_t *tile_offsets;  // kLevels x tiles (+1), level-major
-    uint32_t *block_sums;    // scan scratch for the tile offsets
-    int *order;              // pre-order index -> level-order index
-    int max_tiles;
-};
 int layout_tiles(int64_t n_nodes);
 int layout_scan_len(int64_t n_nodes);
-// Stable partition of the nodes by level, then the GroupNode records.
-void launch_level_order(const NodeArrays na, int n_nodes, const LayoutScratch &ls,
-                        GroupNode *gn, cudaStream_t s);
+// GroupNode records at their level-order positions (after the moments).
+void launch_group_nodes(const NodeArrays &na, GroupNode *gn, cudaStream_t s);
+// Forest: *nn = *total when it fits in cap nodes, else 0 with kErrNodeCap set.
+void launch_clamp_count(const uint32_t *total, int64_t cap, uint32_t *nn, int *err,
+                        cudaStream_t s);
+// Forest: level-order index of every system's root.
+void launch_roots(const NodeArrays &na, const uint32_t *node_off, const Systems &ss, int *roots,
+                  cudaStream_t s);
 
 // ---------------------------------------------------------------- walk_kernels.cu
 struct WalkArgs {
@@ -150,7 +175,6 @@ struct WalkArgs {
     const D4 *com64;
     const uint8_t *level;
     const LevelTables *tab;
-    int n_nodes;
     const D4 *sbody64;
     const float4 *sbody32;
     const uint32_t *ids;
@@ -162,6 +186,13 @@ struct WalkArgs {
     uint32_t *pp, *pc;    // n, sorted order
     const GroupNode *gn;  // level-order tree (FP32 walks)
     int *err;             // device error word (kErrStack)
+    const uint32_t *d_nn; // node count (device)
+    // forest: the walk runs over groups of <= 32 bodies of one system each
+    const int4 *groups;   // (first body, count, system, 0); null for a single system
+    int n_groups;
+    const int *roots;     // level-order index of each system's root
+    const uint32_t *node_off;  // pre-order: nodes of system k are node_off[start[k]] ..
+    const int *start;     // system starts (bodies)
 };
 void launch_walk(int precision, const WalkArgs &a, cudaStream_t s);
 

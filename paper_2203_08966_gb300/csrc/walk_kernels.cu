@@ -192,6 +192,27 @@ __device__ __forceinline__ void axis_bounds(float c, float lo, float hi, float &
     dmax = fmaxf(fabsf(a), fabsf(b));
 }
 
+// The group walked by warp gi: its first sorted body, its size (1..32) and the level-order index
+// of its system's root.  A single system is cut into groups of 32 from body 0; a forest lists
+// its groups (none crosses a system boundary).
+__device__ __forceinline__ bool group_of(const WalkArgs &a, int gi, int &g0, int &count,
+                                         int &root)
+{
+    if (a.groups) {
+        if (gi >= a.n_groups) return false;
+        const int4 g = a.groups[gi];
+        g0 = g.x;
+        count = g.y;
+        root = a.roots[g.z];
+        return true;
+    }
+    g0 = gi * 32;
+    if (g0 >= a.n) return false;
+    count = min(32, a.n - g0);
+    root = 0;
+    return true;
+}
+
 template <bool kKahan, bool kGuard>
 struct GroupEval {
     Acc3<kKahan> acc;
@@ -240,14 +261,16 @@ __global__ void __launch_bounds__(kGThreads) group_walk32_kernel(WalkArgs a)
     __shared__ GroupSmem smem[kGWarps];
     GroupSmem &S = smem[threadIdx.x >> 5];
     const int lane = threadIdx.x & 31;
-    const int g0 = (blockIdx.x * kGWarps + (threadIdx.x >> 5)) * 32;
-    if (g0 >= a.n) return;  // uniform per warp
+    const int gi = blockIdx.x * kGWarps + (threadIdx.x >> 5);
+    int g0, gcount, root;
+    if (!group_of(a, gi, g0, gcount, root)) return;  // uniform per warp
     const int i = g0 + lane;
-    const bool live = i < a.n;
+    const bool live = lane < gcount;
+    const int n_nodes = (int)*a.d_nn;
     const unsigned lt = lanemask_lt_w();
     const unsigned live_mask = __ballot_sync(kFull, live);
-    // lanes past the end stand on the last body so that they do not widen the group box
-    const float4 me = ldg4(a.sbody32 + min(i, a.n - 1));
+    // lanes past the group's end stand on its last body so that they do not widen its box
+    const float4 me = ldg4(a.sbody32 + g0 + min(lane, gcount - 1));
     const float lox = warp_fmin(me.x), loy = warp_fmin(me.y), loz = warp_fmin(me.z);
     const float hix = warp_fmax(me.x), hiy = warp_fmax(me.y), hiz = warp_fmax(me.z);
     const float eps2 = (float)(a.eps * a.eps);
@@ -258,8 +281,8 @@ __global__ void __launch_bounds__(kGThreads) group_walk32_kernel(WalkArgs a)
 
     // the root is never tested: the walk starts with the root's children (none when the root
     // is a leaf, i.e. a single body)
-    if (a.n_nodes >= 2) {
-        const int4 r = __ldg(reinterpret_cast<const int4 *>(&a.gn[0].child));
+    if (root >= 0 && root < n_nodes) {
+        const int4 r = __ldg(reinterpret_cast<const int4 *>(&a.gn[root].child));
         if (r.y > 0) {
             if (lane == 0) {
                 S.st_node[0] = (uint32_t)r.x | ((uint32_t)(r.y - 1) << 28);
@@ -298,7 +321,7 @@ __global__ void __launch_bounds__(kGThreads) group_walk32_kernel(WalkArgs a)
 
     // every node is popped at most once per group, so more steps than nodes means a malformed
     // tree: stop with the error word set rather than loop
-    int steps_left = a.n_nodes;
+    int steps_left = n_nodes;
     while (sp > 0) {
         if (sp > kStackCap - 32 || --steps_left < 0) {  // cannot happen (see kStackCap)
             if (lane == 0) atomicOr(a.err, kErrStack);
@@ -346,7 +369,7 @@ __global__ void __launch_bounds__(kGThreads) group_walk32_kernel(WalkArgs a)
 
         // ---- load the popped nodes (one per lane)
         const int node0 = (int)(ek & kIdxMask) + off;
-        const bool bad = lane < items && node0 >= a.n_nodes;
+        const bool bad = lane < items && node0 >= n_nodes;
         if (bad) atomicOr(a.err, kErrStack);
         const bool has = lane < items && !bad;
         const int node = has ? node0 : 0;
@@ -440,7 +463,7 @@ __global__ void __launch_bounds__(kGThreads) group_walk32_kernel(WalkArgs a)
             for (int base = 0; base < nb; base += 32) {
                 if (fn > kFCap - 32 || pn > kPCap - 32) drain();
                 const bool h = base + lane < nb;
-                const int b = min(b0i + base + lane, a.n - 1);
+                const int b = min(b0i + base + lane, b0i + nb - 1);
                 const float4 s = h ? ldg4(a.sbody32 + b) : make_float4(0.f, 0.f, 0.f, 0.f);
                 unsigned mb = sm;
                 const unsigned d = (unsigned)(b - g0);
@@ -460,11 +483,20 @@ __global__ void __launch_bounds__(kGThreads) group_walk32_kernel(WalkArgs a)
 __global__ void __launch_bounds__(kWalkThreads) walk64_kernel(WalkArgs a)
 {
     const int lane = threadIdx.x & 31;
-    const int warp = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
-    const int i = warp * 32 + lane;
-    if (warp * 32 >= a.n) return;
-    const bool live = i < a.n;
-    const int n_nodes = a.n_nodes;
+    const int gi = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
+    int g0, gcount, root_lo;
+    if (!group_of(a, gi, g0, gcount, root_lo)) return;  // uniform per warp
+    const int i = g0 + lane;
+    const bool live = lane < gcount;
+    // pre-order nodes of the group's system: [first, end)
+    int first = 0, n_nodes = (int)*a.d_nn;
+    const LevelTables *tab = a.tab;  // the group's system's cell sizes
+    if (a.groups) {
+        const int k = a.groups[gi].z;
+        first = (int)a.node_off[a.start[k]];
+        n_nodes = min(n_nodes, (int)a.node_off[a.start[k + 1]]);
+        tab += k;
+    }
     const double G = a.G;
     const double eps2 = __dmul_rn(a.eps, a.eps);
     const double th2 = __dmul_rn(a.theta, a.theta);
@@ -473,7 +505,8 @@ __global__ void __launch_bounds__(kWalkThreads) walk64_kernel(WalkArgs a)
     if (live) me = a.sbody64[i];
     double ax = 0.0, ay = 0.0, az = 0.0;
     uint32_t pp = 0, pc = 0;
-    int next = (!live || n_nodes < 2 || __ldg(&a.wn[0].count) != 0) ? n_nodes : 1;
+    int next = (!live || n_nodes - first < 2 || __ldg(&a.wn[first].count) != 0) ? n_nodes
+                                                                                : first + 1;
     for (;;) {
         const int j = __reduce_min_sync(kFull, next);
         if (j >= n_nodes) break;
@@ -495,7 +528,7 @@ __global__ void __launch_bounds__(kWalkThreads) walk64_kernel(WalkArgs a)
                          dz = __dsub_rn(s.z, me.z);
             const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)),
                                         __dmul_rn(dz, dz));
-            const double l2 = a.tab->l2[a.level[j]];
+            const double l2 = tab->l2[a.level[j]];
             if (l2 < __dmul_rn(th2, d2)) {
                 pair64(s.x, s.y, s.z, s.w, me.x, me.y, me.z, G, eps2, ax, ay, az);
                 ++pc;
@@ -621,12 +654,13 @@ void launch_walk(int precision, const WalkArgs &a, cudaStream_t s)
 {
     if (a.n <= 0) return;
     const bool guard = !(a.eps > 0.0);
+    const int64_t groups = a.groups ? (int64_t)a.n_groups : ((int64_t)a.n + 31) / 32;
+    if (groups <= 0) return;
     if (precision == NBODY_FP64) {
-        const int64_t threads = ((int64_t)a.n + 31) / 32 * 32;
-        const int blocks = (int)((threads + kWalkThreads - 1) / kWalkThreads);
+        const int per_block = kWalkThreads / 32;
+        const int blocks = (int)((groups + per_block - 1) / per_block);
         walk64_kernel<<<blocks, kWalkThreads, 0, s>>>(a);
     } else {
-        const int64_t groups = ((int64_t)a.n + 31) / 32;
         const int blocks = (int)((groups + kGWarps - 1) / kGWarps);
         if (precision == NBODY_FP32_KAHAN) {
             if (guard) group_walk32_kernel<true, true><<<blocks, kGThreads, 0, s>>>(a);

@@ -5,6 +5,7 @@ import os
 import re
 import subprocess
 
+import numpy as np
 import pytest
 
 import paper_2203_08966_gb300 as nb
@@ -59,3 +60,27 @@ def test_null_context_is_rejected_without_gpu(lib_path):
     assert lib.nbody_destroy(None) == 1
     assert lib.nbody_sync(None) == 1
     assert lib.nbody_create(None, 10, None, None) == 1
+
+
+def test_forest_create_rejects_bad_offsets_without_gpu(lib_path):
+    """nbody_forest_create validates its host arguments before touching the device."""
+    lib = nb.load_library(lib_path)
+    p = nb.Params(1.0, 0.01, 0.5, 1e-3, nb.FP32, 0)
+    h = ctypes.c_void_p()
+
+    def create(off, S=None):
+        off = np.ascontiguousarray(off, dtype=np.int64)
+        S = len(off) - 1 if S is None else S
+        return lib.nbody_forest_create(ctypes.byref(h), S, off.ctypes.data_as(ctypes.c_void_p),
+                                       ctypes.byref(p), None)
+
+    assert create([1, 5]) == 1            # offsets[0] != 0
+    assert create([0, 5, 3]) == 1         # decreasing
+    assert create([0, 0, 0]) == 1         # no bodies at all
+    assert create([0, 4], S=0) == 1       # no systems
+    bad = nb.Params(1.0, -1.0, 0.5, 1e-3, nb.FP32, 0)
+    off = np.array([0, 4], dtype=np.int64)
+    assert lib.nbody_forest_create(ctypes.byref(h), 1, off.ctypes.data_as(ctypes.c_void_p),
+                                   ctypes.byref(bad), None) == 1   # eps < 0
+    assert lib.nbody_forest_create(None, 1, off.ctypes.data_as(ctypes.c_void_p),
+                                   ctypes.byref(p), None) == 1
