@@ -211,6 +211,8 @@ def measure_batch(nb, torch, dev, stream, steps=100):
     tv = torch.from_numpy(vel).to(dev)
     tm = torch.from_numpy(mass).to(dev)
     ctx = nb.Context.forest(off, 1.0, w["eps"], w["theta"], w["dt"], nb.FP32_KAHAN, stream=stream)
+    shape, shape_ms = ctx.autotune(tp, tm)
+    shape_threads = ctx.walk_shape()[1]
     ctx.forest_step(tp, tv, tm, 4, use_graph=True)     # a^(0), capture, warm-up replays
     ctx.forest_step(tp, tv, tm, 3, use_graph=False)    # warm-up of the launched form
     ctx.sync()
@@ -235,6 +237,8 @@ def measure_batch(nb, torch, dev, stream, steps=100):
             "bodies_per_s": n * steps / (ms * 1e-3), "ms_per_step": ms / steps,
             "ms_per_step_launched": ms_launched, "steps": steps, "graph": True,
             "gpu_launches": int(launches), "precision": "fp32_kahan",
+            "walk_shape": {"chosen": shape, "threads_per_block": shape_threads,
+                           "autotune_ms": shape_ms},
             "theta": w["theta"], "eps": w["eps"], "dt": w["dt"]}
 
 
@@ -357,6 +361,8 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
 
     ctx = nb.Context(n, 1.0, w["eps"], w["theta"], w["dt"], prec, stream=stream)
+    shape, shape_ms = ctx.autotune(tp, tm)   # launch shape of the walk, before any timing
+    shape_threads = ctx.walk_shape()[1]
     ctx.enable_timing(True)
     for _ in range(args.warmup):
         ctx.step(tp, tv, tm, 1)
@@ -451,7 +457,9 @@ def run_ours(args):
         "data": "synthetic",
         "config": {"workload": f"{args.workload}", "n": n, "theta": w["theta"], "eps": w["eps"],
                    "dt": w["dt"], "precision": args.precision,
-                   "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas{ws}"},
+                   "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas{ws}",
+                   "walk_shape": {"chosen": shape, "threads_per_block": shape_threads,
+                                  "autotune_ms": shape_ms}},
         "phase_ms": {k: float(v / args.steps) for k, v in
                      zip(("kick_box_keys", "sort", "permute_split_moments", "walk", "step"),
                          phase)},

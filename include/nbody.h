@@ -174,6 +174,30 @@ nbody_status nbody_get_timings(nbody_ctx *c, float *h_ms5);
  * can count the launches inside a timed region.  Errors: EINVAL when out == NULL. */
 nbody_status nbody_get_launch_count(int64_t *out);
 
+/* ---- launch-shape autotuning of the walk ---- */
+
+/* Number of launch shapes of the walk: for the FP32 forms 2, 4 or 8 warps per block (one warp
+ * per group of 32 bodies), for FP64 64, 128 or 256 threads per block.  The shape changes only
+ * how groups map to blocks, never a result. */
+#define NBODY_WALK_SHAPES 3
+
+/* Builds the tree of d_pos/d_mass (n bodies; for a forest context n is ignored and the whole
+ * forest is used), times the walk in every launch shape for the context's precision (3 walks
+ * each after a warm-up, CUDA events on the context stream; the call waits for them) and keeps
+ * the fastest for every later walk of that precision class.  h_ms (host, may be NULL):
+ * receives the mean time of each shape in ms (NBODY_WALK_SHAPES floats); chosen (may be NULL):
+ * the shape kept.  The kept acceleration of nbody_step is recomputed by the next step.
+ * Errors as nbody_forces; on error the default shape (1) is kept. */
+nbody_status nbody_autotune(nbody_ctx *c, const double *d_pos, const double *d_mass, int64_t n,
+                            float *h_ms, int32_t *chosen);
+
+/* Sets the walk shape (0 .. NBODY_WALK_SHAPES - 1) for the context's precision class without
+ * timing anything.  Errors: EINVAL for a shape out of range. */
+nbody_status nbody_set_walk_shape(nbody_ctx *c, int32_t shape);
+
+/* The walk shape in use for the context's precision and its threads per block. */
+nbody_status nbody_get_walk_shape(nbody_ctx *c, int32_t *shape, int32_t *threads_per_block);
+
 /* ---- forest: many independent systems advanced together ---- */
 
 /* Creates a context for n_systems independent systems packed into one set of arrays: system k

@@ -20,6 +20,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libnbody.so")
 
 FP64, FP32, FP32_KAHAN = 0, 1, 2
+WALK_SHAPES = 3  # NBODY_WALK_SHAPES
 PRECISIONS = {"fp64": FP64, "fp32": FP32, "fp32_kahan": FP32_KAHAN}
 
 STATUS = {0: "NBODY_OK", 1: "NBODY_EINVAL", 2: "NBODY_ENOMEM", 3: "NBODY_ECUDA",
@@ -31,7 +32,8 @@ EXPORTS = ("nbody_create", "nbody_destroy", "nbody_set_params", "nbody_build_tre
            "nbody_get_keys", "nbody_get_box", "nbody_get_tree", "nbody_get_moments",
            "nbody_get_counters", "nbody_enable_timing", "nbody_get_timings",
            "nbody_last_error", "nbody_get_launch_count", "nbody_sort_keys_noalloc",
-           "nbody_forest_create", "nbody_forest_forces", "nbody_forest_step")
+           "nbody_forest_create", "nbody_forest_forces", "nbody_forest_step",
+           "nbody_autotune", "nbody_set_walk_shape", "nbody_get_walk_shape")
 
 
 class NBodyError(RuntimeError):
@@ -91,6 +93,9 @@ def load_library(path: str = LIB_PATH):
         "nbody_forest_create": [ctypes.POINTER(vp), i32, vp, P, vp],
         "nbody_forest_forces": [vp, vp, vp, vp],
         "nbody_forest_step": [vp, vp, vp, vp, i32, i32],
+        "nbody_autotune": [vp, vp, vp, i64, vp, vp],
+        "nbody_get_walk_shape": [vp, vp, vp],
+        "nbody_set_walk_shape": [vp, i32],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -271,6 +276,28 @@ class Context:
                                                 _dptr(mass, torch.float64, (n,), "mass"),
                                                 int(nsteps), 1 if use_graph else 0),
                     "nbody_forest_step")
+
+    def autotune(self, pos, mass):
+        """Times every launch shape of the walk on this input and keeps the fastest; returns
+        (chosen shape, per-shape ms)."""
+        import torch
+        n = self.capacity if getattr(self, "offsets", None) is not None else int(mass.shape[0])
+        ms = (ctypes.c_float * WALK_SHAPES)()
+        chosen = ctypes.c_int32()
+        self._check(self._lib.nbody_autotune(self._h, _dptr(pos, torch.float64, (3, n), "pos"),
+                                             _dptr(mass, torch.float64, (n,), "mass"), n,
+                                             ms, ctypes.byref(chosen)), "nbody_autotune")
+        return int(chosen.value), [float(x) for x in ms]
+
+    def set_walk_shape(self, shape):
+        self._check(self._lib.nbody_set_walk_shape(self._h, int(shape)), "nbody_set_walk_shape")
+
+    def walk_shape(self):
+        """(shape index, threads per block) of the walk for this context's precision."""
+        k, t = ctypes.c_int32(), ctypes.c_int32()
+        self._check(self._lib.nbody_get_walk_shape(self._h, ctypes.byref(k), ctypes.byref(t)),
+                    "nbody_get_walk_shape")
+        return int(k.value), int(t.value)
 
     def sync(self):
         self._check(self._lib.nbody_sync(self._h), "nbody_sync")

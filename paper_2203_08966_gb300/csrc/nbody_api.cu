@@ -60,6 +60,9 @@ struct nbody_ctx {
     int64_t glaunches = 0;          // kernels per replayed step
     cudaEvent_t gev[2] = {};
 
+    // launch shape of the walk per precision class (FP32 forms, FP64), set by nbody_autotune
+    int shape32 = kDefaultWalkShape, shape64 = kDefaultWalkShape;
+
     // host-buffer stepping
     double *hpos = nullptr, *hvel = nullptr, *hmass = nullptr;
 
@@ -261,7 +264,8 @@ nbody_status walk(nbody_ctx *c, int n, double *acc, double *vel, double h)
     a.roots = c->roots;
     a.node_off = c->node_off;
     a.start = c->sys_start;
-    launch_walk(c->p.precision, a, c->stream);
+    launch_walk(c->p.precision, a, c->p.precision == NBODY_FP64 ? c->shape64 : c->shape32,
+                c->stream);
     record(c, 4);
     CKS(check_launch(c, "walk"));
     c->n_forces = n;
@@ -351,6 +355,7 @@ nbody_status nbody_create(nbody_ctx **out, int64_t n_capacity, const nbody_param
     auto body = [&]() -> nbody_status {
         CK(cudaGetDevice(&c->device));
         CK(sort_prepare());
+        CK(walk_prepare());
         const size_t cap = (size_t)std::max<int64_t>(n_capacity, 1);
         CK(dalloc(&c->keys, cap));
         CK(dalloc(&c->keys_alt, cap));
@@ -693,6 +698,84 @@ nbody_status nbody_last_error(nbody_ctx *c, char *buf, int64_t cap)
 {
     if (!c || !buf || cap <= 0) return NBODY_EINVAL;
     snprintf(buf, (size_t)cap, "%s", c->msg);
+    return NBODY_OK;
+}
+
+// ---------------------------------------------------------------- autotuning
+
+nbody_status nbody_autotune(nbody_ctx *c, const double *d_pos, const double *d_mass, int64_t n,
+                            float *h_ms, int32_t *chosen)
+{
+    if (!c) return NBODY_EINVAL;
+    if (c->n_sys) n = c->cap;
+    CKS(check_n(c, n));
+    if (n > 0 && (!d_pos || !d_mass)) return fail(c, NBODY_EINVAL, "null pointer");
+    int &shape = c->p.precision == NBODY_FP64 ? c->shape64 : c->shape32;
+    if (n == 0) {
+        if (chosen) *chosen = shape;
+        return NBODY_OK;
+    }
+    const bool timing = c->timing;
+    c->timing = false;
+    nbody_status st = c->n_sys ? forest_build(c, d_pos, d_mass) : build(c, d_pos, d_mass, (int)n,
+                                                                        false);
+    float ms[kWalkShapes] = {0.f, 0.f, 0.f};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (st == NBODY_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
+        st = fail(c, NBODY_ECUDA, "event creation failed");
+    const int reps = 3;
+    for (int k = 0; k < kWalkShapes && st == NBODY_OK; ++k) {
+        shape = k;
+        st = walk(c, (int)n, c->acc, nullptr, 0.0);  // warm-up of this shape
+        if (st == NBODY_OK && cudaEventRecord(e0, c->stream) != cudaSuccess)
+            st = fail(c, NBODY_ECUDA, "event record failed");
+        for (int r = 0; r < reps && st == NBODY_OK; ++r) st = walk(c, (int)n, c->acc, nullptr, 0.0);
+        if (st == NBODY_OK && (cudaEventRecord(e1, c->stream) != cudaSuccess ||
+                               cudaEventSynchronize(e1) != cudaSuccess ||
+                               cudaEventElapsedTime(&ms[k], e0, e1) != cudaSuccess))
+            st = fail(c, NBODY_ECUDA, "timing the walk failed");
+        ms[k] /= (float)reps;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    c->timing = timing;
+    c->acc_n = -1;  // the walks above overwrote the kept acceleration
+    if (st != NBODY_OK) {
+        shape = kDefaultWalkShape;
+        return st;
+    }
+    int best = 0;
+    for (int k = 1; k < kWalkShapes; ++k)
+        if (ms[k] < ms[best]) best = k;
+    shape = best;
+    if (c->gexec) {  // a captured forest step holds the old shape
+        cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+    }
+    if (h_ms)
+        for (int k = 0; k < kWalkShapes; ++k) h_ms[k] = ms[k];
+    if (chosen) *chosen = best;
+    return NBODY_OK;
+}
+
+nbody_status nbody_set_walk_shape(nbody_ctx *c, int32_t shape)
+{
+    if (!c) return NBODY_EINVAL;
+    if (shape < 0 || shape >= kWalkShapes) return fail(c, NBODY_EINVAL, "shape %d", (int)shape);
+    (c->p.precision == NBODY_FP64 ? c->shape64 : c->shape32) = shape;
+    if (c->gexec) {
+        cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+    }
+    return NBODY_OK;
+}
+
+nbody_status nbody_get_walk_shape(nbody_ctx *c, int32_t *shape, int32_t *threads_per_block)
+{
+    if (!c) return NBODY_EINVAL;
+    const int k = c->p.precision == NBODY_FP64 ? c->shape64 : c->shape32;
+    if (shape) *shape = k;
+    if (threads_per_block) *threads_per_block = walk_shape_threads(c->p.precision, k);
     return NBODY_OK;
 }
 

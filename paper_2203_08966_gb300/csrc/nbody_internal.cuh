@@ -194,7 +194,12 @@ struct WalkArgs {
     const uint32_t *node_off;  // pre-order: nodes of system k are node_off[start[k]] ..
     const int *start;     // system starts (bodies)
 };
-void launch_walk(int precision, const WalkArgs &a, cudaStream_t s);
+// Launch shapes of the walks (see walk_shape_threads); results do not depend on the shape.
+constexpr int kWalkShapes = 3;
+constexpr int kDefaultWalkShape = 1;
+int walk_shape_threads(int precision, int shape);
+cudaError_t walk_prepare();  // one-time function attributes (dynamic shared memory)
+void launch_walk(int precision, const WalkArgs &a, int shape, cudaStream_t s);
 
 void launch_direct(int precision, const double *pos, const double *mass, int n,
                    const int64_t *targets, int nt, double G, double eps, const Box *box,

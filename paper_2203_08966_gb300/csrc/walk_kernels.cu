@@ -20,7 +20,6 @@ namespace nb {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kWalkThreads = 128;
 
 __device__ __forceinline__ float4 ldg4(const float4 *p) { return __ldg(p); }
 
@@ -143,8 +142,6 @@ __device__ __forceinline__ void write_out(const WalkArgs &a, int i, double ax, d
 // body reading each source by broadcast.
 // ------------------------------------------------------------------------------------------
 
-constexpr int kGWarps = 4;
-constexpr int kGThreads = kGWarps * 32;
 // Stack of child ranges.  Every step pops <= 32 nodes and pushes <= 1 range per popped node, all
 // one level deeper than the shallowest popped node; so the ranges pushed by one step lie
 // strictly deeper than everything left below them, and at most 21 such groups (levels 1..21) of
@@ -154,12 +151,75 @@ constexpr int kFCap = 64;    // full-group interaction buffer
 constexpr int kPCap = 64;    // partial interaction buffer
 constexpr uint32_t kIdxMask = 0x0fffffffu;  // node index bits of a stack entry; 3 bits count - 1
 
+// Interaction buffers hold sources in pairs for the packed (2 x FP32) pair kernel: entries
+// 2k and 2k+1 are f[2k] = (x0, x1, y0, y1) and f[2k+1] = (z0, z1, w0, w1).
 struct GroupSmem {
     uint32_t st_node[kStackCap];  // first node | (count - 1) << 28
     uint32_t st_mask[kStackCap];  // bodies of the group that still need these nodes
-    float4 f[kFCap];
-    float4 p[kPCap];
-    uint2 pm[kPCap];              // (body mask, 1 for a leaf body / 0 for a cell)
+    float4 f[kFCap];              // full-group sources, paired
+    float4 p[kPCap];              // partial sources, paired
+    uint2 pm[kPCap];              // (body mask, 1 for a leaf body / 0 for a cell) per entry
+};
+
+__device__ __forceinline__ void put_entry(float4 *buf, int e, const float4 &c)
+{
+    float *q = reinterpret_cast<float *>(buf + 2 * (e >> 1)) + (e & 1);
+    q[0] = c.x;
+    q[2] = c.y;
+    q[4] = c.z;
+    q[6] = c.w;
+}
+
+// Two softened pair terms at once with packed FP32 arithmetic (each component rounded exactly
+// as the scalar fmaf / add / mul): sources a = (x0, x1, y0, y1), b = (z0, z1, w0, w1); the
+// target's coordinates come negated.  The terms are added to two interleaved partial sums.
+template <bool kGuard>
+__device__ __forceinline__ void pair32x2(const float4 &a, const float4 &b, float2 nx, float2 ny,
+                                         float2 nz, float2 eps2, float2 &ax, float2 &ay,
+                                         float2 &az)
+{
+    const float2 dx = __fadd2_rn(make_float2(a.x, a.y), nx);
+    const float2 dy = __fadd2_rn(make_float2(a.z, a.w), ny);
+    const float2 dz = __fadd2_rn(make_float2(b.x, b.y), nz);
+    float2 r2 = __ffma2_rn(dz, dz, eps2);
+    r2 = __ffma2_rn(dy, dy, r2);
+    r2 = __ffma2_rn(dx, dx, r2);
+    float2 ri = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+    if (kGuard) {
+        ri.x = r2.x > 0.f ? ri.x : 0.f;
+        ri.y = r2.y > 0.f ? ri.y : 0.f;
+    }
+    const float2 f = __fmul2_rn(__fmul2_rn(make_float2(b.z, b.w), __fmul2_rn(ri, ri)), ri);
+    ax = __ffma2_rn(f, dx, ax);
+    ay = __ffma2_rn(f, dy, ay);
+    az = __ffma2_rn(f, dz, az);
+}
+
+// Packed accumulator: two interleaved FP32 partial sums per component.  Compensated form: the
+// partials are folded into a Kahan sum every kFold terms and at the end.
+template <bool kKahan>
+struct Acc3x2 {
+    static constexpr int kFold = 64;
+    float2 x = make_float2(0.f, 0.f), y = make_float2(0.f, 0.f), z = make_float2(0.f, 0.f);
+    float sx = 0.f, sy = 0.f, sz = 0.f;  // compensated total
+    float cx = 0.f, cy = 0.f, cz = 0.f;  // its compensation
+    __device__ __forceinline__ void fold()
+    {
+        if (kKahan) {
+            Acc3<true>::kahan(sx, cx, x.x + x.y);
+            Acc3<true>::kahan(sy, cy, y.x + y.y);
+            Acc3<true>::kahan(sz, cz, z.x + z.y);
+            x = y = z = make_float2(0.f, 0.f);
+        }
+    }
+    __device__ __forceinline__ float3 result()
+    {
+        if (kKahan) {
+            fold();
+            return make_float3(sx, sy, sz);
+        }
+        return make_float3(x.x + x.y, y.x + y.y, z.x + z.y);
+    }
 };
 
 enum : int { kNone = 0, kFullLeaf, kFullCell, kPartLeaf, kPartCell, kOpen, kMixed, kBucket };
@@ -215,53 +275,57 @@ __device__ __forceinline__ bool group_of(const WalkArgs &a, int gi, int &g0, int
 
 template <bool kKahan, bool kGuard>
 struct GroupEval {
-    Acc3<kKahan> acc;
+    Acc3x2<kKahan> acc;
     uint32_t pp = 0, pc = 0;      // partial entries of this lane's body: leaves, all
     int terms = 0;                // terms in the current partial (warp-uniform)
     __device__ __forceinline__ void settle(int cnt)
     {
         terms += cnt;
-        if (terms >= Acc3<kKahan>::kFold) {
+        if (terms >= Acc3x2<kKahan>::kFold) {
             acc.fold();
             terms = 0;
         }
     }
-    __device__ __forceinline__ void full(const GroupSmem &S, int cnt, const float4 &me, float eps2)
+    // cnt entries, padded to an even count by the caller (a zero-weight entry)
+    __device__ __forceinline__ void full(const GroupSmem &S, int cnt, const float2 *nme,
+                                         float2 eps2)
     {
-#pragma unroll 4
-        for (int e = 0; e < cnt; ++e) {
-            float tx, ty, tz;
-            pair32<kGuard>(S.f[e], me.x, me.y, me.z, eps2, tx, ty, tz);
-            acc.add(tx, ty, tz);
-        }
+        const int np = (cnt + 1) >> 1;
+#pragma unroll 2
+        for (int k = 0; k < np; ++k)
+            pair32x2<kGuard>(S.f[2 * k], S.f[2 * k + 1], nme[0], nme[1], nme[2], eps2, acc.x,
+                             acc.y, acc.z);
         settle(cnt);
     }
-    __device__ __forceinline__ void part(const GroupSmem &S, int cnt, const float4 &me, float eps2,
-                                         int lane)
+    __device__ __forceinline__ void part(const GroupSmem &S, int cnt, const float2 *nme,
+                                         float2 eps2, int lane)
     {
+        const int np = (cnt + 1) >> 1;
+        const uint4 *pm2 = reinterpret_cast<const uint4 *>(S.pm);
 #pragma unroll 2
-        for (int e = 0; e < cnt; ++e) {
-            float4 s = S.p[e];
-            const uint2 q = S.pm[e];
-            const uint32_t on = (q.x >> lane) & 1u;
-            s.w = on ? s.w : 0.f;
-            float tx, ty, tz;
-            pair32<kGuard>(s, me.x, me.y, me.z, eps2, tx, ty, tz);
-            acc.add(tx, ty, tz);
-            pp += on & q.y;   // leaf bodies
-            pc += on;         // all partial entries; the cells are pc - pp
+        for (int k = 0; k < np; ++k) {
+            const float4 a = S.p[2 * k];
+            float4 b = S.p[2 * k + 1];
+            const uint4 q = pm2[k];   // (mask0, leaf0, mask1, leaf1)
+            const uint32_t on0 = (q.x >> lane) & 1u, on1 = (q.z >> lane) & 1u;
+            b.z = on0 ? b.z : 0.f;
+            b.w = on1 ? b.w : 0.f;
+            pair32x2<kGuard>(a, b, nme[0], nme[1], nme[2], eps2, acc.x, acc.y, acc.z);
+            pp += (on0 & q.y) + (on1 & q.w);  // leaf bodies
+            pc += on0 + on1;                  // all partial entries; the cells are pc - pp
         }
         settle(cnt);
     }
 };
 
-template <bool kKahan, bool kGuard>
-__global__ void __launch_bounds__(kGThreads) group_walk32_kernel(WalkArgs a)
+// kWarps warps per block (a launch shape the autotuner chooses; results do not depend on it).
+template <int kWarps, bool kKahan, bool kGuard>
+__global__ void __launch_bounds__(kWarps * 32) group_walk32_kernel(WalkArgs a)
 {
-    __shared__ GroupSmem smem[kGWarps];
-    GroupSmem &S = smem[threadIdx.x >> 5];
+    extern __shared__ __align__(16) unsigned char group_smem[];
+    GroupSmem &S = reinterpret_cast<GroupSmem *>(group_smem)[threadIdx.x >> 5];
     const int lane = threadIdx.x & 31;
-    const int gi = blockIdx.x * kGWarps + (threadIdx.x >> 5);
+    const int gi = blockIdx.x * kWarps + (threadIdx.x >> 5);
     int g0, gcount, root;
     if (!group_of(a, gi, g0, gcount, root)) return;  // uniform per warp
     const int i = g0 + lane;
@@ -273,7 +337,10 @@ __global__ void __launch_bounds__(kGThreads) group_walk32_kernel(WalkArgs a)
     const float4 me = ldg4(a.sbody32 + g0 + min(lane, gcount - 1));
     const float lox = warp_fmin(me.x), loy = warp_fmin(me.y), loz = warp_fmin(me.z);
     const float hix = warp_fmax(me.x), hiy = warp_fmax(me.y), hiz = warp_fmax(me.z);
-    const float eps2 = (float)(a.eps * a.eps);
+    const float eps2s = (float)(a.eps * a.eps);
+    const float2 eps2 = make_float2(eps2s, eps2s);
+    const float2 nme[3] = {make_float2(-me.x, -me.x), make_float2(-me.y, -me.y),
+                           make_float2(-me.z, -me.z)};
 
     GroupEval<kKahan, kGuard> ev;
     uint32_t upp = 0, upc = 0;    // full-entry counts (the same for every live body)
@@ -296,7 +363,7 @@ __global__ void __launch_bounds__(kGThreads) group_walk32_kernel(WalkArgs a)
     auto emit = [&](int kind, const float4 &c, unsigned m) {
         const bool isf = kind == kFullLeaf || kind == kFullCell;
         const unsigned fb = __ballot_sync(kFull, isf);
-        if (isf) S.f[fn + __popc(fb & lt)] = c;
+        if (isf) put_entry(S.f, fn + __popc(fb & lt), c);
         fn += __popc(fb);
         const unsigned fl = __ballot_sync(kFull, kind == kFullLeaf);
         upp += __popc(fl);
@@ -305,16 +372,23 @@ __global__ void __launch_bounds__(kGThreads) group_walk32_kernel(WalkArgs a)
         const unsigned pb = __ballot_sync(kFull, isp);
         if (isp) {
             const int o = pn + __popc(pb & lt);
-            S.p[o] = c;
+            put_entry(S.p, o, c);
             S.pm[o] = make_uint2(m, kind == kPartLeaf ? 1u : 0u);
         }
         pn += __popc(pb);
     };
-    // evaluates and empties both buffers
+    // evaluates and empties both buffers (an odd count is padded with a zero-weight source)
     auto drain = [&]() {
+        if (lane == 0) {
+            if (fn & 1) put_entry(S.f, fn, make_float4(0.f, 0.f, 0.f, 0.f));
+            if (pn & 1) {
+                put_entry(S.p, pn, make_float4(0.f, 0.f, 0.f, 0.f));
+                S.pm[pn] = make_uint2(0u, 0u);
+            }
+        }
         __syncwarp();
-        if (fn > 0) ev.full(S, fn, me, eps2);
-        if (pn > 0) ev.part(S, pn, me, eps2, lane);
+        if (fn > 0) ev.full(S, fn, nme, eps2);
+        if (pn > 0) ev.part(S, pn, nme, eps2, lane);
         fn = pn = 0;
         __syncwarp();
     };
@@ -423,12 +497,13 @@ __global__ void __launch_bounds__(kGThreads) group_walk32_kernel(WalkArgs a)
             const float y1 = __shfl_sync(kFull, c.y, s1), y2 = __shfl_sync(kFull, c.y, s2);
             const float z1 = __shfl_sync(kFull, c.z, s1), z2 = __shfl_sync(kFull, c.z, s2);
             const float k1 = __shfl_sync(kFull, crit_l, s1), k2 = __shfl_sync(kFull, crit_l, s2);
-            const float dx1 = x1 - me.x, dy1 = y1 - me.y, dz1 = z1 - me.z;
-            const float dx2 = x2 - me.x, dy2 = y2 - me.y, dz2 = z2 - me.z;
-            const float q1 = fmaf(dx1, dx1, fmaf(dy1, dy1, dz1 * dz1));
-            const float q2 = fmaf(dx2, dx2, fmaf(dy2, dy2, dz2 * dz2));
-            const unsigned A1 = __ballot_sync(kFull, q1 > k1);
-            const unsigned A2 = __ballot_sync(kFull, q2 > k2);
+            // the per-body test, both cells at once (each component rounded as the scalar form)
+            const float2 dx = __fadd2_rn(make_float2(x1, x2), nme[0]);
+            const float2 dy = __fadd2_rn(make_float2(y1, y2), nme[1]);
+            const float2 dz = __fadd2_rn(make_float2(z1, z2), nme[2]);
+            const float2 q = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+            const unsigned A1 = __ballot_sync(kFull, q.x > k1);
+            const unsigned A2 = __ballot_sync(kFull, q.y > k2);
             if (lane == s1) myA = A1;
             if (lane == s2) myA = A2;
         }
@@ -480,7 +555,8 @@ __global__ void __launch_bounds__(kGThreads) group_walk32_kernel(WalkArgs a)
 
 // FP64 walk, operation for operation the plain per-particle definition: the MAC is
 // l^2 < theta^2 d^2 with l^2 of the cell's level and d the distance to its FP64 centre of mass.
-__global__ void __launch_bounds__(kWalkThreads) walk64_kernel(WalkArgs a)
+template <int kThreads>
+__global__ void __launch_bounds__(kThreads) walk64_kernel(WalkArgs a)
 {
     const int lane = threadIdx.x & 31;
     const int gi = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
@@ -650,25 +726,82 @@ __global__ void __launch_bounds__(kDirectThreads) direct64_kernel(
 
 }  // namespace
 
-void launch_walk(int precision, const WalkArgs &a, cudaStream_t s)
+namespace {
+
+// Launch shapes: FP32 group walk with 2 / 4 / 8 warps per block, FP64 walk with 64 / 128 / 256
+// threads per block.
+template <int kWarps>
+void launch_group(const WalkArgs &a, int64_t groups, bool kahan, bool guard, cudaStream_t s)
+{
+    const int blocks = (int)((groups + kWarps - 1) / kWarps);
+    const size_t smem = sizeof(GroupSmem) * kWarps;
+    if (kahan) {
+        if (guard) group_walk32_kernel<kWarps, true, true><<<blocks, kWarps * 32, smem, s>>>(a);
+        else group_walk32_kernel<kWarps, true, false><<<blocks, kWarps * 32, smem, s>>>(a);
+    } else {
+        if (guard) group_walk32_kernel<kWarps, false, true><<<blocks, kWarps * 32, smem, s>>>(a);
+        else group_walk32_kernel<kWarps, false, false><<<blocks, kWarps * 32, smem, s>>>(a);
+    }
+}
+
+template <int kWarps>
+cudaError_t allow_group_smem()
+{
+    const int bytes = (int)(sizeof(GroupSmem) * kWarps);
+    cudaError_t e = cudaSuccess;
+    const void *fns[4] = {(const void *)group_walk32_kernel<kWarps, true, true>,
+                          (const void *)group_walk32_kernel<kWarps, true, false>,
+                          (const void *)group_walk32_kernel<kWarps, false, true>,
+                          (const void *)group_walk32_kernel<kWarps, false, false>};
+    for (const void *f : fns) {
+        e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        if (e != cudaSuccess) return e;
+    }
+    return e;
+}
+
+template <int kThreads>
+void launch_w64(const WalkArgs &a, int64_t groups, cudaStream_t s)
+{
+    const int per_block = kThreads / 32;
+    const int blocks = (int)((groups + per_block - 1) / per_block);
+    walk64_kernel<kThreads><<<blocks, kThreads, 0, s>>>(a);
+}
+
+}  // namespace
+
+cudaError_t walk_prepare()
+{
+    cudaError_t e = allow_group_smem<2>();
+    if (e == cudaSuccess) e = allow_group_smem<4>();
+    if (e == cudaSuccess) e = allow_group_smem<8>();
+    return e;
+}
+
+int walk_shape_threads(int precision, int shape)
+{
+    static const int group_warps[kWalkShapes] = {2, 4, 8};
+    static const int w64_threads[kWalkShapes] = {64, 128, 256};
+    if (shape < 0 || shape >= kWalkShapes) shape = kDefaultWalkShape;
+    return precision == NBODY_FP64 ? w64_threads[shape] : 32 * group_warps[shape];
+}
+
+void launch_walk(int precision, const WalkArgs &a, int shape, cudaStream_t s)
 {
     if (a.n <= 0) return;
     const bool guard = !(a.eps > 0.0);
     const int64_t groups = a.groups ? (int64_t)a.n_groups : ((int64_t)a.n + 31) / 32;
     if (groups <= 0) return;
+    if (shape < 0 || shape >= kWalkShapes) shape = kDefaultWalkShape;
     if (precision == NBODY_FP64) {
-        const int per_block = kWalkThreads / 32;
-        const int blocks = (int)((groups + per_block - 1) / per_block);
-        walk64_kernel<<<blocks, kWalkThreads, 0, s>>>(a);
+        if (shape == 0) launch_w64<64>(a, groups, s);
+        else if (shape == 1) launch_w64<128>(a, groups, s);
+        else launch_w64<256>(a, groups, s);
     } else {
-        const int blocks = (int)((groups + kGWarps - 1) / kGWarps);
-        if (precision == NBODY_FP32_KAHAN) {
-            if (guard) group_walk32_kernel<true, true><<<blocks, kGThreads, 0, s>>>(a);
-            else group_walk32_kernel<true, false><<<blocks, kGThreads, 0, s>>>(a);
-        } else {
-            if (guard) group_walk32_kernel<false, true><<<blocks, kGThreads, 0, s>>>(a);
-            else group_walk32_kernel<false, false><<<blocks, kGThreads, 0, s>>>(a);
-        }
+        const bool kahan = precision == NBODY_FP32_KAHAN;
+        if (shape == 0) launch_group<2>(a, groups, kahan, guard, s);
+        else if (shape == 1) launch_group<4>(a, groups, kahan, guard, s);
+        else launch_group<8>(a, groups, kahan, guard, s);
     }
     count_launches(1);
 }

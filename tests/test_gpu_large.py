@@ -73,3 +73,13 @@ def test_two_plummer_16m_bench_configuration():
     pos, _, mass = ics.two_plummer(w["n"], seeds=w["seeds"])
     err = _check_system(pos, mass, w["eps"], w["theta"], 2048, 9, fp64_sample=False)
     print(f"two_plummer_16m FP32-Kahan rel. RMS vs oracle BH: {err:.2e}")
+
+
+def test_disk_bulge_64m_deep_tree():
+    """The deep, imbalanced stress case: exponential disk + Hernquist bulge, N = 67,108,864,
+    eps = 0.001, theta = 0.5 (keys, order and tree in full; FP32-Kahan forces on sampled
+    targets)."""
+    w = ics.WORKLOADS["disk_bulge_64m"]
+    pos, _, mass = ics.disk_bulge(w["n"], w["seed"])
+    err = _check_system(pos, mass, w["eps"], w["theta"], 1024, 13, fp64_sample=False)
+    print(f"disk_bulge_64m FP32-Kahan rel. RMS vs oracle BH: {err:.2e}")
