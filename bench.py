@@ -244,8 +244,9 @@ def measure_batch(nb, torch, dev, stream, steps=100):
 
 def measure_accuracy(nb, torch, dev, stream, n_targets=16384):
     """Force errors on the 1,048,576-body Plummer sphere (eps 0.005) against the FP64 direct
-    sum on 16,384 sampled targets, per theta, for the plain FP64 path and the FP32-Kahan path,
-    with the walk time of each on this GPU."""
+    sum on 16,384 sampled targets, per theta, for the plain FP64 path, the FP32-Kahan path and
+    the FP32-Kahan path with the grouped acceptance test (NBODY_FLAG_GROUP_MAC), with the walk
+    time of each on this GPU."""
     w = ics.WORKLOADS["plummer_1m"]
     pos, _, mass = ics.plummer(w["n"], w["seed"])
     n = w["n"]
@@ -270,8 +271,11 @@ def measure_accuracy(nb, torch, dev, stream, n_targets=16384):
     for theta in (0.3, 0.5, 0.7):
         row = {}
         res = {}
-        for name, prec in (("fp64", nb.FP64), ("fp32_kahan", nb.FP32_KAHAN)):
-            with nb.Context(n, 1.0, w["eps"], theta, w["dt"], prec, stream=stream) as ctx:
+        for name, prec, flags in (("fp64", nb.FP64, 0), ("fp32_kahan", nb.FP32_KAHAN, 0),
+                                  ("fp32_kahan_group_mac", nb.FP32_KAHAN, nb.FLAG_GROUP_MAC)):
+            with nb.Context(n, 1.0, w["eps"], theta, w["dt"], prec, stream=stream,
+                            flags=flags) as ctx:
+                ctx.autotune(tp, tm)
                 ctx.enable_timing(True)
                 a = ctx.forces(tp, tm)
                 t = ctx.timings()

@@ -67,7 +67,24 @@ typedef enum {
 
 /* Physical and numerical parameters.  G: gravitational constant; eps: Plummer softening length
  * (§2.1); theta: opening angle of the acceptance test l/d < theta (§3); dt: leapfrog time step
- * (§2.4); precision: nbody_precision; flags: 0 (reserved, must be 0). */
+ * (§2.4); precision: nbody_precision; flags: 0, or NBODY_FLAG_GROUP_MAC and/or
+ * NBODY_FLAG_CELL_GROUPS (FP32 forms only). */
+/* Flag: the grouped acceptance test of Barnes (1990) instead of the paper's per-body test
+ * (FP32 forms only; EINVAL with NBODY_FP64).  Bodies are taken in Morton order in groups of 32;
+ * a cell is accepted for all bodies of a group when l/d_min < theta, d_min being the distance
+ * from its centre of mass to the group's bounding box, and opened for all of them otherwise.
+ * Every body then sums a superset-refinement of its own per-body list: at least as many
+ * interactions, a smaller force error, different results and counters. */
+#define NBODY_FLAG_GROUP_MAC 1u
+
+/* Flag: the FP32 walk groups bodies by the tree's cells instead of in consecutive chunks of 32
+ * (FP32 forms only).  A group is a cell of at most 32 bodies whose parent holds more, with
+ * consecutive such siblings merged while they fit in 32, so a group never straddles a jump of
+ * the Morton curve.  Results are unchanged (each body keeps its own interaction list); only the
+ * summation order and the speed differ.  Always on with NBODY_FLAG_GROUP_MAC, whose shared lists
+ * need compact groups. */
+#define NBODY_FLAG_CELL_GROUPS 2u
+
 typedef struct {
     double G;
     double eps;

@@ -20,6 +20,10 @@ Parity status of each function (what pins it is in ``tests/test_oracle_pins.py``
                                          brute-force recursive walk on small N)
     kdk                                  pinned (time reversibility, second-order convergence,
                                          circular Kepler orbit)
+    bh_group (grouped acceptance test,   pinned (groups of one body equal the per-body walk term
+      Barnes 1990; not in the paper)     for term, theta = 0 equals direct sum, every body's
+                                         count >= its per-body count; cell groups: a partition
+                                         of the bodies into <= 32, each inside one tree cell)
     energy                               pinned (two-body closed form)
 """
 from __future__ import annotations
@@ -80,6 +84,8 @@ def _load():
         "orc_tree_records": (i64, [vp, _i64p, vp]),
         "orc_tree_moments": (i64, [vp, _f64p]),
         "orc_tree_forces": (None, [vp, vp, i64, d, d, d, _f64p, vp, vp]),
+        "orc_tree_cell_groups": (i64, [vp, i64, _i64p, _i64p]),
+        "orc_tree_forces_group": (None, [vp, _i64p, _i64p, i64, d, d, d, _f64p, vp, vp]),
         "orc_bh": (None, [_f64p, _f64p, i64, d, d, d, _f64p, vp, vp]),
         "orc_kdk": (None, [_f64p, _f64p, _f64p, i64, _f64p, d, d, d, d, ctypes.c_int32,
                            ctypes.c_int32]),
@@ -236,6 +242,54 @@ class Tree:
         pc = np.zeros(nt, dtype=np.uint32)
         _load().orc_tree_forces(self._h, _ptr(tp), nt, G, eps, theta, acc, _ptr(pp), _ptr(pc))
         return acc, pp, pc
+
+
+def bh_group(pos, mass, G=1.0, eps=0.0, theta=0.5, group=32, grouping="cells"):
+    """Group-walk accelerations (3, N) and counters pp, pc (N,) under the grouped acceptance
+    test (Barnes 1990; not in the paper): a cell is accepted for a whole group when its side and
+    the distance from its centre of mass to the group's bounding box pass the test.
+    grouping="cells": groups follow the tree's cells (a cell of at most `group` bodies whose
+    parent holds more, consecutive such siblings merged while they fit, larger buckets cut into
+    chunks); grouping="chunks": consecutive runs of `group` bodies in Morton order."""
+    pos = _soa(pos)
+    mass = np.ascontiguousarray(mass, dtype=np.float64)
+    n = pos.shape[1]
+    t = Tree(pos, mass)
+    try:
+        if grouping == "cells":
+            members = np.zeros(n, dtype=np.int64)
+            offsets = np.zeros(n + 1, dtype=np.int64)
+            ng = int(_load().orc_tree_cell_groups(t._h, int(group), members, offsets))
+        elif grouping == "chunks":
+            _, members = sort_pairs(keys(pos))
+            members = np.ascontiguousarray(members, dtype=np.int64)
+            offsets = np.minimum(np.arange(0, n + group, group, dtype=np.int64), n)
+            offsets = np.ascontiguousarray(np.unique(offsets))
+            ng = offsets.shape[0] - 1
+        else:
+            raise ValueError(grouping)
+        acc = np.zeros((3, n))
+        pp = np.zeros(n, dtype=np.uint32)
+        pc = np.zeros(n, dtype=np.uint32)
+        _load().orc_tree_forces_group(t._h, members, offsets, ng, G, eps, theta, acc, _ptr(pp),
+                                      _ptr(pc))
+        return acc, pp, pc
+    finally:
+        t.close()
+
+
+def cell_groups(pos, mass, group=32):
+    """The groups of bh_group(grouping="cells") as a list of user-id arrays."""
+    pos = _soa(pos)
+    n = pos.shape[1]
+    t = Tree(pos, np.ascontiguousarray(mass, dtype=np.float64))
+    try:
+        members = np.zeros(n, dtype=np.int64)
+        offsets = np.zeros(n + 1, dtype=np.int64)
+        ng = int(_load().orc_tree_cell_groups(t._h, int(group), members, offsets))
+        return [members[offsets[k]:offsets[k + 1]].copy() for k in range(ng)]
+    finally:
+        t.close()
 
 
 def bh(pos, mass, G=1.0, eps=0.0, theta=0.5):

@@ -508,6 +508,189 @@ void orc_bh(const double *pos, const double *mass, int64_t n, double G, double e
 }
 
 /* ------------------------------------------------------------------ */
+/* Group walk: NOT in the paper.  The grouped acceptance test of Barnes (1990): bodies close in  */
+/* space form groups; a cell is accepted for the whole group when its side l                    */
+/* and the distance d_min from its centre of mass to the group's bounding box satisfy           */
+/* l*l < theta*theta*d_min*d_min, else it is opened; leaves interact with every member but the   */
+/* body itself.  Every member then uses the group's interaction list.  With groups of one body   */
+/* the box is a point, d_min is the per-body distance and this is the walk above, term for term. */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+    const int64_t *ids;   /* members (user ids) */
+    int64_t ng;
+    double lo[3], hi[3];  /* bounding box of the members */
+    double G, eps2, th2;
+    double *acc;          /* (3, n) user order */
+    int64_t n;
+    uint32_t *pp, *pc;
+} group_state;
+
+static double axis_gap(double c, double lo, double hi)
+{
+    if (c < lo) return lo - c;
+    if (c > hi) return c - hi;
+    return 0.0;
+}
+
+static void group_walk(const orc_tree *t, int32_t nd, group_state *g)
+{
+    const double *X = t->pos, *Y = t->pos + t->n, *Z = t->pos + 2 * t->n;
+    for (int c = 0; c < 8; ++c) {
+        int32_t ch = t->nodes[nd].child[c];
+        if (ch < 0) continue;
+        const orc_node *C = &t->nodes[ch];
+        if (C->is_leaf) {
+            for (int32_t j = C->head; j >= 0; j = t->next[j]) {
+                for (int64_t k = 0; k < g->ng; ++k) {
+                    const int64_t p = g->ids[k];
+                    if (j == p) continue;
+                    double a[3] = {g->acc[p], g->acc[g->n + p], g->acc[2 * g->n + p]};
+                    accumulate(X[p], Y[p], Z[p], X[j], Y[j], Z[j], t->mass[j], g->G, g->eps2, a);
+                    g->acc[p] = a[0];
+                    g->acc[g->n + p] = a[1];
+                    g->acc[2 * g->n + p] = a[2];
+                    if (g->pp) g->pp[p] += 1;
+                }
+            }
+        } else {
+            double l = ldexp(t->box[3], -C->level);
+            double dx = axis_gap(C->x, g->lo[0], g->hi[0]);
+            double dy = axis_gap(C->y, g->lo[1], g->hi[1]);
+            double dz = axis_gap(C->z, g->lo[2], g->hi[2]);
+            double d2 = dx * dx + dy * dy + dz * dz;
+            if (l * l < g->th2 * d2) {
+                for (int64_t k = 0; k < g->ng; ++k) {
+                    const int64_t p = g->ids[k];
+                    double a[3] = {g->acc[p], g->acc[g->n + p], g->acc[2 * g->n + p]};
+                    accumulate(X[p], Y[p], Z[p], C->x, C->y, C->z, C->m, g->G, g->eps2, a);
+                    g->acc[p] = a[0];
+                    g->acc[g->n + p] = a[1];
+                    g->acc[2 * g->n + p] = a[2];
+                    if (g->pc) g->pc[p] += 1;
+                }
+            } else {
+                group_walk(t, ch, g);
+            }
+        }
+    }
+}
+
+/* Groups that follow the tree's cells: a cell of more than gmax bodies hands out its children
+ * in octant order, consecutive children of at most gmax bodies merged while the group stays
+ * within gmax, larger children handled the same way in turn (buckets of more than gmax bodies cut
+ * into chunks of gmax in their list order); a root of at most gmax bodies is one group.
+ * members receives the user ids group after group (each in Morton order), offsets the group
+ * starts (n_groups + 1 entries).  Returns the number of groups. */
+typedef struct {
+    int64_t *members, *offsets;
+    int64_t nm, ng, cur;     /* members written, groups closed, members in the open group */
+    int64_t gmax;
+} cell_groups_state;
+
+static void cg_flush(cell_groups_state *s)
+{
+    if (s->cur == 0) return;
+    s->ng += 1;
+    s->offsets[s->ng] = s->nm;
+    s->cur = 0;
+}
+
+static void cg_add_subtree(const orc_tree *t, int32_t nd, cell_groups_state *s)
+{
+    const orc_node *N = &t->nodes[nd];
+    if (N->is_leaf) {
+        for (int32_t j = N->head; j >= 0; j = t->next[j]) {
+            s->members[s->nm++] = j;
+            s->cur += 1;
+        }
+        return;
+    }
+    for (int c = 0; c < 8; ++c)
+        if (N->child[c] >= 0) cg_add_subtree(t, N->child[c], s);
+}
+
+static void cg_visit(const orc_tree *t, int32_t nd, cell_groups_state *s)
+{
+    for (int c = 0; c < 8; ++c) {
+        const int32_t ch = t->nodes[nd].child[c];
+        if (ch < 0) continue;
+        const orc_node *C = &t->nodes[ch];
+        if (C->nbody > s->gmax) {
+            cg_flush(s);
+            if (C->is_leaf) {
+                for (int32_t j = C->head; j >= 0; j = t->next[j]) {
+                    s->members[s->nm++] = j;
+                    if (++s->cur == s->gmax) cg_flush(s);
+                }
+                cg_flush(s);
+            } else {
+                cg_visit(t, ch, s);
+            }
+            continue;
+        }
+        if (s->cur > 0 && s->cur + C->nbody > s->gmax) cg_flush(s);
+        cg_add_subtree(t, ch, s);
+    }
+    cg_flush(s);
+}
+
+int64_t orc_tree_cell_groups(void *h, int64_t gmax, int64_t *members, int64_t *offsets)
+{
+    orc_tree *t = (orc_tree *)h;
+    cell_groups_state s = {members, offsets, 0, 0, 0, gmax};
+    offsets[0] = 0;
+    if (t->n == 0) return 0;
+    if (t->nodes[0].nbody <= gmax) {
+        cg_add_subtree(t, 0, &s);
+        cg_flush(&s);
+    } else {
+        cg_visit(t, 0, &s);
+    }
+    return s.ng;
+}
+
+/* Group-walk accelerations of all bodies.  Group k is members[offsets[k] .. offsets[k+1] - 1]
+ * (user ids).  acc (3, n) user order; pp, pc (n) may be NULL. */
+void orc_tree_forces_group(void *h, const int64_t *members, const int64_t *offsets,
+                           int64_t ngroups, double G, double eps, double theta, double *acc,
+                           uint32_t *pp, uint32_t *pc)
+{
+    orc_tree *t = (orc_tree *)h;
+    const int64_t n = t->n;
+    const double *X = t->pos, *Y = t->pos + n, *Z = t->pos + 2 * n;
+    memset(acc, 0, sizeof(double) * 3 * n);
+    if (pp) memset(pp, 0, sizeof(uint32_t) * n);
+    if (pc) memset(pc, 0, sizeof(uint32_t) * n);
+#pragma omp parallel for schedule(dynamic, 16) num_threads(g_threads)
+    for (int64_t k = 0; k < ngroups; ++k) {
+        group_state g;
+        g.ids = members + offsets[k];
+        g.ng = offsets[k + 1] - offsets[k];
+        for (int d = 0; d < 3; ++d) {
+            g.lo[d] = INFINITY;
+            g.hi[d] = -INFINITY;
+        }
+        for (int64_t m = 0; m < g.ng; ++m) {
+            const int64_t p = g.ids[m];
+            const double v[3] = {X[p], Y[p], Z[p]};
+            for (int d = 0; d < 3; ++d) {
+                if (v[d] < g.lo[d]) g.lo[d] = v[d];
+                if (v[d] > g.hi[d]) g.hi[d] = v[d];
+            }
+        }
+        g.G = G;
+        g.eps2 = eps * eps;
+        g.th2 = theta * theta;
+        g.acc = acc;
+        g.n = n;
+        g.pp = pp;
+        g.pc = pc;
+        if (!t->nodes[0].is_leaf) group_walk(t, 0, &g);
+    }
+}
+
+/* ------------------------------------------------------------------ */
 /* Kick-drift-kick leapfrog (§2.4, eqs. leapkick1, leapdrift, leapkick2). */
 /* ------------------------------------------------------------------ */
 

@@ -21,6 +21,8 @@ LIB_PATH = os.path.join(HERE, "libnbody.so")
 
 FP64, FP32, FP32_KAHAN = 0, 1, 2
 WALK_SHAPES = 3  # NBODY_WALK_SHAPES
+FLAG_GROUP_MAC = 1  # NBODY_FLAG_GROUP_MAC: grouped acceptance test (Barnes 1990), FP32 forms
+FLAG_CELL_GROUPS = 2  # NBODY_FLAG_CELL_GROUPS: FP32 walk groups follow the tree's cells
 PRECISIONS = {"fp64": FP64, "fp32": FP32, "fp32_kahan": FP32_KAHAN}
 
 STATUS = {0: "NBODY_OK", 1: "NBODY_EINVAL", 2: "NBODY_ENOMEM", 3: "NBODY_ECUDA",
@@ -134,12 +136,12 @@ class Context:
     ``stream``, a torch.cuda.Stream)."""
 
     def __init__(self, capacity, G=1.0, eps=0.0, theta=0.5, dt=1e-3, precision=FP32,
-                 stream=None, offsets=None):
+                 stream=None, offsets=None, flags=0):
         import torch
         self._lib = load_library()
         if isinstance(precision, str):
             precision = PRECISIONS[precision]
-        self.params = Params(G, eps, theta, dt, precision, 0)
+        self.params = Params(G, eps, theta, dt, precision, int(flags))
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
@@ -163,10 +165,11 @@ class Context:
         self.capacity = int(capacity)
 
     @classmethod
-    def forest(cls, offsets, G=1.0, eps=0.0, theta=0.5, dt=1e-3, precision=FP32, stream=None):
+    def forest(cls, offsets, G=1.0, eps=0.0, theta=0.5, dt=1e-3, precision=FP32, stream=None,
+               flags=0):
         """A context for independent systems packed into one set of arrays: system k owns
         bodies offsets[k] .. offsets[k+1] - 1 (nbody_forest_create)."""
-        return cls(0, G, eps, theta, dt, precision, stream, offsets=offsets)
+        return cls(0, G, eps, theta, dt, precision, stream, offsets=offsets, flags=flags)
 
     # ---------------------------------------------------------------- plumbing
     def _check(self, st, what):
@@ -192,13 +195,14 @@ class Context:
     def __exit__(self, *exc):
         self.close()
 
-    def set_params(self, G=None, eps=None, theta=None, dt=None, precision=None):
+    def set_params(self, G=None, eps=None, theta=None, dt=None, precision=None, flags=None):
         p = self.params
         if isinstance(precision, str):
             precision = PRECISIONS[precision]
         new = Params(p.G if G is None else G, p.eps if eps is None else eps,
                      p.theta if theta is None else theta, p.dt if dt is None else dt,
-                     p.precision if precision is None else precision, 0)
+                     p.precision if precision is None else precision,
+                     p.flags if flags is None else int(flags))
         self._check(self._lib.nbody_set_params(self._h, ctypes.byref(new)), "nbody_set_params")
         self.params = new
 

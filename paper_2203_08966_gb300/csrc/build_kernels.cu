@@ -792,6 +792,62 @@ __global__ void group_nodes_kernel(const uint32_t *__restrict__ d_nn, int64_t ca
     }
 }
 
+// Walk groups that follow the tree (see launch_cell_groups).  A cell of more than gmax bodies
+// hands out its children: runs of consecutive small children merged up to gmax bodies, large
+// buckets in chunks; a root of at most gmax bodies is one group.  Every body lands in exactly one
+// group: the largest cell around it with at most gmax bodies is a child of a larger cell (or the
+// root), and a body in no such cell sits in a bucket larger than gmax.
+__device__ __forceinline__ void put_group(int4 *groups, unsigned *ngroups, int64_t cap, int *err,
+                                          int first, int count, int sys)
+{
+    const unsigned k = atomicAdd(ngroups, 1u);
+    if ((int64_t)k < cap) groups[k] = make_int4(first, count, sys, 0);
+    else atomicOr(err, kErrNodeCap);
+}
+
+__global__ void cell_groups_kernel(NodeArrays na, const uint32_t *__restrict__ node_off,
+                                   Systems ss, int n, int gmax, int4 *groups, unsigned *ngroups,
+                                   int64_t cap, int *err)
+{
+    const int nn = (int)min((int64_t)*na.d_nn, na.cap);
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nn; j += gridDim.x * blockDim.x) {
+        const WalkNode w = na.wn[j];
+        const int sy = system_of(ss, w.first);
+        const int bend = ss.sys ? ss.start[sy + 1] : n;            // system's body end
+        const int nend = ss.sys ? min((int)node_off[ss.start[sy + 1]], nn) : nn;  // node end
+        const int cnt = w.count != 0 ? w.count
+                                     : (w.skip < nend ? na.wn[w.skip].first : bend) - w.first;
+        if (na.level[j] == 0 && cnt <= gmax) {
+            put_group(groups, ngroups, cap, err, w.first, cnt, sy);
+            continue;
+        }
+        if (w.count != 0 || cnt <= gmax) continue;  // handled by the parent
+        int cf = 0, cc = 0;
+        int k = 0;
+        for (int c = j + 1; c < w.skip && k < 8; c = max(na.wn[c].skip, c + 1), ++k) {
+            const WalkNode wc = na.wn[c];
+            const int ccnt = wc.count != 0
+                                 ? wc.count
+                                 : (wc.skip < nend ? na.wn[wc.skip].first : bend) - wc.first;
+            if (ccnt > gmax) {
+                if (cc) put_group(groups, ngroups, cap, err, cf, cc, sy);
+                cc = 0;
+                if (wc.count != 0)  // a bucket of more than gmax bodies: chunks of gmax
+                    for (int b = 0; b < ccnt; b += gmax)
+                        put_group(groups, ngroups, cap, err, wc.first + b, min(gmax, ccnt - b), sy);
+                continue;
+            }
+            if (cc && cc + ccnt > gmax) {
+                put_group(groups, ngroups, cap, err, cf, cc, sy);
+                cc = 0;
+            }
+            if (cc == 0) cf = wc.first;
+            cc += ccnt;
+        }
+        if (cc) put_group(groups, ngroups, cap, err, cf, cc, sy);
+    }
+}
+
 // Forest: level-order index of the root of every non-empty system (its first pre-order node).
 __global__ void roots_kernel(const uint32_t *__restrict__ node_off, Systems ss,
                              const uint32_t *__restrict__ d_nn, const int *__restrict__ order,
@@ -1081,6 +1137,16 @@ void launch_roots(const NodeArrays &na, const uint32_t *node_off, const Systems 
 {
     roots_kernel<<<grid_for(ss.count, 256, kMaxGrid), 256, 0, s>>>(node_off, ss, na.d_nn, na.order,
                                                                    roots);
+    count_launches(1);
+}
+
+void launch_cell_groups(const NodeArrays &na, const uint32_t *node_off, const Systems &ss, int n,
+                        int gmax, int4 *groups, unsigned *ngroups, int64_t cap, int *err,
+                        cudaStream_t s)
+{
+    cell_groups_kernel<<<grid_for(na.cap, 256, kMaxGrid * 4), 256, 0, s>>>(na, node_off, ss, n, gmax,
+                                                                          groups, ngroups, cap,
+                                                                          err);
     count_launches(1);
 }
 

@@ -53,6 +53,11 @@ struct nbody_ctx {
     int n_groups = 0;
     int *roots = nullptr;           // level-order root of every system
     uint32_t *nn = nullptr;         // node count the forest's kernels use (device)
+    // walk groups that follow the tree's cells (FP32 walks with NBODY_FLAG_CELL_GROUPS or
+    // NBODY_FLAG_GROUP_MAC), rebuilt on the device with every tree
+    int4 *cgroups = nullptr;
+    unsigned *cgroups_n = nullptr;
+    unsigned *work = nullptr;       // group counter of the persistent FP32 walk
     // one forest step captured as a CUDA graph, replayed on its own stream
     cudaStream_t gstream = nullptr;
     cudaGraphExec_t gexec = nullptr;
@@ -104,6 +109,12 @@ nbody_status fail(nbody_ctx *c, nbody_status st, const char *fmt, ...)
         if (s_ != NBODY_OK) return s_;   \
     } while (0)
 
+// FP32 walks over groups that follow the tree's cells (the grouped acceptance test needs them).
+bool cell_groups(const nbody_ctx *c)
+{
+    return (c->p.flags & (NBODY_FLAG_GROUP_MAC | NBODY_FLAG_CELL_GROUPS)) != 0;
+}
+
 bool params_ok(const nbody_params *p)
 {
     if (!p) return false;
@@ -111,7 +122,9 @@ bool params_ok(const nbody_params *p)
     if (!(p->eps >= 0.0) || !isfinite(p->eps)) return false;
     if (!(p->theta >= 0.0) || !isfinite(p->theta)) return false;
     if (p->precision < NBODY_FP64 || p->precision > NBODY_FP32_KAHAN) return false;
-    if (p->flags != 0) return false;
+    const uint32_t known = NBODY_FLAG_GROUP_MAC | NBODY_FLAG_CELL_GROUPS;
+    if ((p->flags & ~known) != 0) return false;
+    if ((p->flags & known) && p->precision == NBODY_FP64) return false;
     return true;
 }
 
@@ -230,6 +243,11 @@ nbody_status build(nbody_ctx *c, const double *pos, const double *mass, int n,
     launch_level_order(c->na, s);
     launch_moments(c->keys, max_level, c->sbody64, c->box, c->tab, one, c->p.G, c->na, s);
     if (group) launch_group_nodes(c->na, c->gn, s);
+    if (group && cell_groups(c)) {
+        CK(cudaMemsetAsync(c->cgroups_n, 0, sizeof(unsigned), s));
+        launch_cell_groups(c->na, c->node_off, one, n, 32, c->cgroups, c->cgroups_n, c->cap + 1,
+                           c->err, s);
+    }
     record(c, 3);
     CKS(check_launch(c, "node split / moments"));
     c->n_built = n;
@@ -261,9 +279,17 @@ nbody_status walk(nbody_ctx *c, int n, double *acc, double *vel, double h)
     a.d_nn = c->na.d_nn;
     a.groups = c->groups;
     a.n_groups = c->n_groups;
+    a.d_ngroups = nullptr;
     a.roots = c->roots;
+    a.work = c->work;
+    if (c->p.precision != NBODY_FP64 && cell_groups(c)) {
+        a.groups = c->cgroups;
+        a.n_groups = (int)std::min<int64_t>(c->cap + 1, INT32_MAX);
+        a.d_ngroups = c->cgroups_n;
+    }
     a.node_off = c->node_off;
     a.start = c->sys_start;
+    a.group_mac = (c->p.flags & NBODY_FLAG_GROUP_MAC) != 0;
     launch_walk(c->p.precision, a, c->p.precision == NBODY_FP64 ? c->shape64 : c->shape32,
                 c->stream);
     record(c, 4);
@@ -301,6 +327,11 @@ nbody_status forest_build(nbody_ctx *c, const double *pos, const double *mass)
     launch_moments(c->keys, kMaxLevel, c->sbody64, c->box, c->tab, ss, c->p.G, c->na, s);
     if (c->p.precision != NBODY_FP64) launch_group_nodes(c->na, c->gn, s);
     launch_roots(c->na, c->node_off, ss, c->roots, s);
+    if (c->p.precision != NBODY_FP64 && cell_groups(c)) {
+        CK(cudaMemsetAsync(c->cgroups_n, 0, sizeof(unsigned), s));
+        launch_cell_groups(c->na, c->node_off, ss, n, 32, c->cgroups, c->cgroups_n, c->cap + 1,
+                           c->err, s);
+    }
     CKS(check_launch(c, "forest build"));
     c->n_built = n;
     c->n_nodes = -1;  // on the device only
@@ -375,6 +406,9 @@ nbody_status nbody_create(nbody_ctx **out, int64_t n_capacity, const nbody_param
         CK(dalloc(&c->pp, cap));
         CK(dalloc(&c->pc, cap));
         CK(dalloc(&c->err, 1));
+        CK(dalloc(&c->cgroups, cap + 1));
+        CK(dalloc(&c->cgroups_n, 1));
+        CK(dalloc(&c->work, 1));
         CK(cudaMemset(c->err, 0, sizeof(int)));
         CK(cudaMallocHost((void **)&c->h_word, 2 * sizeof(uint32_t)));
         CK(dalloc(&c->info, 1));
@@ -412,6 +446,9 @@ nbody_status nbody_destroy(nbody_ctx *c)
     dfree(c->pc);
     dfree(c->err);
     dfree(c->info);
+    dfree(c->cgroups);
+    dfree(c->cgroups_n);
+    dfree(c->work);
     dfree(c->sys);
     dfree(c->sys_start);
     dfree(c->sys_hist);

@@ -162,6 +162,13 @@ int layout_tiles(int64_t n_nodes);
 int layout_scan_len(int64_t n_nodes);
 // GroupNode records at their level-order positions (after the moments).
 void launch_group_nodes(const NodeArrays &na, GroupNode *gn, cudaStream_t s);
+// Walk groups that follow the tree: every cell of at most gmax bodies whose parent holds more
+// (consecutive such siblings merged while they fit in gmax), buckets of more than gmax bodies cut
+// into chunks.  (first body, count, system, 0) entries, *ngroups of them (zeroed by the caller);
+// more than cap entries set kErrNodeCap.
+void launch_cell_groups(const NodeArrays &na, const uint32_t *node_off, const Systems &ss, int n,
+                        int gmax, int4 *groups, unsigned *ngroups, int64_t cap, int *err,
+                        cudaStream_t s);
 // Forest: *nn = *total when it fits in cap nodes, else 0 with kErrNodeCap set.
 void launch_clamp_count(const uint32_t *total, int64_t cap, uint32_t *nn, int *err,
                         cudaStream_t s);
@@ -193,6 +200,9 @@ struct WalkArgs {
     const int *roots;     // level-order index of each system's root
     const uint32_t *node_off;  // pre-order: nodes of system k are node_off[start[k]] ..
     const int *start;     // system starts (bodies)
+    bool group_mac;       // FP32 walks: grouped acceptance test (NBODY_FLAG_GROUP_MAC)
+    const unsigned *d_ngroups;  // groups built on the device: their count (n_groups = capacity)
+    unsigned *work;       // FP32 walk: group counter of the persistent warps (zeroed per launch)
 };
 // Launch shapes of the walks (see walk_shape_threads); results do not depend on the shape.
 constexpr int kWalkShapes = 3;

@@ -13,6 +13,8 @@
 // FP32 walk: the group walk below (same interaction lists, terms summed in another order).
 #include <math.h>
 
+#include <algorithm>
+
 #include "nbody_internal.cuh"
 
 namespace nb {
@@ -58,48 +60,14 @@ __device__ __forceinline__ void pair64(double xj, double yj, double zj, double m
     }
 }
 
-// FP32 accumulator.  Plain: one running sum per component.  Compensated: the terms go into a
-// plain FP32 partial sum, which is folded into a Kahan-compensated total (Kahan 1965) every
-// kFold walk iterations and at the end, so the compensation costs a few operations per block of
-// terms instead of four per term; the error of the total is that of partials of at most kFold
-// terms plus a compensated sum over the partials.
-template <bool kKahan>
-struct Acc3 {
-    static constexpr int kFold = 64;
-    float x = 0.f, y = 0.f, z = 0.f;     // plain sum, or the current partial
-    float sx = 0.f, sy = 0.f, sz = 0.f;  // compensated total
-    float cx = 0.f, cy = 0.f, cz = 0.f;  // its compensation
-    __device__ __forceinline__ void add(float tx, float ty, float tz)
-    {
-        x += tx;
-        y += ty;
-        z += tz;
-    }
-    __device__ __forceinline__ static void kahan(float &s, float &c, float t)
-    {
-        const float yv = t - c;
-        const float u = s + yv;
-        c = (u - s) - yv;
-        s = u;
-    }
-    __device__ __forceinline__ void fold()
-    {
-        if (kKahan) {
-            kahan(sx, cx, x);
-            kahan(sy, cy, y);
-            kahan(sz, cz, z);
-            x = y = z = 0.f;
-        }
-    }
-    __device__ __forceinline__ float3 result()
-    {
-        if (kKahan) {
-            fold();
-            return make_float3(sx, sy, sz);
-        }
-        return make_float3(x, y, z);
-    }
-};
+// One step of Kahan's compensated summation (Kahan 1965): s + c tracks the exact running sum.
+__device__ __forceinline__ void kahan_add(float &s, float &c, float t)
+{
+    const float yv = t - c;
+    const float u = s + yv;
+    c = (u - s) - yv;
+    s = u;
+}
 
 __device__ __forceinline__ void write_out(const WalkArgs &a, int i, double ax, double ay, double az,
                                           uint32_t pp, uint32_t pc)
@@ -206,9 +174,9 @@ struct Acc3x2 {
     __device__ __forceinline__ void fold()
     {
         if (kKahan) {
-            Acc3<true>::kahan(sx, cx, x.x + x.y);
-            Acc3<true>::kahan(sy, cy, y.x + y.y);
-            Acc3<true>::kahan(sz, cz, z.x + z.y);
+            kahan_add(sx, cx, x.x + x.y);
+            kahan_add(sy, cy, y.x + y.y);
+            kahan_add(sz, cz, z.x + z.y);
             x = y = z = make_float2(0.f, 0.f);
         }
     }
@@ -252,18 +220,20 @@ __device__ __forceinline__ void axis_bounds(float c, float lo, float hi, float &
     dmax = fmaxf(fabsf(a), fabsf(b));
 }
 
-// The group walked by warp gi: its first sorted body, its size (1..32) and the level-order index
-// of its system's root.  A single system is cut into groups of 32 from body 0; a forest lists
-// its groups (none crosses a system boundary).
+// Group gi: its first sorted body, its size (1..32) and the level-order index of its system's
+// root.  Without a table a single system is cut into groups of 32 from body 0; a table lists
+// the groups (none crosses a system boundary): a forest's fixed chunks, or groups that follow
+// the tree's cells, built on the device (count in *d_ngroups).
 __device__ __forceinline__ bool group_of(const WalkArgs &a, int gi, int &g0, int &count,
                                          int &root)
 {
     if (a.groups) {
-        if (gi >= a.n_groups) return false;
+        const int ng = a.d_ngroups ? (int)min(*a.d_ngroups, (unsigned)a.n_groups) : a.n_groups;
+        if (gi >= ng) return false;
         const int4 g = a.groups[gi];
         g0 = g.x;
         count = g.y;
-        root = a.roots[g.z];
+        root = a.roots ? a.roots[g.z] : 0;
         return true;
     }
     g0 = gi * 32;
@@ -319,15 +289,16 @@ struct GroupEval {
 };
 
 // kWarps warps per block (a launch shape the autotuner chooses; results do not depend on it).
-template <int kWarps, bool kKahan, bool kGuard>
-__global__ void __launch_bounds__(kWarps * 32) group_walk32_kernel(WalkArgs a)
+// kGroup: the grouped acceptance test (Barnes 1990; not in the paper): a cell is accepted for
+// the whole group when the lower bound of the group's distances passes the test, else it is
+// opened for the whole group; no body masks, no per-body tests.  A body meets its own leaf and
+// interacts with itself there, which adds exactly zero (zero separation), and is not counted.
+// The walk of one group (bodies g0 .. g0 + gcount - 1, its system's root at level-order index
+// root) by one warp with its shared-memory slice S.
+template <bool kKahan, bool kGuard, bool kGroup>
+__device__ __forceinline__ void walk_group(const WalkArgs &a, GroupSmem &S, int lane, int g0,
+                                           int gcount, int root)
 {
-    extern __shared__ __align__(16) unsigned char group_smem[];
-    GroupSmem &S = reinterpret_cast<GroupSmem *>(group_smem)[threadIdx.x >> 5];
-    const int lane = threadIdx.x & 31;
-    const int gi = blockIdx.x * kWarps + (threadIdx.x >> 5);
-    int g0, gcount, root;
-    if (!group_of(a, gi, g0, gcount, root)) return;  // uniform per warp
     const int i = g0 + lane;
     const bool live = lane < gcount;
     const int n_nodes = (int)*a.d_nn;
@@ -344,6 +315,7 @@ __global__ void __launch_bounds__(kWarps * 32) group_walk32_kernel(WalkArgs a)
 
     GroupEval<kKahan, kGuard> ev;
     uint32_t upp = 0, upc = 0;    // full-entry counts (the same for every live body)
+    unsigned self_seen = 0u;      // group walk: bodies whose own leaf entered the list
     int sp = 0, fn = 0, pn = 0;   // stack depth and buffer fills (warp-uniform)
 
     // the root is never tested: the walk starts with the root's children (none when the root
@@ -465,11 +437,23 @@ __global__ void __launch_bounds__(kWarps * 32) group_walk32_kernel(WalkArgs a)
             if (meta.y < 0) {
                 if (meta.y == -1) {
                     const unsigned d = (unsigned)(meta.x - g0);
-                    if (d < 32u) emask &= ~(1u << d);   // the body itself
-                    kind = emask == 0u ? kNone : (emask == live_mask ? kFullLeaf : kPartLeaf);
+                    if (kGroup) {
+                        kind = kFullLeaf;
+                    } else {
+                        if (d < 32u) emask &= ~(1u << d);   // the body itself
+                        kind = emask == 0u ? kNone : (emask == live_mask ? kFullLeaf : kPartLeaf);
+                    }
                 } else {
                     kind = kBucket;
                 }
+            } else if (kGroup) {
+                const float crit = __int_as_float(meta.z);
+                float nx, ny, nz, fx, fy, fz;
+                axis_bounds(c.x, lox, hix, nx, fx);
+                axis_bounds(c.y, loy, hiy, ny, fy);
+                axis_bounds(c.z, loz, hiz, nz, fz);
+                const float dmin2 = fmaf(nx, nx, fmaf(ny, ny, nz * nz));
+                kind = dmin2 > crit ? kFullCell : kOpen;
             } else {
                 const float crit = __int_as_float(meta.z);
                 float nx, ny, nz, fx, fy, fz;
@@ -484,8 +468,13 @@ __global__ void __launch_bounds__(kWarps * 32) group_walk32_kernel(WalkArgs a)
             }
         }
 
+        if (kGroup) {  // the bodies whose own leaf is among this step's entries
+            const unsigned d = (unsigned)(meta.x - g0);
+            self_seen |= __reduce_or_sync(kFull, (kind == kFullLeaf && d < 32u) ? 1u << d : 0u);
+        }
+
         // ---- mixed cells: every body tests its own acceptance, two cells per pass
-        unsigned mx = __ballot_sync(kFull, kind == kMixed);
+        unsigned mx = kGroup ? 0u : __ballot_sync(kFull, kind == kMixed);
         unsigned myA = 0u;
         const float crit_l = __int_as_float(meta.z);
         while (mx) {
@@ -542,15 +531,42 @@ __global__ void __launch_bounds__(kWarps * 32) group_walk32_kernel(WalkArgs a)
                 const float4 s = h ? ldg4(a.sbody32 + b) : make_float4(0.f, 0.f, 0.f, 0.f);
                 unsigned mb = sm;
                 const unsigned d = (unsigned)(b - g0);
-                if (d < 32u) mb &= ~(1u << d);
-                const int kb = (!h || mb == 0u) ? kNone : (mb == live_mask ? kFullLeaf : kPartLeaf);
+                int kb;
+                if (kGroup) {
+                    kb = h ? kFullLeaf : kNone;
+                    self_seen |= __reduce_or_sync(kFull, (h && d < 32u) ? 1u << d : 0u);
+                } else {
+                    if (d < 32u) mb &= ~(1u << d);
+                    kb = (!h || mb == 0u) ? kNone : (mb == live_mask ? kFullLeaf : kPartLeaf);
+                }
                 emit(kb, s, mb);
             }
         }
     }
     drain();
     const float3 r = ev.acc.result();
-    if (live) write_out(a, i, (double)r.x, (double)r.y, (double)r.z, ev.pp + upp, ev.pc - ev.pp + upc);
+    const uint32_t self_term = kGroup ? (self_seen >> lane) & 1u : 0u;
+    if (live)
+        write_out(a, i, (double)r.x, (double)r.y, (double)r.z, ev.pp + upp - self_term,
+                  ev.pc - ev.pp + upc);
+}
+
+template <int kWarps, bool kKahan, bool kGuard, bool kGroup>
+__global__ void __launch_bounds__(kWarps * 32) group_walk32_kernel(WalkArgs a)
+{
+    extern __shared__ __align__(16) unsigned char group_smem[];
+    GroupSmem &S = reinterpret_cast<GroupSmem *>(group_smem)[threadIdx.x >> 5];
+    const int lane = threadIdx.x & 31;
+    // persistent warps: each takes the next group from the shared counter until none is left
+    for (;;) {
+        unsigned gi = 0;
+        if (lane == 0) gi = atomicAdd(a.work, 1u);
+        gi = __shfl_sync(kFull, gi, 0);
+        int g0, gcount, root;
+        if (!group_of(a, (int)gi, g0, gcount, root)) break;  // uniform per warp
+        walk_group<kKahan, kGuard, kGroup>(a, S, lane, g0, gcount, root);
+        __syncwarp();
+    }
 }
 
 // FP64 walk, operation for operation the plain per-particle definition: the MAC is
@@ -730,18 +746,48 @@ namespace {
 
 // Launch shapes: FP32 group walk with 2 / 4 / 8 warps per block, FP64 walk with 64 / 128 / 256
 // threads per block.
+// Blocks of the persistent group walk: as many as fit on the GPU at once (never more than the
+// groups need).
+template <int kWarps, bool kGroup>
+int persistent_blocks(bool kahan, bool guard, int64_t groups)
+{
+    static int resident[2][2] = {{0, 0}, {0, 0}};  // [kahan][guard], per process
+    int &r = resident[kahan][guard];
+    if (r == 0) {
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const void *f = kahan ? (guard ? (const void *)group_walk32_kernel<kWarps, true, true, kGroup>
+                                       : (const void *)group_walk32_kernel<kWarps, true, false, kGroup>)
+                              : (guard ? (const void *)group_walk32_kernel<kWarps, false, true, kGroup>
+                                       : (const void *)group_walk32_kernel<kWarps, false, false, kGroup>);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, kWarps * 32,
+                                                      sizeof(GroupSmem) * kWarps);
+        r = std::max(1, sms) * std::max(1, per_sm);
+    }
+    return (int)std::min<int64_t>((groups + kWarps - 1) / kWarps, r);
+}
+
+template <int kWarps, bool kGroup>
+void launch_group(const WalkArgs &a, int64_t groups, bool kahan, bool guard, cudaStream_t s)
+{
+    const int blocks = persistent_blocks<kWarps, kGroup>(kahan, guard, groups);
+    const size_t smem = sizeof(GroupSmem) * kWarps;
+    const int t = kWarps * 32;
+    if (kahan) {
+        if (guard) group_walk32_kernel<kWarps, true, true, kGroup><<<blocks, t, smem, s>>>(a);
+        else group_walk32_kernel<kWarps, true, false, kGroup><<<blocks, t, smem, s>>>(a);
+    } else {
+        if (guard) group_walk32_kernel<kWarps, false, true, kGroup><<<blocks, t, smem, s>>>(a);
+        else group_walk32_kernel<kWarps, false, false, kGroup><<<blocks, t, smem, s>>>(a);
+    }
+}
+
 template <int kWarps>
 void launch_group(const WalkArgs &a, int64_t groups, bool kahan, bool guard, cudaStream_t s)
 {
-    const int blocks = (int)((groups + kWarps - 1) / kWarps);
-    const size_t smem = sizeof(GroupSmem) * kWarps;
-    if (kahan) {
-        if (guard) group_walk32_kernel<kWarps, true, true><<<blocks, kWarps * 32, smem, s>>>(a);
-        else group_walk32_kernel<kWarps, true, false><<<blocks, kWarps * 32, smem, s>>>(a);
-    } else {
-        if (guard) group_walk32_kernel<kWarps, false, true><<<blocks, kWarps * 32, smem, s>>>(a);
-        else group_walk32_kernel<kWarps, false, false><<<blocks, kWarps * 32, smem, s>>>(a);
-    }
+    if (a.group_mac) launch_group<kWarps, true>(a, groups, kahan, guard, s);
+    else launch_group<kWarps, false>(a, groups, kahan, guard, s);
 }
 
 template <int kWarps>
@@ -749,10 +795,14 @@ cudaError_t allow_group_smem()
 {
     const int bytes = (int)(sizeof(GroupSmem) * kWarps);
     cudaError_t e = cudaSuccess;
-    const void *fns[4] = {(const void *)group_walk32_kernel<kWarps, true, true>,
-                          (const void *)group_walk32_kernel<kWarps, true, false>,
-                          (const void *)group_walk32_kernel<kWarps, false, true>,
-                          (const void *)group_walk32_kernel<kWarps, false, false>};
+    const void *fns[8] = {(const void *)group_walk32_kernel<kWarps, true, true, false>,
+                          (const void *)group_walk32_kernel<kWarps, true, false, false>,
+                          (const void *)group_walk32_kernel<kWarps, false, true, false>,
+                          (const void *)group_walk32_kernel<kWarps, false, false, false>,
+                          (const void *)group_walk32_kernel<kWarps, true, true, true>,
+                          (const void *)group_walk32_kernel<kWarps, true, false, true>,
+                          (const void *)group_walk32_kernel<kWarps, false, true, true>,
+                          (const void *)group_walk32_kernel<kWarps, false, false, true>};
     for (const void *f : fns) {
         e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
         if (e != cudaSuccess) return e;
@@ -799,6 +849,7 @@ void launch_walk(int precision, const WalkArgs &a, int shape, cudaStream_t s)
         else launch_w64<256>(a, groups, s);
     } else {
         const bool kahan = precision == NBODY_FP32_KAHAN;
+        cudaMemsetAsync(a.work, 0, sizeof(unsigned), s);
         if (shape == 0) launch_group<2>(a, groups, kahan, guard, s);
         else if (shape == 1) launch_group<4>(a, groups, kahan, guard, s);
         else launch_group<8>(a, groups, kahan, guard, s);

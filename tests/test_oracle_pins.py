@@ -463,3 +463,103 @@ def test_moments_every_cell_is_mean_of_children():
     # children of the root are the records at level 1
     kids = np.nonzero(level == 1)[0]
     assert abs(math.fsum(mom[kids, 0]) - mom[0, 0]) <= 1e-13 * mom[0, 0]
+
+
+# ---- group walk (grouped acceptance test of Barnes 1990; not in the paper) ----------------
+
+@pytest.mark.parametrize("name", ["plummer", "coincident", "uniform"])
+def test_group_walk_of_single_bodies_is_the_per_body_walk(name):
+    """With groups of one body the group's box is the body itself, so every decision and every
+    term is the per-body walk's: bit-identical forces and counters."""
+    if name == "plummer":
+        pos, _, mass = ics.plummer(2000, 41)
+    elif name == "coincident":
+        pos, _, mass = ics.plummer(800, 42)
+        pos[:, 50:70] = pos[:, 50:51]
+    else:
+        pos, _, mass = ics.uniform_cube(700, 43)
+    for theta in (0.0, 0.5, 0.9):
+        a, pp, pc = oracle.bh(pos, mass, 1.0, 0.01, theta)
+        g, gpp, gpc = oracle.bh_group(pos, mass, 1.0, 0.01, theta, group=1)
+        assert np.array_equal(a, g)
+        assert np.array_equal(pp, gpp) and np.array_equal(pc, gpc)
+
+
+def test_group_walk_theta_zero_is_direct_sum():
+    pos, _, mass = ics.plummer(1500, 44)
+    g, gpp, gpc = oracle.bh_group(pos, mass, 1.0, 0.01, 0.0, group=32)
+    d = oracle.direct(pos, mass, 1.0, 0.01)
+    assert np.all(gpc == 0) and np.all(gpp == 1499)
+    assert np.abs(g - d).max() <= 1e-12 * np.abs(d).max()
+
+
+@pytest.mark.parametrize("theta", [0.3, 0.6, 0.9])
+def test_group_walk_refines_every_per_body_list(theta):
+    """A cell the group accepts passes the test for every member (its distance to a member is
+    at least the distance to the group's box), so each group list splits each per-body list
+    further: no body has fewer interactions, and the group forces are at least as accurate in
+    aggregate."""
+    pos, _, mass = ics.plummer(4000, 45)
+    a, pp, pc = oracle.bh(pos, mass, 1.0, 0.01, theta)
+    g, gpp, gpc = oracle.bh_group(pos, mass, 1.0, 0.01, theta, group=32)
+    assert np.all(gpp.astype(np.int64) + gpc >= pp.astype(np.int64) + pc)
+    d = oracle.direct(pos, mass, 1.0, 0.01)
+    err = lambda x: np.sqrt(((x - d) ** 2).sum() / (d ** 2).sum())
+    assert err(g) <= err(a)
+
+
+def _cell_groups_from_keys(pos, gmax=32):
+    """Brute-force restatement of the cell-grouping rule on sorted Morton keys: a body's cell is
+    the largest cell around it with at most gmax bodies; consecutive cells with the same parent
+    merge while the group stays within gmax; bodies of a bucket larger than gmax go in chunks."""
+    k, order = oracle.sort_pairs(oracle.keys(pos))
+    n = len(k)
+    if n <= gmax:
+        return [set(order.tolist())]
+    prefix = lambda a, lev: int(k[a]) >> (3 * (21 - lev)) if lev < 21 else int(k[a])
+    def run(a, lev):
+        p = prefix(a, lev)
+        return sum(1 for b in range(n) if prefix(b, lev) == p)
+    groups, cur, cur_parent, cur_cell = [], [], None, None
+    a = 0
+    while a < n:
+        lev = next((l for l in range(1, 22) if run(a, l) <= gmax), None)
+        if lev is None:                      # bucket larger than gmax: chunks
+            if cur:
+                groups.append(cur)
+                cur, cur_parent = [], None
+            p = int(k[a])
+            b = a
+            while b < n and int(k[b]) == p:
+                b += 1
+            for s in range(a, b, gmax):
+                groups.append(order[s:min(b, s + gmax)].tolist())
+            a = b
+            continue
+        cell = (lev, prefix(a, lev))
+        size = run(a, lev)
+        parent = (lev - 1, prefix(a, lev - 1))
+        if cur and (parent != cur_parent or len(cur) + size > gmax):
+            groups.append(cur)
+            cur = []
+        cur_parent = parent
+        cur.extend(order[a:a + size].tolist())
+        a += size
+    if cur:
+        groups.append(cur)
+    return [set(g) for g in groups]
+
+
+@pytest.mark.parametrize("name", ["plummer", "coincident", "uniform"])
+def test_cell_groups_match_brute_force_rule(name):
+    if name == "plummer":
+        pos, _, mass = ics.plummer(900, 46)
+    elif name == "coincident":
+        pos, _, mass = ics.plummer(600, 47)
+        pos[:, 10:80] = pos[:, 10:11]          # a 70-body bucket
+    else:
+        pos, _, mass = ics.uniform_cube(700, 48)
+    got = [set(g.tolist()) for g in oracle.cell_groups(pos, mass, 32)]
+    want = _cell_groups_from_keys(pos, 32)
+    assert sorted(map(sorted, got)) == sorted(map(sorted, want))
+    assert max(len(g) for g in got) <= 32
