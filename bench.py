@@ -38,6 +38,13 @@ import ics  # noqa: E402
 METRIC = "Barnes-Hut bodies/s per step at N=16M theta=0.5"
 FLOP_PER_INTERACTION = 20          # softened monopole pair term, counting rsqrt as 2 flops
 FP32_LANES_PER_SM = 128            # FP32 FMA lanes per SM (Blackwell)
+# Algorithmic bytes per body of the build phases (compulsory reads + writes):
+#   kick + drift + box partials: pos, vel, acc, mass read (80 B), pos, vel written (48 B);
+#   keys: pos read (24 B), key + id written (12 B)
+BYTES_KICK_KEYS = 80 + 48 + 24 + 12
+#   radix sort: digit histograms read the keys once (8 B); each of 8 passes reads the keys in the
+#   upsweep (8 B) and reads + writes keys and ids in the downsweep (24 B)
+BYTES_SORT = 8 + 8 * (8 + 24)
 CPU_SAMPLE_N = 1 << 20             # bodies in the CPU-baseline sample
 CPU_SAMPLE_STEPS = 3               # timed oracle steps on that sample (about 10-15 s on 16 cores)
 REF_SAMPLE_N = 1 << 20             # bodies per step of the reference arm
@@ -232,10 +239,20 @@ def measure_batch(nb, torch, dev, stream, steps=100):
     ctx.close()
     ms = ev[0].elapsed_time(ev[1])
     ms_launched = ev[2].elapsed_time(ev[3]) / k
+    # the plain FP64 path on the same forest, one launched step after its starting forces
+    with nb.Context.forest(off, 1.0, w["eps"], w["theta"], w["dt"], nb.FP64, stream=stream) as c64:
+        c64.forest_step(tp, tv, tm, 1, use_graph=False)
+        c64.sync()
+        ev[0].record(stream)
+        c64.forest_step(tp, tv, tm, 1, use_graph=False)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        ms64 = ev[0].elapsed_time(ev[1])
     return {"metric": "batch steps/s", "value": steps / (ms * 1e-3), "unit": "steps/s",
             "workload": "forest_512", "systems": int(w["systems"]), "bodies": n,
             "bodies_per_s": n * steps / (ms * 1e-3), "ms_per_step": ms / steps,
-            "ms_per_step_launched": ms_launched, "steps": steps, "graph": True,
+            "ms_per_step_launched": ms_launched, "ms_per_step_fp64": ms64,
+            "steps": steps, "graph": True,
             "gpu_launches": int(launches), "precision": "fp32_kahan",
             "walk_shape": {"chosen": shape, "threads_per_block": shape_threads,
                            "autotune_ms": shape_ms},
@@ -263,11 +280,24 @@ def measure_accuracy(nb, torch, dev, stream, n_targets=16384):
                 "global": float(np.sqrt(num.sum() / den.sum())),
                 "p99": float(np.sqrt(np.quantile(num / den, 0.99)))}
 
+    direct_rate = {}
+    for name, prec in (("fp64", nb.FP64), ("fp32", nb.FP32)):
+        with nb.Context(n, 1.0, w["eps"], 0.5, w["dt"], prec, stream=stream) as ctx:
+            a = ctx.direct_forces(tp, tm, tt)   # warm-up
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            a = ctx.direct_forces(tp, tm, tt)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            pairs = float(n_targets) * (n - 1)
+            direct_rate[name] = {"ms": ms, "pairs": pairs,
+                                 "tflops": pairs * FLOP_PER_INTERACTION / (ms * 1e-3) / 1e12}
+            if name == "fp64":
+                direct = a.cpu().numpy()
     out = {"workload": "plummer_1m", "n": n, "eps": w["eps"], "targets": n_targets,
            "reference": "FP64 direct sum (nbody_direct_forces) on the sampled targets",
-           "theta": {}}
-    with nb.Context(n, 1.0, w["eps"], 0.5, w["dt"], nb.FP64, stream=stream) as ctx:
-        direct = ctx.direct_forces(tp, tm, tt).cpu().numpy()
+           "direct_sum": direct_rate, "theta": {}}
     for theta in (0.3, 0.5, 0.7):
         row = {}
         res = {}
@@ -467,6 +497,12 @@ def run_ours(args):
         "phase_ms": {k: float(v / args.steps) for k, v in
                      zip(("kick_box_keys", "sort", "permute_split_moments", "walk", "step"),
                          phase)},
+        "build_roofline": {
+            "unit": "GB/s", "peak": peaks.get("hbm_gbs"), "peak_source": f"{peak_src} copy bandwidth",
+            "kick_box_keys": {"bytes_per_body": BYTES_KICK_KEYS,
+                              "achieved": BYTES_KICK_KEYS * n / (phase[0] / args.steps * 1e-3) / 1e9},
+            "sort": {"bytes_per_body": BYTES_SORT,
+                     "achieved": BYTES_SORT * n / (phase[1] / args.steps * 1e-3) / 1e9}},
         "interactions_per_step": inter,
         "interactions_per_s": inter / (walk_avg * 1e-3),
         "roofline": {"kernel": "walk32 (Kahan)" if args.precision == "fp32_kahan" else

@@ -69,14 +69,24 @@ __device__ __forceinline__ void add_body(double v[kPart], double x, double y, do
     v[9] = __fma_rn(m, z, v[9]);
 }
 
+// aos (may be null): the bodies as (x, y, z, m) records in the caller's order, which the
+// permutation gathers with one 32-byte access per body.
 __global__ void __launch_bounds__(kBoxThreads) bbox_partials_kernel(const double *__restrict__ pos,
                                                                     const double *__restrict__ mass,
-                                                                    int n, double *partials)
+                                                                    int n, double *partials,
+                                                                    D4 *__restrict__ aos)
 {
     double v[kPart];
     init10(v);
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        add_body(v, pos[i], pos[(size_t)n + i], pos[2 * (size_t)n + i], mass[i]);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        D4 b;
+        b.x = pos[i];
+        b.y = pos[(size_t)n + i];
+        b.z = pos[2 * (size_t)n + i];
+        b.w = mass[i];
+        add_body(v, b.x, b.y, b.z, b.w);
+        if (aos) aos[i] = b;
+    }
     block_reduce10(v, partials + kPart * blockIdx.x);
 }
 
@@ -84,7 +94,8 @@ __global__ void __launch_bounds__(kBoxThreads) bbox_partials_kernel(const double
 // rounded products and sums, fused with the box and centre-of-mass partials of the new positions.
 __global__ void __launch_bounds__(kBoxThreads) kick_drift_bbox_kernel(
     double *__restrict__ pos, double *__restrict__ vel, const double *__restrict__ acc,
-    const double *__restrict__ mass, int n, double h, double dt, double *partials)
+    const double *__restrict__ mass, int n, double h, double dt, double *partials,
+    D4 *__restrict__ aos)
 {
     double v[kPart];
     init10(v);
@@ -98,7 +109,14 @@ __global__ void __launch_bounds__(kBoxThreads) kick_drift_bbox_kernel(
             vel[k] = vh;
             pos[k] = x[d];
         }
-        add_body(v, x[0], x[1], x[2], mass[i]);
+        const double m = mass[i];
+        add_body(v, x[0], x[1], x[2], m);
+        D4 b;
+        b.x = x[0];
+        b.y = x[1];
+        b.z = x[2];
+        b.w = m;
+        aos[i] = b;
     }
     block_reduce10(v, partials + kPart * blockIdx.x);
 }
@@ -169,13 +187,20 @@ __global__ void kick_drift_kernel(double *__restrict__ pos, double *__restrict__
 // Forest: one block per system reduces its bodies and writes its root box and level tables.
 __global__ void __launch_bounds__(kBoxThreads) system_box_kernel(
     const double *__restrict__ pos, const double *__restrict__ mass, int n, Systems ss, Box *box,
-    LevelTables *tab, double theta)
+    LevelTables *tab, double theta, D4 *__restrict__ aos)
 {
     const int k = blockIdx.x;
     double v[kPart];
     init10(v);
-    for (int i = ss.start[k] + threadIdx.x; i < ss.start[k + 1]; i += blockDim.x)
-        add_body(v, pos[i], pos[(size_t)n + i], pos[2 * (size_t)n + i], mass[i]);
+    for (int i = ss.start[k] + threadIdx.x; i < ss.start[k + 1]; i += blockDim.x) {
+        D4 b;
+        b.x = pos[i];
+        b.y = pos[(size_t)n + i];
+        b.z = pos[2 * (size_t)n + i];
+        b.w = mass[i];
+        add_body(v, b.x, b.y, b.z, b.w);
+        aos[i] = b;
+    }
     __shared__ double r[kPart];
     block_reduce10(v, r);
     __syncthreads();
@@ -442,20 +467,14 @@ __global__ void __launch_bounds__(kSortThreads) radix_downsweep_kernel(
 // centre with w = G m.
 // ------------------------------------------------------------------------------------------
 
-__global__ void permute_kernel(const double *__restrict__ pos, const double *__restrict__ mass,
-                               const uint32_t *__restrict__ ids, int n, const Box *__restrict__ box,
-                               Systems ss, double G, D4 *__restrict__ sbody64,
-                               float4 *__restrict__ sbody32)
+__global__ void permute_kernel(const D4 *__restrict__ aos, const uint32_t *__restrict__ ids, int n,
+                               const Box *__restrict__ box, Systems ss, double G,
+                               D4 *__restrict__ sbody64, float4 *__restrict__ sbody32)
 {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const Box *bx = box + system_of(ss, i);
         const double cx = bx->c[0], cy = bx->c[1], cz = bx->c[2];
-        const uint32_t id = ids[i];
-        D4 b;
-        b.x = pos[id];
-        b.y = pos[(size_t)n + id];
-        b.z = pos[2 * (size_t)n + id];
-        b.w = mass[id];
+        const D4 b = aos[ids[i]];
         sbody64[i] = b;
         sbody32[i] = make_float4((float)(b.x - cx), (float)(b.y - cy), (float)(b.z - cz),
                                  (float)(G * b.w));
@@ -648,6 +667,9 @@ __global__ void link_leaves_kernel(const uint64_t *__restrict__ keys, NodeArrays
                 m.z = __ddiv_rn(sz, s);
             }
             store_node(na, j, w, m, box + system_of(ss, w.first), G, 0.f);
+            const int b = na.order[j];
+            na.com_lo[b] = m;
+            na.lo_child[b] = make_int4(0, 0, w.first, 0);
             continue;
         }
         const int shift = 3 * (kMaxLevel - 1 - lev);
@@ -659,6 +681,8 @@ __global__ void link_leaves_kernel(const uint64_t *__restrict__ keys, NodeArrays
             mask |= 1u << (unsigned)((keys[na.wn[c].first] >> shift) & 7u);
         na.mask[j] = (uint8_t)mask;
         na.kind[j] = (uint8_t)lev;
+        // children of a cell are consecutive in level order, starting with the next pre-order node
+        na.lo_child[na.order[j]] = make_int4(na.order[j + 1], __popc(mask), w.first, 0);
     }
 }
 
@@ -668,17 +692,16 @@ __global__ void link_leaves_kernel(const uint64_t *__restrict__ keys, NodeArrays
 __global__ void moments_level_kernel(int level, NodeArrays na, const Box *__restrict__ box,
                                      const LevelTables *__restrict__ tab, Systems ss, double G)
 {
-    // the nodes of this level are level-order indices [start(level), start(level + 1))
+    // the nodes of this level are level-order indices [start(level), start(level + 1)); the
+    // children of each cell are a contiguous level-order run (in octant order)
     const int lo = (int)na.tile_offsets[level * na.tiles];
     const int hi = (int)na.tile_offsets[(level + 1) * na.tiles];
     for (int t = lo + blockIdx.x * blockDim.x + threadIdx.x; t < hi; t += gridDim.x * blockDim.x) {
-        const int j = na.inv[t];
-        if (na.kind[j] == kLeafKind) continue;
-        const WalkNode w = na.wn[j];
+        const int4 ch = na.lo_child[t];
+        if (ch.y == 0) continue;  // leaf: done by link_leaves
         double s = 0.0, sx = 0.0, sy = 0.0, sz = 0.0;
-        int nc = 0;
-        for (int c = j + 1; c < w.skip && nc < 8; c = max(__ldcg(&na.wn[c].skip), c + 1), ++nc) {
-            const D4 q = ld_cg(&na.com64[c]);
+        for (int k = 0; k < min(ch.y, 8); ++k) {
+            const D4 q = ld_cg(&na.com_lo[ch.x + k]);
             s = __dadd_rn(s, q.w);
             sx = __dadd_rn(sx, __dmul_rn(q.w, q.x));
             sy = __dadd_rn(sy, __dmul_rn(q.w, q.y));
@@ -689,8 +712,14 @@ __global__ void moments_level_kernel(int level, NodeArrays na, const Box *__rest
         m.x = __ddiv_rn(sx, s);
         m.y = __ddiv_rn(sy, s);
         m.z = __ddiv_rn(sz, s);
-        const int k = system_of(ss, w.first);
-        store_node(na, j, w, m, box + k, G, tab[k].crit32[level]);
+        na.com_lo[t] = m;
+        const int k = system_of(ss, ch.z);
+        const Box *bx = box + k;
+        const int j = na.inv[t];
+        na.com64[j] = m;
+        na.wn[j].c = make_float4((float)(m.x - bx->c[0]), (float)(m.y - bx->c[1]),
+                                 (float)(m.z - bx->c[2]), (float)(G * m.w));
+        na.wn[j].crit = tab[k].crit32[level];
     }
 }
 
@@ -968,16 +997,18 @@ int bbox_blocks(int64_t n) { return grid_for(n, kBoxThreads * 4, 152 * 8); }
 int bbox_partial_doubles() { return kPart; }
 
 void launch_bbox_partials(const double *pos, const double *mass, int n, double *partials, int nblk,
-                          cudaStream_t s)
+                          D4 *aos, cudaStream_t s)
 {
-    bbox_partials_kernel<<<nblk, kBoxThreads, 0, s>>>(pos, mass, n, partials);
+    bbox_partials_kernel<<<nblk, kBoxThreads, 0, s>>>(pos, mass, n, partials, aos);
     count_launches(1);
 }
 
 void launch_kick_drift_bbox(double *pos, double *vel, const double *acc, const double *mass, int n,
-                            double h, double dt, double *partials, int nblk, cudaStream_t s)
+                            double h, double dt, double *partials, int nblk, D4 *aos,
+                            cudaStream_t s)
 {
-    kick_drift_bbox_kernel<<<nblk, kBoxThreads, 0, s>>>(pos, vel, acc, mass, n, h, dt, partials);
+    kick_drift_bbox_kernel<<<nblk, kBoxThreads, 0, s>>>(pos, vel, acc, mass, n, h, dt, partials,
+                                                        aos);
     count_launches(1);
 }
 
@@ -996,9 +1027,9 @@ void launch_kick_drift(double *pos, double *vel, const double *acc, int n, doubl
 }
 
 void launch_system_boxes(const double *pos, const double *mass, int n, const Systems &ss,
-                         Box *box, LevelTables *tab, double theta, cudaStream_t s)
+                         Box *box, LevelTables *tab, double theta, D4 *aos, cudaStream_t s)
 {
-    system_box_kernel<<<ss.count, kBoxThreads, 0, s>>>(pos, mass, n, ss, box, tab, theta);
+    system_box_kernel<<<ss.count, kBoxThreads, 0, s>>>(pos, mass, n, ss, box, tab, theta, aos);
     count_launches(1);
 }
 
@@ -1054,12 +1085,11 @@ void launch_radix_sort(uint64_t *keys, uint32_t *ids, int n, const SortScratch &
     // an even number of passes (8, or 8 + 2) leaves the result in the caller's buffers
 }
 
-void launch_permute(const double *pos, const double *mass, const uint32_t *ids, int n,
-                    const Box *box, const Systems &ss, double G, D4 *sbody64, float4 *sbody32,
-                    cudaStream_t s)
+void launch_permute(const D4 *aos, const uint32_t *ids, int n, const Box *box, const Systems &ss,
+                    double G, D4 *sbody64, float4 *sbody32, cudaStream_t s)
 {
-    permute_kernel<<<grid_for(n, 256, kMaxGrid), 256, 0, s>>>(pos, mass, ids, n, box, ss, G,
-                                                              sbody64, sbody32);
+    permute_kernel<<<grid_for(n, 256, kMaxGrid), 256, 0, s>>>(aos, ids, n, box, ss, G, sbody64,
+                                                              sbody32);
     count_launches(1);
 }
 

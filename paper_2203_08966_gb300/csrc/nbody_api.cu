@@ -24,6 +24,7 @@ struct nbody_ctx {
     uint64_t *keys = nullptr, *keys_alt = nullptr;
     uint32_t *ids = nullptr, *ids_alt = nullptr;
     D4 *sbody64 = nullptr;
+    D4 *aos = nullptr;              // (x, y, z, m) records in the caller's order
     float4 *sbody32 = nullptr;
     uint32_t *node_off = nullptr;   // cap + 1
     uint32_t *hist = nullptr;       // 8 x 256
@@ -58,6 +59,8 @@ struct nbody_ctx {
     int4 *cgroups = nullptr;
     unsigned *cgroups_n = nullptr;
     unsigned *work = nullptr;       // group counter of the persistent FP32 walk
+    float *dscratch = nullptr;      // FP32 direct sum: sources + partial sums (grown on demand)
+    int64_t dscratch_cap = 0;       // floats
     // one forest step captured as a CUDA graph, replayed on its own stream
     cudaStream_t gstream = nullptr;
     cudaGraphExec_t gexec = nullptr;
@@ -152,6 +155,8 @@ void free_nodes(nbody_ctx *c)
     dfree(c->na.kind);
     dfree(c->na.order);
     dfree(c->na.inv);
+    dfree(c->na.com_lo);
+    dfree(c->na.lo_child);
     dfree(c->na.tile_offsets);
     dfree(c->na.block_sums);
     dfree(c->gn);
@@ -170,6 +175,8 @@ nbody_status ensure_nodes(nbody_ctx *c, int64_t need)
     CK(dalloc(&c->na.kind, cap));
     CK(dalloc(&c->na.order, cap));
     CK(dalloc(&c->na.inv, cap));
+    CK(dalloc(&c->na.com_lo, cap));
+    CK(dalloc(&c->na.lo_child, cap));
     const int len = layout_scan_len(cap);
     CK(dalloc(&c->na.tile_offsets, (size_t)len));
     CK(dalloc(&c->na.block_sums, (size_t)scan_tiles(len) + 1));
@@ -211,7 +218,7 @@ nbody_status build(nbody_ctx *c, const double *pos, const double *mass, int n,
         return NBODY_OK;
     }
     const Systems one{nullptr, nullptr, 1};
-    if (!have_partials) launch_bbox_partials(pos, mass, n, c->partials, c->nblk, s);
+    if (!have_partials) launch_bbox_partials(pos, mass, n, c->partials, c->nblk, c->aos, s);
     launch_bbox_finalize(c->partials, c->nblk, c->box, c->tab, c->p.theta, s);
     launch_keys(pos, n, c->box, one, c->keys, c->ids, s);
     record(c, 1);
@@ -219,7 +226,7 @@ nbody_status build(nbody_ctx *c, const double *pos, const double *mass, int n,
                    nullptr};
     launch_radix_sort(c->keys, c->ids, n, sc, s);
     record(c, 2);
-    launch_permute(pos, mass, c->ids, n, c->box, one, c->p.G, c->sbody64, c->sbody32, s);
+    launch_permute(c->aos, c->ids, n, c->box, one, c->p.G, c->sbody64, c->sbody32, s);
     CK(cudaMemsetAsync(c->info, 0, sizeof(unsigned), s));
     launch_count_nodes(c->keys, n, one, c->node_off, c->info, s);
     ScanScratch ss{c->block_sums, scan_tiles((int)c->cap + 1)};
@@ -310,12 +317,12 @@ nbody_status forest_build(nbody_ctx *c, const double *pos, const double *mass)
     cudaStream_t s = c->stream;
     const int n = (int)c->cap;
     const Systems ss = systems(c);
-    launch_system_boxes(pos, mass, n, ss, c->box, c->tab, c->p.theta, s);
+    launch_system_boxes(pos, mass, n, ss, c->box, c->tab, c->p.theta, c->aos, s);
     launch_keys(pos, n, c->box, ss, c->keys, c->ids, s);
     SortScratch sc{c->keys_alt, c->ids_alt, c->hist, c->counts, sort_tiles(n), c->sys,
                    c->sys_hist};
     launch_radix_sort(c->keys, c->ids, n, sc, s);
-    launch_permute(pos, mass, c->ids, n, c->box, ss, c->p.G, c->sbody64, c->sbody32, s);
+    launch_permute(c->aos, c->ids, n, c->box, ss, c->p.G, c->sbody64, c->sbody32, s);
     CK(cudaMemsetAsync(c->info, 0, sizeof(unsigned), s));
     launch_count_nodes(c->keys, n, ss, c->node_off, c->info, s);
     ScanScratch sn{c->block_sums, scan_tiles(n + 1)};
@@ -393,6 +400,7 @@ nbody_status nbody_create(nbody_ctx **out, int64_t n_capacity, const nbody_param
         CK(dalloc(&c->ids, cap));
         CK(dalloc(&c->ids_alt, cap));
         CK(dalloc(&c->sbody64, cap));
+        CK(dalloc(&c->aos, cap));
         CK(dalloc(&c->sbody32, cap));
         CK(dalloc(&c->node_off, cap + 1));
         CK(dalloc(&c->hist, 8 * 256));
@@ -433,6 +441,7 @@ nbody_status nbody_destroy(nbody_ctx *c)
     dfree(c->ids);
     dfree(c->ids_alt);
     dfree(c->sbody64);
+    dfree(c->aos);
     dfree(c->sbody32);
     dfree(c->node_off);
     dfree(c->hist);
@@ -446,6 +455,7 @@ nbody_status nbody_destroy(nbody_ctx *c)
     dfree(c->pc);
     dfree(c->err);
     dfree(c->info);
+    dfree(c->dscratch);
     dfree(c->cgroups);
     dfree(c->cgroups_n);
     dfree(c->work);
@@ -525,7 +535,7 @@ nbody_status nbody_step(nbody_ctx *c, double *d_pos, double *d_vel, const double
     for (int32_t k = 0; k < nsteps; ++k) {
         CKS(begin_timing(c));
         launch_kick_drift_bbox(d_pos, d_vel, c->acc, d_mass, (int)n, h, c->p.dt, c->partials,
-                               c->nblk, c->stream);
+                               c->nblk, c->aos, c->stream);
         CKS(check_launch(c, "kick/drift"));
         CKS(build(c, d_pos, d_mass, (int)n, true));
         CKS(walk(c, (int)n, c->acc, d_vel, h));
@@ -585,10 +595,23 @@ nbody_status nbody_direct_forces(nbody_ctx *c, const double *d_pos, const double
     if (nt < 0 || nt > ((int64_t)1 << 30)) return fail(c, NBODY_EINVAL, "bad target count");
     if (n > 0 && (!d_pos || !d_mass || !d_acc)) return fail(c, NBODY_EINVAL, "null pointer");
     if (n == 0 || nt == 0) return NBODY_OK;
-    launch_bbox_partials(d_pos, d_mass, (int)n, c->partials, c->nblk, c->stream);
+    launch_bbox_partials(d_pos, d_mass, (int)n, c->partials, c->nblk, nullptr, c->stream);
     launch_bbox_finalize(c->partials, c->nblk, c->box + 1, c->tab + 1, c->p.theta, c->stream);
+    DirectScratch ds{nullptr, nullptr};
+    if (c->p.precision != NBODY_FP64) {
+        // FP32 scratch, grown on demand: sources, then per-chunk partial sums
+        const int64_t need = (int64_t)4 * n + (int64_t)direct32_chunks((int)n, (int)nt) * 3 * nt;
+        if (need > c->dscratch_cap) {
+            dfree(c->dscratch);
+            c->dscratch_cap = 0;
+            CK(dalloc(&c->dscratch, (size_t)need));
+            c->dscratch_cap = need;
+        }
+        ds.src = reinterpret_cast<float4 *>(c->dscratch);
+        ds.part = c->dscratch + 4 * n;
+    }
     launch_direct(c->p.precision, d_pos, d_mass, (int)n, d_targets, (int)nt, c->p.G, c->p.eps,
-                  c->box + 1, d_acc, c->stream);
+                  c->box + 1, d_acc, ds, c->stream);
     return check_launch(c, "direct sum");
 }
 

@@ -66,10 +66,12 @@ int64_t launch_count();
 // ---------------------------------------------------------------- build_kernels.cu
 int bbox_blocks(int64_t n);
 int bbox_partial_doubles();  // doubles per block in the partials buffer
+// aos: the bodies as (x, y, z, m) records in the caller's order, written for the permutation
+// (may be null for launch_bbox_partials).
 void launch_bbox_partials(const double *pos, const double *mass, int n, double *partials,
-                          int nblk, cudaStream_t s);
+                          int nblk, D4 *aos, cudaStream_t s);
 void launch_kick_drift_bbox(double *pos, double *vel, const double *acc, const double *mass,
-                            int n, double h, double dt, double *partials, int nblk,
+                            int n, double h, double dt, double *partials, int nblk, D4 *aos,
                             cudaStream_t s);
 void launch_bbox_finalize(const double *partials, int nblk, Box *box, LevelTables *tab,
                           double theta, cudaStream_t s);
@@ -77,7 +79,7 @@ void launch_bbox_finalize(const double *partials, int nblk, Box *box, LevelTable
 void launch_kick_drift(double *pos, double *vel, const double *acc, int n, double h, double dt,
                        cudaStream_t s);
 void launch_system_boxes(const double *pos, const double *mass, int n, const Systems &ss,
-                         Box *box, LevelTables *tab, double theta, cudaStream_t s);
+                         Box *box, LevelTables *tab, double theta, D4 *aos, cudaStream_t s);
 void launch_keys(const double *pos, int n, const Box *box, const Systems &ss, uint64_t *keys,
                  uint32_t *ids, cudaStream_t s);
 
@@ -95,9 +97,8 @@ cudaError_t sort_prepare(); // one-time function attributes
 void launch_radix_sort(uint64_t *keys, uint32_t *ids, int n, const SortScratch &sc,
                        cudaStream_t s);
 
-void launch_permute(const double *pos, const double *mass, const uint32_t *ids, int n,
-                    const Box *box, const Systems &ss, double G, D4 *sbody64, float4 *sbody32,
-                    cudaStream_t s);
+void launch_permute(const D4 *aos, const uint32_t *ids, int n, const Box *box, const Systems &ss,
+                    double G, D4 *sbody64, float4 *sbody32, cudaStream_t s);
 
 struct ScanScratch {
     uint32_t *block_sums;  // tiles + 1
@@ -122,6 +123,8 @@ struct NodeArrays {
     uint8_t *kind;
     int *order;               // pre-order index -> level-order index
     int *inv;                 // level-order index -> pre-order index
+    D4 *com_lo;               // FP64 moments in level order
+    int4 *lo_child;           // level order: (first child, child count, first body, 0); count 0 = leaf
     uint32_t *tile_offsets;   // level-major (level, tile) offsets; level l starts at [l * tiles]
     uint32_t *block_sums;     // scan scratch for tile_offsets
     const uint32_t *d_nn;     // node count (device)
@@ -211,8 +214,15 @@ int walk_shape_threads(int precision, int shape);
 cudaError_t walk_prepare();  // one-time function attributes (dynamic shared memory)
 void launch_walk(int precision, const WalkArgs &a, int shape, cudaStream_t s);
 
+// FP32 direct sum scratch: FP32 sources (n) and per-chunk partial sums
+// (direct32_chunks(n, nt) x 3 x nt floats).
+struct DirectScratch {
+    float4 *src;
+    float *part;
+};
+int direct32_chunks(int n, int nt);
 void launch_direct(int precision, const double *pos, const double *mass, int n,
                    const int64_t *targets, int nt, double G, double eps, const Box *box,
-                   double *acc, cudaStream_t s);
+                   double *acc, const DirectScratch &sc, cudaStream_t s);
 
 }  // namespace nb

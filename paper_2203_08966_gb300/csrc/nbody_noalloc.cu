@@ -78,7 +78,7 @@ extern "C" nbody_status nbody_sort_keys_noalloc(const double *d_pos, const doubl
     double *partials = reinterpret_cast<double *>(base + kOffPartials);
     Box *box = reinterpret_cast<Box *>(base + kOffBox);
     LevelTables *tab = reinterpret_cast<LevelTables *>(base + kOffTab);
-    launch_bbox_partials(d_pos, d_mass, (int)n, partials, nblk, s);
+    launch_bbox_partials(d_pos, d_mass, (int)n, partials, nblk, nullptr, s);
     launch_bbox_finalize(partials, nblk, box, tab, 0.0, s);
     launch_keys(d_pos, (int)n, box, Systems{nullptr, nullptr, 1}, d_keys_sorted, d_ids_sorted, s);
     SortScratch sc{reinterpret_cast<uint64_t *>(base + kOffKeys),

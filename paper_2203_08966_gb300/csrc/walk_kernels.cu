@@ -639,59 +639,68 @@ __global__ void __launch_bounds__(kThreads) walk64_kernel(WalkArgs a)
 // skipping itself.  Sources are staged through shared memory a tile at a time.
 // ------------------------------------------------------------------------------------------
 
-constexpr int kDirectThreads = 256;
+constexpr int kDirectThreads = 256;   // FP64 direct sum
+constexpr int kD32Threads = 128;      // FP32 direct sum: targets per block
+constexpr int kD32Tile = 256;         // sources per shared-memory tile
+constexpr int kD32MinChunk = 4096;    // sources per block at least
 
-template <bool kGuard>
-__global__ void __launch_bounds__(kDirectThreads) direct32_kernel(
-    const double *__restrict__ pos, const double *__restrict__ mass, int n,
-    const int64_t *__restrict__ targets, int nt, double G, float eps2, const Box *__restrict__ box,
-    double *__restrict__ acc)
+// FP32 sources (x - c, y - c, z - c, G m) of all bodies, converted once per call.
+__global__ void direct32_prep_kernel(const double *__restrict__ pos, const double *__restrict__ mass,
+                                     int n, double G, const Box *__restrict__ box,
+                                     float4 *__restrict__ src)
 {
-    __shared__ float4 tile[kDirectThreads];
     const double cx = box->c[0], cy = box->c[1], cz = box->c[2];
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
+        src[j] = make_float4((float)(pos[j] - cx), (float)(pos[(size_t)n + j] - cy),
+                             (float)(pos[2 * (size_t)n + j] - cz), (float)(G * mass[j]));
+}
+
+// One block: kD32Threads targets against one chunk of the sources (blockIdx.y), two sources at a
+// time with packed FP32 arithmetic.  A target meets itself in its own chunk at zero separation,
+// which adds exactly zero.  Partial sums go to part[chunk][3][nt].
+template <bool kGuard>
+__global__ void __launch_bounds__(kD32Threads) direct32_chunk_kernel(
+    const float4 *__restrict__ src, int n, const int64_t *__restrict__ targets, int nt,
+    float eps2s, int chunk, float *__restrict__ part)
+{
+    __shared__ float4 tile[kD32Tile];   // pair-interleaved (see put_entry)
+    const int t = blockIdx.x * kD32Threads + threadIdx.x;
     const bool live = t < nt;
-    const int i = live ? (targets ? (int)targets[t] : t) : -1;
-    float xi = 0.f, yi = 0.f, zi = 0.f;
-    if (live) {
-        xi = (float)(pos[i] - cx);
-        yi = (float)(pos[(size_t)n + i] - cy);
-        zi = (float)(pos[2 * (size_t)n + i] - cz);
-    }
-    float ax = 0.f, ay = 0.f, az = 0.f;
-    for (int base = 0; base < n; base += kDirectThreads) {
-        const int j = base + threadIdx.x;
+    const int i = live ? (targets ? (int)targets[t] : t) : 0;
+    const float4 me = src[i];
+    const float2 nme[3] = {make_float2(-me.x, -me.x), make_float2(-me.y, -me.y),
+                           make_float2(-me.z, -me.z)};
+    const float2 eps2 = make_float2(eps2s, eps2s);
+    float2 ax = make_float2(0.f, 0.f), ay = ax, az = ax;
+    const int lo = blockIdx.y * chunk, hi = min(n, lo + chunk);
+    for (int base = lo; base < hi; base += kD32Tile) {
         __syncthreads();
-        if (j < n) {
-            tile[threadIdx.x] = make_float4((float)(pos[j] - cx), (float)(pos[(size_t)n + j] - cy),
-                                            (float)(pos[2 * (size_t)n + j] - cz),
-                                            (float)(G * mass[j]));
-        } else {
-            tile[threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int k = threadIdx.x; k < kD32Tile; k += kD32Threads) {
+            const int j = base + k;
+            put_entry(tile, k, j < hi ? src[j] : make_float4(0.f, 0.f, 0.f, 0.f));
         }
         __syncthreads();
-        const int m = min(kDirectThreads, n - base);
-        const int self = i - base;  // in [0, m) when the target itself is in this tile
-        if (self >= 0 && self < m) {
-            for (int k = 0; k < m; ++k) {
-                if (k == self) continue;
-                float tx, ty, tz;
-                pair32<kGuard>(tile[k], xi, yi, zi, eps2, tx, ty, tz);
-                ax += tx; ay += ty; az += tz;
-            }
-        } else {
-#pragma unroll 8
-            for (int k = 0; k < m; ++k) {
-                float tx, ty, tz;
-                pair32<kGuard>(tile[k], xi, yi, zi, eps2, tx, ty, tz);
-                ax += tx; ay += ty; az += tz;
-            }
-        }
+        const int pairs = (min(kD32Tile, hi - base) + 1) >> 1;
+#pragma unroll 4
+        for (int q = 0; q < pairs; ++q)
+            pair32x2<kGuard>(tile[2 * q], tile[2 * q + 1], nme[0], nme[1], nme[2], eps2, ax, ay, az);
     }
     if (live) {
-        acc[t] = ax;
-        acc[(size_t)nt + t] = ay;
-        acc[2 * (size_t)nt + t] = az;
+        float *o = part + (size_t)blockIdx.y * 3 * nt;
+        o[t] = ax.x + ax.y;
+        o[(size_t)nt + t] = ay.x + ay.y;
+        o[2 * (size_t)nt + t] = az.x + az.y;
+    }
+}
+
+// acc = sum over the chunks, in chunk order, in FP64.
+__global__ void direct32_reduce_kernel(const float *__restrict__ part, int chunks, int nt,
+                                       double *__restrict__ acc)
+{
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < 3 * nt; k += gridDim.x * blockDim.x) {
+        double sum = 0.0;
+        for (int c = 0; c < chunks; ++c) sum += (double)part[(size_t)c * 3 * nt + k];
+        acc[k] = sum;
     }
 }
 
@@ -857,25 +866,42 @@ void launch_walk(int precision, const WalkArgs &a, int shape, cudaStream_t s)
     count_launches(1);
 }
 
+int direct32_chunks(int n, int nt)
+{
+    // enough blocks for every SM several times over, chunks of at least kD32MinChunk sources
+    const int tblocks = (nt + kD32Threads - 1) / kD32Threads;
+    int chunks = (152 * 8 + tblocks - 1) / std::max(1, tblocks);
+    chunks = std::min(chunks, std::max(1, n / kD32MinChunk));
+    return std::max(1, chunks);
+}
+
 void launch_direct(int precision, const double *pos, const double *mass, int n,
                    const int64_t *targets, int nt, double G, double eps, const Box *box,
-                   double *acc, cudaStream_t s)
+                   double *acc, const DirectScratch &sc, cudaStream_t s)
 {
     if (nt <= 0) return;
-    const int blocks = (nt + kDirectThreads - 1) / kDirectThreads;
     if (precision == NBODY_FP64) {
+        const int blocks = (nt + kDirectThreads - 1) / kDirectThreads;
         direct64_kernel<<<blocks, kDirectThreads, 0, s>>>(pos, mass, n, targets, nt, G, eps * eps,
                                                           acc);
-    } else {
-        const float eps2 = (float)(eps * eps);
-        if (eps > 0.0)
-            direct32_kernel<false><<<blocks, kDirectThreads, 0, s>>>(pos, mass, n, targets, nt, G,
-                                                                     eps2, box, acc);
-        else
-            direct32_kernel<true><<<blocks, kDirectThreads, 0, s>>>(pos, mass, n, targets, nt, G,
-                                                                    eps2, box, acc);
+        count_launches(1);
+        return;
     }
-    count_launches(1);
+    const int chunks = direct32_chunks(n, nt);
+    const int chunk = (n + chunks - 1) / chunks;
+    direct32_prep_kernel<<<std::min((n + 255) / 256, 152 * 16), 256, 0, s>>>(pos, mass, n, G, box,
+                                                                            sc.src);
+    const dim3 grid((nt + kD32Threads - 1) / kD32Threads, chunks);
+    const float eps2 = (float)(eps * eps);
+    if (eps > 0.0)
+        direct32_chunk_kernel<false><<<grid, kD32Threads, 0, s>>>(sc.src, n, targets, nt, eps2,
+                                                                  chunk, sc.part);
+    else
+        direct32_chunk_kernel<true><<<grid, kD32Threads, 0, s>>>(sc.src, n, targets, nt, eps2,
+                                                                 chunk, sc.part);
+    direct32_reduce_kernel<<<std::min((3 * nt + 255) / 256, 152 * 16), 256, 0, s>>>(
+        sc.part, chunks, nt, acc);
+    count_launches(3);
 }
 
 }  // namespace nb
