@@ -57,7 +57,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="two_plummer_16m", choices=sorted(ics.WORKLOADS))
-    ap.add_argument("--n", type=int, default=0, help="override N (smaller runs, profiling)")
+    ap.add_argument("--n", "--bodies", dest="n", type=int, default=0,
+                    help="override N (smaller runs, profiling; --bodies under torchrun)")
     ap.add_argument("--precision", default="fp32_kahan", choices=["fp64", "fp32", "fp32_kahan"])
     ap.add_argument("--theta", type=float, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -175,7 +176,8 @@ def run_reference(args):
     oracle.build()
     cores = os.cpu_count() or 1
     oracle.set_threads(cores)
-    _, pos, vel, mass = make_workload(args.workload, REF_SAMPLE_N)
+    sample_n = args.n or REF_SAMPLE_N
+    _, pos, vel, mass = make_workload(args.workload, sample_n)
     acc, _, _ = oracle.bh(pos, mass, 1.0, w["eps"], w["theta"])
     for _ in range(args.warmup):
         pos, vel, acc = oracle.kdk(pos, vel, mass, acc, 1.0, w["eps"], w["theta"], w["dt"], 1)
@@ -183,15 +185,15 @@ def run_reference(args):
     for _ in range(args.steps):
         pos, vel, acc = oracle.kdk(pos, vel, mass, acc, 1.0, w["eps"], w["theta"], w["dt"], 1)
     dt = time.perf_counter() - t0
-    value = REF_SAMPLE_N * args.steps / dt
+    value = sample_n * args.steps / dt
     sample = (f"CPU oracle (FP64 pointer-octree Barnes-Hut by insertion + KDK), "
-              f"{REF_SAMPLE_N} bodies drawn with the workload's recipe per step")
+              f"{sample_n} bodies drawn with the workload's recipe per step")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "bodies/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"{args.workload} sampled at N={REF_SAMPLE_N}",
+        "config": {"workload": f"{args.workload} sampled at N={sample_n}",
                    "theta": w["theta"], "eps": w["eps"], "dt": w["dt"]},
         "cpu_baseline": {"value": value, "unit": "bodies/s", "cores": cores, "kind": "oracle",
                          "sample": sample},
