@@ -264,8 +264,8 @@ def measure_batch(nb, torch, dev, stream, steps=100):
 def measure_accuracy(nb, torch, dev, stream, n_targets=16384):
     """Force errors on the 1,048,576-body Plummer sphere (eps 0.005) against the FP64 direct
     sum on 16,384 sampled targets, per theta, for the plain FP64 path, the FP32-Kahan path and
-    the FP32-Kahan path with the grouped acceptance test (NBODY_FLAG_GROUP_MAC), with the walk
-    time of each on this GPU."""
+    the FP32-Kahan path with the grouped acceptance test (NBODY_FLAG_GROUP_MAC) or with
+    quadrupole cell terms (NBODY_FLAG_QUADRUPOLE), with the walk time of each on this GPU.""" 
     w = ics.WORKLOADS["plummer_1m"]
     pos, _, mass = ics.plummer(w["n"], w["seed"])
     n = w["n"]
@@ -304,7 +304,8 @@ def measure_accuracy(nb, torch, dev, stream, n_targets=16384):
         row = {}
         res = {}
         for name, prec, flags in (("fp64", nb.FP64, 0), ("fp32_kahan", nb.FP32_KAHAN, 0),
-                                  ("fp32_kahan_group_mac", nb.FP32_KAHAN, nb.FLAG_GROUP_MAC)):
+                                  ("fp32_kahan_group_mac", nb.FP32_KAHAN, nb.FLAG_GROUP_MAC),
+                                  ("fp32_kahan_quadrupole", nb.FP32_KAHAN, nb.FLAG_QUADRUPOLE)):
             with nb.Context(n, 1.0, w["eps"], theta, w["dt"], prec, stream=stream,
                             flags=flags) as ctx:
                 ctx.autotune(tp, tm)

@@ -67,8 +67,8 @@ typedef enum {
 
 /* Physical and numerical parameters.  G: gravitational constant; eps: Plummer softening length
  * (§2.1); theta: opening angle of the acceptance test l/d < theta (§3); dt: leapfrog time step
- * (§2.4); precision: nbody_precision; flags: 0, or NBODY_FLAG_GROUP_MAC and/or
- * NBODY_FLAG_CELL_GROUPS (FP32 forms only). */
+ * (§2.4); precision: nbody_precision; flags: a combination of NBODY_FLAG_GROUP_MAC and
+ * NBODY_FLAG_CELL_GROUPS (FP32 forms only) and NBODY_FLAG_QUADRUPOLE, or 0. */
 /* Flag: the grouped acceptance test of Barnes (1990) instead of the paper's per-body test
  * (FP32 forms only; EINVAL with NBODY_FP64).  Bodies are taken in Morton order in groups of 32;
  * a cell is accepted for all bodies of a group when l/d_min < theta, d_min being the distance
@@ -84,6 +84,16 @@ typedef enum {
  * summation order and the speed differ.  Always on with NBODY_FLAG_GROUP_MAC, whose shared lists
  * need compact groups. */
 #define NBODY_FLAG_CELL_GROUPS 2u
+
+/* Flag: accepted cells add their quadrupole term (§2.1, the truncated multipole expansion about
+ * the cell's centre of mass, where the dipole vanishes), softened like the monopole: with
+ * d = r_J - r_i and r_s^2 = |d|^2 + eps^2,
+ *   a_i += G (M d / r_s^3 - Q d / r_s^5 + 5/2 (d.Q.d) d / r_s^7),
+ *   Q_ab = sum_j m_j (3 x_a,j x_b,j - r_j^2 delta_ab) over the cell's bodies.
+ * All precisions.  The same cells are accepted (counters unchanged); forces are more accurate.
+ * Quadrupoles are built bottom-up (parallel-axis sums), so the FP64 path matches a body-by-body
+ * evaluation to rounding rather than bit for bit. */
+#define NBODY_FLAG_QUADRUPOLE 4u
 
 typedef struct {
     double G;

@@ -18,6 +18,9 @@ Parity status of each function (what pins it is in ``tests/test_oracle_pins.py``
     direct                               pinned (Kepler closed forms, Newton's third law)
     tree forces (Barnes-Hut)             pinned (theta = 0 equals direct sum, N = 2 exact,
                                          brute-force recursive walk on small N)
+    quadrupoles, quadrupole walk         pinned (two-body closed form, traceless and symmetric,
+                                         far-field error third order in size/distance against
+                                         second order for the monopole, smaller BH error)
     kdk                                  pinned (time reversibility, second-order convergence,
                                          circular Kepler orbit)
     bh_group (grouped acceptance test,   pinned (groups of one body equal the per-body walk term
@@ -84,6 +87,8 @@ def _load():
         "orc_tree_records": (i64, [vp, _i64p, vp]),
         "orc_tree_moments": (i64, [vp, _f64p]),
         "orc_tree_forces": (None, [vp, vp, i64, d, d, d, _f64p, vp, vp]),
+        "orc_tree_forces_q": (None, [vp, vp, i64, d, d, d, ctypes.c_int, _f64p, vp, vp]),
+        "orc_tree_quads": (i64, [vp, _f64p]),
         "orc_tree_cell_groups": (i64, [vp, i64, _i64p, _i64p]),
         "orc_tree_forces_group": (None, [vp, _i64p, _i64p, i64, d, d, d, _f64p, vp, vp]),
         "orc_bh": (None, [_f64p, _f64p, i64, d, d, d, _f64p, vp, vp]),
@@ -228,8 +233,17 @@ class Tree:
         k = _load().orc_tree_moments(self._h, out)
         return out[:k]
 
-    def forces(self, G=1.0, eps=0.0, theta=0.5, targets=None):
-        """Barnes-Hut accelerations (3, nt) and counters pp, pc (nt,) uint32."""
+    def quads(self):
+        """Quadrupole moments of every node in the order of records(): (n_nodes, 6) as
+        (xx, yy, zz, xy, xz, yz) about each node's centre of mass (§2.1)."""
+        nn = self.stats()["nodes"]
+        out = np.zeros((max(nn, 1), 6))
+        k = _load().orc_tree_quads(self._h, out)
+        return out[:k]
+
+    def forces(self, G=1.0, eps=0.0, theta=0.5, targets=None, quadrupole=False):
+        """Barnes-Hut accelerations (3, nt) and counters pp, pc (nt,) uint32.  quadrupole: accepted
+        cells add their quadrupole term (§2.1, softened like the monopole)."""
         if targets is None:
             nt = self.n
             tp = None
@@ -240,7 +254,8 @@ class Tree:
         acc = np.zeros((3, nt))
         pp = np.zeros(nt, dtype=np.uint32)
         pc = np.zeros(nt, dtype=np.uint32)
-        _load().orc_tree_forces(self._h, _ptr(tp), nt, G, eps, theta, acc, _ptr(pp), _ptr(pc))
+        _load().orc_tree_forces_q(self._h, _ptr(tp), nt, G, eps, theta, 1 if quadrupole else 0,
+                                  acc, _ptr(pp), _ptr(pc))
         return acc, pp, pc
 
 
@@ -292,11 +307,12 @@ def cell_groups(pos, mass, group=32):
         t.close()
 
 
-def bh(pos, mass, G=1.0, eps=0.0, theta=0.5):
-    """Barnes-Hut accelerations of all bodies plus (pp, pc) counters."""
+def bh(pos, mass, G=1.0, eps=0.0, theta=0.5, quadrupole=False):
+    """Barnes-Hut accelerations of all bodies plus (pp, pc) counters (with the cells' quadrupole
+    terms when `quadrupole`)."""
     t = Tree(pos, mass)
     try:
-        return t.forces(G, eps, theta)
+        return t.forces(G, eps, theta, quadrupole=quadrupole)
     finally:
         t.close()
 

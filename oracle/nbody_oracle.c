@@ -186,11 +186,13 @@ typedef struct {
     int32_t tail;
     int64_t nbody;        /* bodies in the subtree */
     double m, x, y, z;    /* total mass and centre of mass */
+    double q[6];          /* quadrupole about the centre of mass: xx, yy, zz, xy, xz, yz */
 } orc_node;
 
 typedef struct {
     orc_node *nodes;
     int64_t n_nodes, cap;
+    int has_quad;         /* quadrupoles computed (on first request) */
     int64_t n;
     int32_t *next;        /* body linked lists inside leaves (bucket members in id order) */
     uint32_t *q;          /* quantised coordinates, (3, n) */
@@ -431,6 +433,76 @@ int64_t orc_tree_moments(void *h, double *out)
 }
 
 /* ------------------------------------------------------------------ */
+/* Quadrupole moments (§2.1, eq. `truncmultipole` and the coefficients below it): about the     */
+/* cell's centre of mass, where the dipole vanishes,                                            */
+/*   Q_aa = sum_j m_j (3 x_a,j^2 - r_j^2),   Q_ab = sum_j m_j 3 x_a,j x_b,j  (a != b),          */
+/* x_j = r_j - r_J.  Computed here from that definition, body by body, for every cell.          */
+/* ------------------------------------------------------------------ */
+
+static void quad_add_bodies(const orc_tree *t, int32_t nd, const orc_node *J, double *q)
+{
+    const orc_node *N = &t->nodes[nd];
+    const double *X = t->pos, *Y = t->pos + t->n, *Z = t->pos + 2 * t->n;
+    if (N->is_leaf) {
+        for (int32_t j = N->head; j >= 0; j = t->next[j]) {
+            const double m = t->mass[j];
+            const double x = X[j] - J->x, y = Y[j] - J->y, z = Z[j] - J->z;
+            const double r2 = x * x + y * y + z * z;
+            q[0] += m * (3.0 * x * x - r2);
+            q[1] += m * (3.0 * y * y - r2);
+            q[2] += m * (3.0 * z * z - r2);
+            q[3] += m * (3.0 * x * y);
+            q[4] += m * (3.0 * x * z);
+            q[5] += m * (3.0 * y * z);
+        }
+        return;
+    }
+    for (int c = 0; c < 8; ++c)
+        if (N->child[c] >= 0) quad_add_bodies(t, N->child[c], J, q);
+}
+
+static void quads(orc_tree *t)
+{
+    if (t->has_quad) return;
+#pragma omp parallel for schedule(dynamic, 64) num_threads(g_threads)
+    for (int64_t k = 0; k < t->n_nodes; ++k) {
+        orc_node *J = &t->nodes[k];
+        for (int a = 0; a < 6; ++a) J->q[a] = 0.0;
+        quad_add_bodies(t, (int32_t)k, J, J->q);
+    }
+    t->has_quad = 1;
+}
+
+/* Cell term with the quadrupole: the acceleration -grad Phi of the softened truncated expansion
+ * Phi = -G (M / r_s + (x.Q.x) / (2 r_s^5)), x = r_p - r_J, r_s^2 = |x|^2 + eps^2, i.e. with
+ * d = r_J - r_p:  a += G (M d / r_s^3 - Q d / r_s^5 + 5/2 (d.Q.d) d / r_s^7). */
+static inline void accumulate_quad(double xp, double yp, double zp, const orc_node *C, double G,
+                                   double eps2, double *a)
+{
+    double dx = C->x - xp;
+    double dy = C->y - yp;
+    double dz = C->z - zp;
+    double r2 = dx * dx + dy * dy + dz * dz + eps2;
+    if (r2 > 0.0) {
+        const double *q = C->q;
+        double rinv = 1.0 / sqrt(r2);
+        double rinv2 = rinv * rinv;
+        double rinv3 = rinv * rinv2;
+        double rinv5 = rinv3 * rinv2;
+        double rinv7 = rinv5 * rinv2;
+        double qx = q[0] * dx + q[3] * dy + q[4] * dz;
+        double qy = q[3] * dx + q[1] * dy + q[5] * dz;
+        double qz = q[4] * dx + q[5] * dy + q[2] * dz;
+        double dqd = dx * qx + dy * qy + dz * qz;
+        double s = G * (C->m * rinv3 + 2.5 * dqd * rinv7);
+        double u = G * rinv5;
+        a[0] += s * dx - u * qx;
+        a[1] += s * dy - u * qy;
+        a[2] += s * dz - u * qz;
+    }
+}
+
+/* ------------------------------------------------------------------ */
 /* Barnes-Hut walk (Algorithm 2, "Compute Cell Force"; counters of Algorithm 9). */
 /* ------------------------------------------------------------------ */
 
@@ -440,6 +512,7 @@ typedef struct {
     double G, eps2, th2;
     double a[3];
     uint32_t pp, pc;
+    int quad;             /* accepted cells add the quadrupole term */
 } walk_state;
 
 static void walk(const orc_tree *t, int32_t nd, walk_state *w)
@@ -462,7 +535,10 @@ static void walk(const orc_tree *t, int32_t nd, walk_state *w)
             double dz = C->z - w->zp;
             double d2 = dx * dx + dy * dy + dz * dz;
             if (l * l < w->th2 * d2) {
-                accumulate(w->xp, w->yp, w->zp, C->x, C->y, C->z, C->m, w->G, w->eps2, w->a);
+                if (w->quad)
+                    accumulate_quad(w->xp, w->yp, w->zp, C, w->G, w->eps2, w->a);
+                else
+                    accumulate(w->xp, w->yp, w->zp, C->x, C->y, C->z, C->m, w->G, w->eps2, w->a);
                 w->pc += 1;
             } else {
                 walk(t, ch, w);
@@ -472,11 +548,13 @@ static void walk(const orc_tree *t, int32_t nd, walk_state *w)
 }
 
 /* Accelerations of the given targets (user ids; NULL = all bodies, nt ignored) on the tree.
- * acc is (3, nt) row-major; pp/pc (nt) may be NULL. */
-void orc_tree_forces(void *h, const int64_t *targets, int64_t nt, double G, double eps,
-                     double theta, double *acc, uint32_t *pp, uint32_t *pc)
+ * acc is (3, nt) row-major; pp/pc (nt) may be NULL.  quad != 0: accepted cells add their
+ * quadrupole term. */
+void orc_tree_forces_q(void *h, const int64_t *targets, int64_t nt, double G, double eps,
+                       double theta, int quad, double *acc, uint32_t *pp, uint32_t *pc)
 {
     orc_tree *t = (orc_tree *)h;
+    if (quad) quads(t);
     if (targets == NULL) nt = t->n;
     const double *X = t->pos, *Y = t->pos + t->n, *Z = t->pos + 2 * t->n;
     const double eps2 = eps * eps, th2 = theta * theta;
@@ -489,6 +567,7 @@ void orc_tree_forces(void *h, const int64_t *targets, int64_t nt, double G, doub
         w.G = G; w.eps2 = eps2; w.th2 = th2;
         w.a[0] = w.a[1] = w.a[2] = 0.0;
         w.pp = w.pc = 0;
+        w.quad = quad;
         if (!t->nodes[0].is_leaf) walk(t, 0, &w);
         acc[k] = w.a[0];
         acc[nt + k] = w.a[1];
@@ -496,6 +575,32 @@ void orc_tree_forces(void *h, const int64_t *targets, int64_t nt, double G, doub
         if (pp) pp[k] = w.pp;
         if (pc) pc[k] = w.pc;
     }
+}
+
+void orc_tree_forces(void *h, const int64_t *targets, int64_t nt, double G, double eps,
+                     double theta, double *acc, uint32_t *pp, uint32_t *pc)
+{
+    orc_tree_forces_q(h, targets, nt, G, eps, theta, 0, acc, pp, pc);
+}
+
+/* Quadrupole moments of every node in the pre-order of orc_tree_records:
+ * out[6k .. 6k+5] = (xx, yy, zz, xy, xz, yz). */
+static void emit_quads(const orc_tree *t, int32_t nd, double *out, int64_t *k)
+{
+    memcpy(out + 6 * (*k), t->nodes[nd].q, 6 * sizeof(double));
+    *k += 1;
+    if (t->nodes[nd].is_leaf) return;
+    for (int c = 0; c < 8; ++c)
+        if (t->nodes[nd].child[c] >= 0) emit_quads(t, t->nodes[nd].child[c], out, k);
+}
+
+int64_t orc_tree_quads(void *h, double *out)
+{
+    orc_tree *t = (orc_tree *)h;
+    quads(t);
+    int64_t k = 0;
+    if (t->n > 0) emit_quads(t, 0, out, &k);
+    return k;
 }
 
 /* One-shot Barnes-Hut accelerations of all bodies (build + walk + free). */

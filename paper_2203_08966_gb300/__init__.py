@@ -23,6 +23,7 @@ FP64, FP32, FP32_KAHAN = 0, 1, 2
 WALK_SHAPES = 3  # NBODY_WALK_SHAPES
 FLAG_GROUP_MAC = 1  # NBODY_FLAG_GROUP_MAC: grouped acceptance test (Barnes 1990), FP32 forms
 FLAG_CELL_GROUPS = 2  # NBODY_FLAG_CELL_GROUPS: FP32 walk groups follow the tree's cells
+FLAG_QUADRUPOLE = 4  # NBODY_FLAG_QUADRUPOLE: accepted cells add their quadrupole term
 PRECISIONS = {"fp64": FP64, "fp32": FP32, "fp32_kahan": FP32_KAHAN}
 
 STATUS = {0: "NBODY_OK", 1: "NBODY_EINVAL", 2: "NBODY_ENOMEM", 3: "NBODY_ECUDA",

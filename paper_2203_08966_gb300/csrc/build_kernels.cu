@@ -624,6 +624,33 @@ __device__ __forceinline__ D4 ld_cg(const D4 *p)
     return r;
 }
 
+// Adds a mass m at offset (x, y, z) from a centre of mass to a quadrupole (§2.1):
+// Q_ab += m (3 x_a x_b - r^2 delta_ab), components xx, yy, zz, xy, xz, yz.
+__device__ __forceinline__ void quad_add(double q[6], double m, double x, double y, double z)
+{
+    const double r2 = x * x + y * y + z * z;
+    q[0] += m * (3.0 * x * x - r2);
+    q[1] += m * (3.0 * y * y - r2);
+    q[2] += m * (3.0 * z * z - r2);
+    q[3] += m * (3.0 * x * y);
+    q[4] += m * (3.0 * x * z);
+    q[5] += m * (3.0 * y * z);
+}
+
+__device__ __forceinline__ void store_quad(NodeArrays &na, int j, int b, const double q[6],
+                                           double G)
+{
+    for (int k = 0; k < 6; ++k) {
+        na.q_lo[6 * (size_t)b + k] = q[k];
+        na.q64[6 * (size_t)j + k] = q[k];
+    }
+    if (na.gq) {
+        na.gq[2 * (size_t)b] = make_float4((float)(G * q[0]), (float)(G * q[1]), (float)(G * q[2]),
+                                           (float)(G * q[3]));
+        na.gq[2 * (size_t)b + 1] = make_float4((float)(G * q[4]), (float)(G * q[5]), 0.f, 0.f);
+    }
+}
+
 __device__ __forceinline__ void store_node(NodeArrays &na, int j, const WalkNode &w0, const D4 &m,
                                            const Box *box, double G, float crit)
 {
@@ -670,6 +697,16 @@ __global__ void link_leaves_kernel(const uint64_t *__restrict__ keys, NodeArrays
             const int b = na.order[j];
             na.com_lo[b] = m;
             na.lo_child[b] = make_int4(0, 0, w.first, 0);
+            if (na.q_lo) {
+                // quadrupole of the leaf's bodies about their centre of mass (§2.1): 0 for one
+                // body; a bucket sums over its members
+                double q[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+                for (int p = w.first; w.count > 1 && p < w.first + w.count; ++p) {
+                    const D4 r = sbody64[p];
+                    quad_add(q, r.w, r.x - m.x, r.y - m.y, r.z - m.z);
+                }
+                store_quad(na, j, b, q, G);
+            }
             continue;
         }
         const int shift = 3 * (kMaxLevel - 1 - lev);
@@ -720,6 +757,17 @@ __global__ void moments_level_kernel(int level, NodeArrays na, const Box *__rest
         na.wn[j].c = make_float4((float)(m.x - bx->c[0]), (float)(m.y - bx->c[1]),
                                  (float)(m.z - bx->c[2]), (float)(G * m.w));
         na.wn[j].crit = tab[k].crit32[level];
+        if (na.q_lo) {
+            // parallel-axis sum: each child's quadrupole plus its mass at its offset
+            double q[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+            for (int c = 0; c < min(ch.y, 8); ++c) {
+                const D4 r = ld_cg(&na.com_lo[ch.x + c]);
+                const double *qc = na.q_lo + 6 * (size_t)(ch.x + c);
+                for (int e = 0; e < 6; ++e) q[e] += __ldcg(qc + e);
+                quad_add(q, r.w, r.x - m.x, r.y - m.y, r.z - m.z);
+            }
+            store_quad(na, j, t, q, G);
+        }
     }
 }
 

@@ -44,6 +44,10 @@ struct nbody_ctx {
     NodeArrays na{};
     int64_t n_nodes = 0;
     GroupNode *gn = nullptr;        // level-order copy for the FP32 group walk (capacity na.cap)
+    // quadrupoles (NBODY_FLAG_QUADRUPOLE), capacity quad_cap nodes
+    double *q_lo = nullptr, *q64 = nullptr;
+    float4 *gq = nullptr;
+    int64_t quad_cap = 0;
 
     // forest (n_sys > 0): systems packed in one set of arrays
     int n_sys = 0;
@@ -125,9 +129,9 @@ bool params_ok(const nbody_params *p)
     if (!(p->eps >= 0.0) || !isfinite(p->eps)) return false;
     if (!(p->theta >= 0.0) || !isfinite(p->theta)) return false;
     if (p->precision < NBODY_FP64 || p->precision > NBODY_FP32_KAHAN) return false;
-    const uint32_t known = NBODY_FLAG_GROUP_MAC | NBODY_FLAG_CELL_GROUPS;
-    if ((p->flags & ~known) != 0) return false;
-    if ((p->flags & known) && p->precision == NBODY_FP64) return false;
+    const uint32_t fp32_only = NBODY_FLAG_GROUP_MAC | NBODY_FLAG_CELL_GROUPS;
+    if ((p->flags & ~(fp32_only | NBODY_FLAG_QUADRUPOLE)) != 0) return false;
+    if ((p->flags & fp32_only) && p->precision == NBODY_FP64) return false;
     return true;
 }
 
@@ -160,7 +164,34 @@ void free_nodes(nbody_ctx *c)
     dfree(c->na.tile_offsets);
     dfree(c->na.block_sums);
     dfree(c->gn);
+    dfree(c->q_lo);
+    dfree(c->q64);
+    dfree(c->gq);
+    c->quad_cap = 0;
+    c->na.q_lo = c->na.q64 = nullptr;
+    c->na.gq = nullptr;
     c->na.cap = 0;
+}
+
+// Quadrupole arrays for the current node capacity when the flag asks for them (allocates only
+// when the capacity grew: at creation, set_params or a larger tree, never inside a forest step).
+nbody_status ensure_quad(nbody_ctx *c)
+{
+    const bool quad = (c->p.flags & NBODY_FLAG_QUADRUPOLE) != 0;
+    if (quad && c->quad_cap < c->na.cap) {
+        dfree(c->q_lo);
+        dfree(c->q64);
+        dfree(c->gq);
+        c->quad_cap = 0;
+        CK(dalloc(&c->q_lo, 6 * (size_t)c->na.cap));
+        CK(dalloc(&c->q64, 6 * (size_t)c->na.cap));
+        CK(dalloc(&c->gq, 2 * (size_t)c->na.cap));
+        c->quad_cap = c->na.cap;
+    }
+    c->na.q_lo = quad ? c->q_lo : nullptr;
+    c->na.q64 = quad ? c->q64 : nullptr;
+    c->na.gq = quad ? c->gq : nullptr;
+    return NBODY_OK;
 }
 
 nbody_status ensure_nodes(nbody_ctx *c, int64_t need)
@@ -244,6 +275,7 @@ nbody_status build(nbody_ctx *c, const double *pos, const double *mass, int n,
         return fail(c, NBODY_EINVAL, "%lld tree nodes: the FP32 walk indexes at most %lld",
                     (long long)nn, (long long)kMaxGroupNodes);
     CKS(ensure_nodes(c, nn));
+    CKS(ensure_quad(c));
     c->n_nodes = nn;
     c->na.d_nn = c->node_off + n;
     launch_emit_nodes(c->keys, n, one, c->node_off, c->na, c->err, s);
@@ -297,6 +329,8 @@ nbody_status walk(nbody_ctx *c, int n, double *acc, double *vel, double h)
     a.node_off = c->node_off;
     a.start = c->sys_start;
     a.group_mac = (c->p.flags & NBODY_FLAG_GROUP_MAC) != 0;
+    a.q64 = c->na.q64;
+    a.gq = c->p.precision != NBODY_FP64 ? c->na.gq : nullptr;
     launch_walk(c->p.precision, a, c->p.precision == NBODY_FP64 ? c->shape64 : c->shape32,
                 c->stream);
     record(c, 4);
@@ -328,6 +362,7 @@ nbody_status forest_build(nbody_ctx *c, const double *pos, const double *mass)
     ScanScratch sn{c->block_sums, scan_tiles(n + 1)};
     launch_exclusive_scan(c->node_off, c->node_off, n + 1, sn, s);
     launch_clamp_count(c->node_off + n, c->na.cap, c->nn, c->err, s);
+    CKS(ensure_quad(c));  // pointers only: the arrays exist since creation / set_params
     c->na.d_nn = c->nn;
     launch_emit_nodes(c->keys, n, ss, c->node_off, c->na, c->err, s);
     launch_level_order(c->na, s);
@@ -486,6 +521,7 @@ nbody_status nbody_set_params(nbody_ctx *c, const nbody_params *p)
     if (!params_ok(p)) return fail(c, NBODY_EINVAL, "invalid parameters");
     c->p = *p;
     c->acc_n = -1;
+    CKS(ensure_quad(c));
     if (c->gexec) {  // the captured step holds the old parameters
         cudaGraphExecDestroy(c->gexec);
         c->gexec = nullptr;
@@ -892,6 +928,7 @@ nbody_status nbody_forest_create(nbody_ctx **out, int32_t n_systems, const int64
         // the node count is only known on the device during a step: room for 4 nodes per body
         // (Plummer-like systems need about 1.5) plus a full chain of 22 levels per system
         CKS(ensure_nodes(c, 4 * n + 22 * (int64_t)S + 1024));
+        CKS(ensure_quad(c));
         if (c->na.cap > kMaxGroupNodes)
             return fail(c, NBODY_EINVAL, "forest of %lld bodies exceeds the node index range",
                         (long long)n);

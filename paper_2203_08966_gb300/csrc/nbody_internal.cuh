@@ -124,6 +124,12 @@ struct NodeArrays {
     int *order;               // pre-order index -> level-order index
     int *inv;                 // level-order index -> pre-order index
     D4 *com_lo;               // FP64 moments in level order
+    // quadrupoles about each node's centre of mass (null unless requested): 6 doubles per node
+    // (xx, yy, zz, xy, xz, yz), in level order and in pre-order; FP32 G*Q for the group walk,
+    // two float4 per node in level order: (xx, yy, zz, xy), (xz, yz, 0, 0)
+    double *q_lo;
+    double *q64;
+    float4 *gq;
     int4 *lo_child;           // level order: (first child, child count, first body, 0); count 0 = leaf
     uint32_t *tile_offsets;   // level-major (level, tile) offsets; level l starts at [l * tiles]
     uint32_t *block_sums;     // scan scratch for tile_offsets
@@ -204,6 +210,8 @@ struct WalkArgs {
     const uint32_t *node_off;  // pre-order: nodes of system k are node_off[start[k]] ..
     const int *start;     // system starts (bodies)
     bool group_mac;       // FP32 walks: grouped acceptance test (NBODY_FLAG_GROUP_MAC)
+    const double *q64;    // quadrupoles (pre-order) for the FP64 walk, null without them
+    const float4 *gq;     // G * quadrupoles (level order) for the FP32 walk, null without them
     const unsigned *d_ngroups;  // groups built on the device: their count (n_groups = capacity)
     unsigned *work;       // FP32 walk: group counter of the persistent warps (zeroed per launch)
 };

@@ -60,6 +60,59 @@ __device__ __forceinline__ void pair64(double xj, double yj, double zj, double m
     }
 }
 
+// FP64 cell term with the quadrupole (§2.1, eq. `truncmultipole`): the acceleration of the
+// softened expansion Phi = -G (M / r_s + (x.Q.x) / (2 r_s^5)), x = r_i - r_J,
+// r_s^2 = |x|^2 + eps^2; with d = r_J - r_i:
+//   a += G (M d / r_s^3 - Q d / r_s^5 + 5/2 (d.Q.d) d / r_s^7),
+// q = (xx, yy, zz, xy, xz, yz); every operation separately rounded.
+__device__ __forceinline__ void cell64q(double xj, double yj, double zj, double mj,
+                                        const double *__restrict__ q, double xi, double yi,
+                                        double zi, double G, double eps2, double &ax, double &ay,
+                                        double &az)
+{
+    const double dx = __dsub_rn(xj, xi), dy = __dsub_rn(yj, yi), dz = __dsub_rn(zj, zi);
+    const double r2 = __dadd_rn(__dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)),
+                                          __dmul_rn(dz, dz)), eps2);
+    if (!(r2 > 0.0)) return;
+    const double rinv = __ddiv_rn(1.0, __dsqrt_rn(r2));
+    const double rinv2 = __dmul_rn(rinv, rinv);
+    const double rinv3 = __dmul_rn(rinv, rinv2);
+    const double rinv5 = __dmul_rn(rinv3, rinv2);
+    const double rinv7 = __dmul_rn(rinv5, rinv2);
+    const double qx = __dadd_rn(__dadd_rn(__dmul_rn(q[0], dx), __dmul_rn(q[3], dy)), __dmul_rn(q[4], dz));
+    const double qy = __dadd_rn(__dadd_rn(__dmul_rn(q[3], dx), __dmul_rn(q[1], dy)), __dmul_rn(q[5], dz));
+    const double qz = __dadd_rn(__dadd_rn(__dmul_rn(q[4], dx), __dmul_rn(q[5], dy)), __dmul_rn(q[2], dz));
+    const double dqd = __dadd_rn(__dadd_rn(__dmul_rn(dx, qx), __dmul_rn(dy, qy)), __dmul_rn(dz, qz));
+    const double s = __dmul_rn(G, __dadd_rn(__dmul_rn(mj, rinv3), __dmul_rn(__dmul_rn(2.5, dqd), rinv7)));
+    const double u = __dmul_rn(G, rinv5);
+    ax = __dadd_rn(ax, __dsub_rn(__dmul_rn(s, dx), __dmul_rn(u, qx)));
+    ay = __dadd_rn(ay, __dsub_rn(__dmul_rn(s, dy), __dmul_rn(u, qy)));
+    az = __dadd_rn(az, __dsub_rn(__dmul_rn(s, dz), __dmul_rn(u, qz)));
+}
+
+// FP32 cell term with the quadrupole (the same expansion): c = (x - c0, y - c0, z - c0, G M),
+// q0 = G (xx, yy, zz, xy), q1 = G (xz, yz, -, -); on = 0 drops the term.
+template <bool kGuard>
+__device__ __forceinline__ void cell32q(const float4 &c, const float4 &q0, const float4 &q1,
+                                        float xi, float yi, float zi, float eps2, float on,
+                                        float &ax, float &ay, float &az)
+{
+    const float dx = c.x - xi, dy = c.y - yi, dz = c.z - zi;
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
+    float ri = rsqrtf(r2);
+    if (kGuard) ri = r2 > 0.f ? ri : 0.f;
+    ri *= on;
+    const float ri2 = ri * ri, ri3 = ri * ri2, ri5 = ri3 * ri2, ri7 = ri5 * ri2;
+    const float qx = fmaf(q0.x, dx, fmaf(q0.w, dy, q1.x * dz));
+    const float qy = fmaf(q0.w, dx, fmaf(q0.y, dy, q1.y * dz));
+    const float qz = fmaf(q1.x, dx, fmaf(q1.y, dy, q0.z * dz));
+    const float dqd = fmaf(dx, qx, fmaf(dy, qy, dz * qz));
+    const float s = fmaf(c.w, ri3, 2.5f * dqd * ri7);
+    ax = fmaf(s, dx, fmaf(-ri5, qx, ax));
+    ay = fmaf(s, dy, fmaf(-ri5, qy, ay));
+    az = fmaf(s, dz, fmaf(-ri5, qz, az));
+}
+
 // One step of Kahan's compensated summation (Kahan 1965): s + c tracks the exact running sum.
 __device__ __forceinline__ void kahan_add(float &s, float &c, float t)
 {
@@ -128,6 +181,20 @@ struct GroupSmem {
     float4 p[kPCap];              // partial sources, paired
     uint2 pm[kPCap];              // (body mask, 1 for a leaf body / 0 for a cell) per entry
 };
+
+// With quadrupoles, accepted cells go to their own buffers (their term needs G Q): centre of
+// mass and mass, then G (xx, yy, zz, xy) and G (xz, yz, -, -); the partial ones with a mask.
+constexpr int kQCap = 32;
+struct QuadSmem {
+    float4 fc[kQCap], fq0[kQCap], fq1[kQCap];
+    float4 pc[kQCap], pq0[kQCap], pq1[kQCap];
+    uint32_t pm[kQCap];
+};
+template <bool kQuad>
+__host__ __device__ constexpr size_t group_smem_bytes()
+{
+    return kQuad ? sizeof(GroupSmem) + sizeof(QuadSmem) : sizeof(GroupSmem);
+}
 
 __device__ __forceinline__ void put_entry(float4 *buf, int e, const float4 &c)
 {
@@ -256,6 +323,33 @@ struct GroupEval {
             terms = 0;
         }
     }
+    // quadrupole cells: every live body of the group (full) or the masked ones (part)
+    __device__ __forceinline__ void full_quad(const QuadSmem &Q, int cnt, const float4 &me,
+                                              float eps2)
+    {
+        float ax = 0.f, ay = 0.f, az = 0.f;
+        for (int e = 0; e < cnt; ++e)
+            cell32q<kGuard>(Q.fc[e], Q.fq0[e], Q.fq1[e], me.x, me.y, me.z, eps2, 1.f, ax, ay, az);
+        acc.x.x += ax;
+        acc.y.x += ay;
+        acc.z.x += az;
+        settle(cnt);
+    }
+    __device__ __forceinline__ void part_quad(const QuadSmem &Q, int cnt, const float4 &me,
+                                              float eps2, int lane)
+    {
+        float ax = 0.f, ay = 0.f, az = 0.f;
+        for (int e = 0; e < cnt; ++e) {
+            const uint32_t on = (Q.pm[e] >> lane) & 1u;
+            cell32q<kGuard>(Q.pc[e], Q.pq0[e], Q.pq1[e], me.x, me.y, me.z, eps2, (float)on, ax,
+                            ay, az);
+            pc += on;
+        }
+        acc.x.x += ax;
+        acc.y.x += ay;
+        acc.z.x += az;
+        settle(cnt);
+    }
     // cnt entries, padded to an even count by the caller (a zero-weight entry)
     __device__ __forceinline__ void full(const GroupSmem &S, int cnt, const float2 *nme,
                                          float2 eps2)
@@ -289,15 +383,16 @@ struct GroupEval {
 };
 
 // kWarps warps per block (a launch shape the autotuner chooses; results do not depend on it).
+// kQuad: accepted cells add their quadrupole term (§2.1).
 // kGroup: the grouped acceptance test (Barnes 1990; not in the paper): a cell is accepted for
 // the whole group when the lower bound of the group's distances passes the test, else it is
 // opened for the whole group; no body masks, no per-body tests.  A body meets its own leaf and
 // interacts with itself there, which adds exactly zero (zero separation), and is not counted.
 // The walk of one group (bodies g0 .. g0 + gcount - 1, its system's root at level-order index
 // root) by one warp with its shared-memory slice S.
-template <bool kKahan, bool kGuard, bool kGroup>
-__device__ __forceinline__ void walk_group(const WalkArgs &a, GroupSmem &S, int lane, int g0,
-                                           int gcount, int root)
+template <bool kKahan, bool kGuard, bool kGroup, bool kQuad>
+__device__ __forceinline__ void walk_group(const WalkArgs &a, GroupSmem &S, QuadSmem &Q, int lane,
+                                           int g0, int gcount, int root)
 {
     const int i = g0 + lane;
     const bool live = lane < gcount;
@@ -317,6 +412,7 @@ __device__ __forceinline__ void walk_group(const WalkArgs &a, GroupSmem &S, int 
     uint32_t upp = 0, upc = 0;    // full-entry counts (the same for every live body)
     unsigned self_seen = 0u;      // group walk: bodies whose own leaf entered the list
     int sp = 0, fn = 0, pn = 0;   // stack depth and buffer fills (warp-uniform)
+    int qfn = 0, qpn = 0;         // quadrupole-cell buffer fills (warp-uniform)
 
     // the root is never tested: the walk starts with the root's children (none when the root
     // is a leaf, i.e. a single body)
@@ -331,8 +427,34 @@ __device__ __forceinline__ void walk_group(const WalkArgs &a, GroupSmem &S, int 
         }
     }
 
-    // appends one entry per lane whose kind says so: full-group entries to f, others to p
-    auto emit = [&](int kind, const float4 &c, unsigned m) {
+    // appends one entry per lane whose kind says so: full-group entries to f, others to p;
+    // with quadrupoles accepted cells go to their own buffers, with their G Q (node: level-order
+    // index of the cell)
+    auto emit = [&](int kind, const float4 &c, unsigned m, int node) {
+        if (kQuad) {
+            const bool qf = kind == kFullCell, qp = kind == kPartCell;
+            const unsigned qfb = __ballot_sync(kFull, qf), qpb = __ballot_sync(kFull, qp);
+            if (qf || qp) {
+                const float4 q0 = ldg4(a.gq + 2 * (size_t)node);
+                const float4 q1 = ldg4(a.gq + 2 * (size_t)node + 1);
+                if (qf) {
+                    const int o = qfn + __popc(qfb & lt);
+                    Q.fc[o] = c;
+                    Q.fq0[o] = q0;
+                    Q.fq1[o] = q1;
+                } else {
+                    const int o = qpn + __popc(qpb & lt);
+                    Q.pc[o] = c;
+                    Q.pq0[o] = q0;
+                    Q.pq1[o] = q1;
+                    Q.pm[o] = m;
+                }
+            }
+            qfn += __popc(qfb);
+            qpn += __popc(qpb);
+            upc += __popc(qfb);
+            if (qf || qp) kind = kNone;
+        }
         const bool isf = kind == kFullLeaf || kind == kFullCell;
         const unsigned fb = __ballot_sync(kFull, isf);
         if (isf) put_entry(S.f, fn + __popc(fb & lt), c);
@@ -361,6 +483,11 @@ __device__ __forceinline__ void walk_group(const WalkArgs &a, GroupSmem &S, int 
         __syncwarp();
         if (fn > 0) ev.full(S, fn, nme, eps2);
         if (pn > 0) ev.part(S, pn, nme, eps2, lane);
+        if (kQuad) {
+            if (qfn > 0) ev.full_quad(Q, qfn, me, eps2s);
+            if (qpn > 0) ev.part_quad(Q, qpn, me, eps2s, lane);
+            qfn = qpn = 0;
+        }
         fn = pn = 0;
         __syncwarp();
     };
@@ -504,7 +631,7 @@ __device__ __forceinline__ void walk_group(const WalkArgs &a, GroupSmem &S, int 
         }
 
         // ---- buffer the entries, push the children
-        emit(kind, c, emask);
+        emit(kind, c, emask, node);
         {
             const bool isp = pmask != 0u;
             const unsigned ob = __ballot_sync(kFull, isp);
@@ -539,7 +666,7 @@ __device__ __forceinline__ void walk_group(const WalkArgs &a, GroupSmem &S, int 
                     if (d < 32u) mb &= ~(1u << d);
                     kb = (!h || mb == 0u) ? kNone : (mb == live_mask ? kFullLeaf : kPartLeaf);
                 }
-                emit(kb, s, mb);
+                emit(kb, s, mb, 0);
             }
         }
     }
@@ -551,11 +678,13 @@ __device__ __forceinline__ void walk_group(const WalkArgs &a, GroupSmem &S, int 
                   ev.pc - ev.pp + upc);
 }
 
-template <int kWarps, bool kKahan, bool kGuard, bool kGroup>
+template <int kWarps, bool kKahan, bool kGuard, bool kGroup, bool kQuad>
 __global__ void __launch_bounds__(kWarps * 32) group_walk32_kernel(WalkArgs a)
 {
     extern __shared__ __align__(16) unsigned char group_smem[];
-    GroupSmem &S = reinterpret_cast<GroupSmem *>(group_smem)[threadIdx.x >> 5];
+    unsigned char *slice = group_smem + group_smem_bytes<kQuad>() * (threadIdx.x >> 5);
+    GroupSmem &S = *reinterpret_cast<GroupSmem *>(slice);
+    QuadSmem &Q = *reinterpret_cast<QuadSmem *>(slice + sizeof(GroupSmem));  // used with kQuad
     const int lane = threadIdx.x & 31;
     // persistent warps: each takes the next group from the shared counter until none is left
     for (;;) {
@@ -564,7 +693,7 @@ __global__ void __launch_bounds__(kWarps * 32) group_walk32_kernel(WalkArgs a)
         gi = __shfl_sync(kFull, gi, 0);
         int g0, gcount, root;
         if (!group_of(a, (int)gi, g0, gcount, root)) break;  // uniform per warp
-        walk_group<kKahan, kGuard, kGroup>(a, S, lane, g0, gcount, root);
+        walk_group<kKahan, kGuard, kGroup, kQuad>(a, S, Q, lane, g0, gcount, root);
         __syncwarp();
     }
 }
@@ -622,7 +751,11 @@ __global__ void __launch_bounds__(kThreads) walk64_kernel(WalkArgs a)
                                         __dmul_rn(dz, dz));
             const double l2 = tab->l2[a.level[j]];
             if (l2 < __dmul_rn(th2, d2)) {
-                pair64(s.x, s.y, s.z, s.w, me.x, me.y, me.z, G, eps2, ax, ay, az);
+                if (a.q64)
+                    cell64q(s.x, s.y, s.z, s.w, a.q64 + 6 * (size_t)j, me.x, me.y, me.z, G, eps2,
+                            ax, ay, az);
+                else
+                    pair64(s.x, s.y, s.z, s.w, me.x, me.y, me.z, G, eps2, ax, ay, az);
                 ++pc;
                 next = skip;
             } else {
@@ -757,65 +890,81 @@ namespace {
 // threads per block.
 // Blocks of the persistent group walk: as many as fit on the GPU at once (never more than the
 // groups need).
-template <int kWarps, bool kGroup>
-int persistent_blocks(bool kahan, bool guard, int64_t groups)
+template <int kWarps, bool kKahan, bool kGuard, bool kGroup, bool kQuad>
+int persistent_blocks(int64_t groups)
 {
-    static int resident[2][2] = {{0, 0}, {0, 0}};  // [kahan][guard], per process
-    int &r = resident[kahan][guard];
-    if (r == 0) {
+    static int resident = 0;  // per kernel instance, per process
+    if (resident == 0) {
         int dev = 0, sms = 0, per_sm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        const void *f = kahan ? (guard ? (const void *)group_walk32_kernel<kWarps, true, true, kGroup>
-                                       : (const void *)group_walk32_kernel<kWarps, true, false, kGroup>)
-                              : (guard ? (const void *)group_walk32_kernel<kWarps, false, true, kGroup>
-                                       : (const void *)group_walk32_kernel<kWarps, false, false, kGroup>);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, kWarps * 32,
-                                                      sizeof(GroupSmem) * kWarps);
-        r = std::max(1, sms) * std::max(1, per_sm);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &per_sm, group_walk32_kernel<kWarps, kKahan, kGuard, kGroup, kQuad>, kWarps * 32,
+            group_smem_bytes<kQuad>() * kWarps);
+        resident = std::max(1, sms) * std::max(1, per_sm);
     }
-    return (int)std::min<int64_t>((groups + kWarps - 1) / kWarps, r);
+    return (int)std::min<int64_t>((groups + kWarps - 1) / kWarps, resident);
 }
 
-template <int kWarps, bool kGroup>
-void launch_group(const WalkArgs &a, int64_t groups, bool kahan, bool guard, cudaStream_t s)
+template <int kWarps, bool kKahan, bool kGuard, bool kGroup, bool kQuad>
+void launch_group_variant(const WalkArgs &a, int64_t groups, cudaStream_t s)
 {
-    const int blocks = persistent_blocks<kWarps, kGroup>(kahan, guard, groups);
-    const size_t smem = sizeof(GroupSmem) * kWarps;
-    const int t = kWarps * 32;
-    if (kahan) {
-        if (guard) group_walk32_kernel<kWarps, true, true, kGroup><<<blocks, t, smem, s>>>(a);
-        else group_walk32_kernel<kWarps, true, false, kGroup><<<blocks, t, smem, s>>>(a);
+    const int blocks = persistent_blocks<kWarps, kKahan, kGuard, kGroup, kQuad>(groups);
+    group_walk32_kernel<kWarps, kKahan, kGuard, kGroup, kQuad>
+        <<<blocks, kWarps * 32, group_smem_bytes<kQuad>() * kWarps, s>>>(a);
+}
+
+template <int kWarps, bool kKahan, bool kGuard>
+void launch_group(const WalkArgs &a, int64_t groups, cudaStream_t s)
+{
+    const bool quad = a.gq != nullptr;
+    if (a.group_mac) {
+        if (quad) launch_group_variant<kWarps, kKahan, kGuard, true, true>(a, groups, s);
+        else launch_group_variant<kWarps, kKahan, kGuard, true, false>(a, groups, s);
     } else {
-        if (guard) group_walk32_kernel<kWarps, false, true, kGroup><<<blocks, t, smem, s>>>(a);
-        else group_walk32_kernel<kWarps, false, false, kGroup><<<blocks, t, smem, s>>>(a);
+        if (quad) launch_group_variant<kWarps, kKahan, kGuard, false, true>(a, groups, s);
+        else launch_group_variant<kWarps, kKahan, kGuard, false, false>(a, groups, s);
     }
 }
 
 template <int kWarps>
 void launch_group(const WalkArgs &a, int64_t groups, bool kahan, bool guard, cudaStream_t s)
 {
-    if (a.group_mac) launch_group<kWarps, true>(a, groups, kahan, guard, s);
-    else launch_group<kWarps, false>(a, groups, kahan, guard, s);
+    if (kahan) {
+        if (guard) launch_group<kWarps, true, true>(a, groups, s);
+        else launch_group<kWarps, true, false>(a, groups, s);
+    } else {
+        if (guard) launch_group<kWarps, false, true>(a, groups, s);
+        else launch_group<kWarps, false, false>(a, groups, s);
+    }
+}
+
+template <int kWarps, bool kKahan, bool kGuard>
+cudaError_t allow_group_smem_kg()
+{
+    const void *fns[4] = {(const void *)group_walk32_kernel<kWarps, kKahan, kGuard, false, false>,
+                          (const void *)group_walk32_kernel<kWarps, kKahan, kGuard, true, false>,
+                          (const void *)group_walk32_kernel<kWarps, kKahan, kGuard, false, true>,
+                          (const void *)group_walk32_kernel<kWarps, kKahan, kGuard, true, true>};
+    const int bytes[4] = {(int)(group_smem_bytes<false>() * kWarps),
+                          (int)(group_smem_bytes<false>() * kWarps),
+                          (int)(group_smem_bytes<true>() * kWarps),
+                          (int)(group_smem_bytes<true>() * kWarps)};
+    for (int k = 0; k < 4; ++k) {
+        const cudaError_t e =
+            cudaFuncSetAttribute(fns[k], cudaFuncAttributeMaxDynamicSharedMemorySize, bytes[k]);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 template <int kWarps>
 cudaError_t allow_group_smem()
 {
-    const int bytes = (int)(sizeof(GroupSmem) * kWarps);
-    cudaError_t e = cudaSuccess;
-    const void *fns[8] = {(const void *)group_walk32_kernel<kWarps, true, true, false>,
-                          (const void *)group_walk32_kernel<kWarps, true, false, false>,
-                          (const void *)group_walk32_kernel<kWarps, false, true, false>,
-                          (const void *)group_walk32_kernel<kWarps, false, false, false>,
-                          (const void *)group_walk32_kernel<kWarps, true, true, true>,
-                          (const void *)group_walk32_kernel<kWarps, true, false, true>,
-                          (const void *)group_walk32_kernel<kWarps, false, true, true>,
-                          (const void *)group_walk32_kernel<kWarps, false, false, true>};
-    for (const void *f : fns) {
-        e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-        if (e != cudaSuccess) return e;
-    }
+    cudaError_t e = allow_group_smem_kg<kWarps, true, true>();
+    if (e == cudaSuccess) e = allow_group_smem_kg<kWarps, true, false>();
+    if (e == cudaSuccess) e = allow_group_smem_kg<kWarps, false, true>();
+    if (e == cudaSuccess) e = allow_group_smem_kg<kWarps, false, false>();
     return e;
 }
 

@@ -91,7 +91,7 @@ def test_group_mac_flag_rejected_for_fp64_without_gpu(lib_path):
     h = ctypes.c_void_p()
     bad = nb.Params(1.0, 0.01, 0.5, 1e-3, nb.FP64, nb.FLAG_GROUP_MAC)
     assert lib.nbody_create(ctypes.byref(h), 10, ctypes.byref(bad), None) == 1
-    unknown = nb.Params(1.0, 0.01, 0.5, 1e-3, nb.FP32, 4)
+    unknown = nb.Params(1.0, 0.01, 0.5, 1e-3, nb.FP32, 8)
     assert lib.nbody_create(ctypes.byref(h), 10, ctypes.byref(unknown), None) == 1
     cells64 = nb.Params(1.0, 0.01, 0.5, 1e-3, nb.FP64, nb.FLAG_CELL_GROUPS)
     assert lib.nbody_create(ctypes.byref(h), 10, ctypes.byref(cells64), None) == 1

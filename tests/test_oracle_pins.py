@@ -563,3 +563,71 @@ def test_cell_groups_match_brute_force_rule(name):
     want = _cell_groups_from_keys(pos, 32)
     assert sorted(map(sorted, got)) == sorted(map(sorted, want))
     assert max(len(g) for g in got) <= 32
+
+
+# ---- quadrupole moments (§2.1, truncated multipole expansion) ------------------------------
+
+def test_quadrupole_two_body_closed_form():
+    """Two masses m at (+-a, 0, 0): about their centre of mass Q_xx = 4 m a^2,
+    Q_yy = Q_zz = -2 m a^2, no off-diagonal terms."""
+    a, m = 0.7, 0.3
+    pos = np.array([[-a, a], [0.0, 0.0], [0.0, 0.0]])
+    t = oracle.Tree(pos, np.array([m, m]))
+    q = t.quads()[0]   # the root
+    t.close()
+    assert np.allclose(q, [4 * m * a * a, -2 * m * a * a, -2 * m * a * a, 0, 0, 0], rtol=1e-14,
+                       atol=1e-15)
+
+
+def test_quadrupoles_are_traceless_and_vanish_for_single_bodies():
+    pos, _, mass = ics.plummer(500, 61)
+    t = oracle.Tree(pos, mass)
+    q = t.quads()
+    rec = t.records()
+    t.close()
+    scale = np.abs(q).max(axis=1) + 1e-300
+    assert np.all(np.abs(q[:, 0] + q[:, 1] + q[:, 2]) <= 1e-12 * scale)
+    single = rec[:, 4] == 1
+    assert np.all(q[single] == 0.0)
+
+
+def test_quadrupole_far_field_error_is_third_order():
+    """A small cluster (radius 0.5) seen from a body at distance R: with the cell accepted, the
+    monopole's relative error falls as (a/R)^2 (the dipole vanishes about the centre of mass),
+    the quadrupole expansion's as (a/R)^3."""
+    rng = np.random.default_rng(62)
+    k = 30
+    u = rng.normal(size=(3, k))
+    u *= 0.5 * rng.uniform(0, 1, k) ** (1 / 3) / np.linalg.norm(u, axis=0)
+    mass = np.concatenate([rng.uniform(0.5, 1.5, k), [1.0]])
+    direction = np.array([1.0, 0.3, 0.2]) / np.linalg.norm([1.0, 0.3, 0.2])
+    err = {False: [], True: []}
+    for R in (40.0, 80.0, 160.0):
+        pos = np.concatenate([u, (R * direction)[:, None]], axis=1)
+        d = oracle.direct(pos, mass, 1.0, 0.0, targets=np.array([k]))[:, 0]
+        for quad in (False, True):
+            t = oracle.Tree(pos, mass)
+            a, pp, pc = t.forces(1.0, 0.0, 0.7, targets=np.array([k]), quadrupole=quad)
+            t.close()
+            assert pc[0] >= 1   # the cluster is seen as cell(s)
+            err[quad].append(np.linalg.norm(a[:, 0] - d) / np.linalg.norm(d))
+    mono, quad = err[False], err[True]
+    for r in (mono[0] / mono[1], mono[1] / mono[2]):
+        assert 3.0 < r < 5.0, mono
+    for r in (quad[0] / quad[1], quad[1] / quad[2]):
+        assert 6.0 < r < 10.0, quad
+    assert all(q < m for q, m in zip(quad, mono))
+
+
+def test_quadrupole_walk_theta_zero_and_smaller_error():
+    pos, _, mass = ics.plummer(2500, 63)
+    a0, _, _ = oracle.bh(pos, mass, 1.0, 0.01, 0.0)
+    q0, _, _ = oracle.bh(pos, mass, 1.0, 0.01, 0.0, quadrupole=True)
+    assert np.array_equal(a0, q0)   # no cell is ever accepted
+    d = oracle.direct(pos, mass, 1.0, 0.01)
+    err = lambda x: np.sqrt(((x - d) ** 2).sum() / (d ** 2).sum())
+    for theta in (0.5, 0.7):
+        a, pp, pc = oracle.bh(pos, mass, 1.0, 0.01, theta)
+        q, qpp, qpc = oracle.bh(pos, mass, 1.0, 0.01, theta, quadrupole=True)
+        assert np.array_equal(pp, qpp) and np.array_equal(pc, qpc)   # same lists
+        assert err(q) < 0.5 * err(a)
