@@ -39,9 +39,10 @@ METRIC = "Barnes-Hut bodies/s per step at N=16M theta=0.5"
 FLOP_PER_INTERACTION = 20          # softened monopole pair term, counting rsqrt as 2 flops
 FP32_LANES_PER_SM = 128            # FP32 FMA lanes per SM (Blackwell)
 # Algorithmic bytes per body of the build phases (compulsory reads + writes):
-#   kick + drift + box partials: pos, vel, acc, mass read (80 B), pos, vel written (48 B);
-#   keys: pos read (24 B), key + id written (12 B)
-BYTES_KICK_KEYS = 80 + 48 + 24 + 12
+#   kick + drift + box partials: pos, vel, acc, mass read (80 B), pos, vel written (48 B), the
+#   (x, y, z, m) record for the permutation written (32 B); keys: pos read (24 B), key + id
+#   written (12 B)
+BYTES_KICK_KEYS = 80 + 48 + 32 + 24 + 12
 #   radix sort: digit histograms read the keys once (8 B); each of 8 passes reads the keys in the
 #   upsweep (8 B) and reads + writes keys and ids in the downsweep (24 B)
 BYTES_SORT = 8 + 8 * (8 + 24)

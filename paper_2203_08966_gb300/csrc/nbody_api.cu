@@ -75,8 +75,11 @@ struct nbody_ctx {
     // launch shape of the walk per precision class (FP32 forms, FP64), set by nbody_autotune
     int shape32 = kDefaultWalkShape, shape64 = kDefaultWalkShape;
 
-    // host-buffer stepping
+    // host-buffer stepping: device copies, and a side stream that reads the positions back while
+    // the last step's tree and walk run
     double *hpos = nullptr, *hvel = nullptr, *hmass = nullptr;
+    cudaStream_t xstream = nullptr;
+    cudaEvent_t xdrift = nullptr;
 
     // state
     int64_t n_built = -1;       // n of the last build (-1: none)
@@ -390,6 +393,35 @@ nbody_status forest_step_once(nbody_ctx *c, double *pos, double *vel, const doub
     return walk(c, n, c->acc, vel, h);
 }
 
+nbody_status begin_timing(nbody_ctx *c);
+nbody_status end_timing(nbody_ctx *c);
+
+// a^(k) at the current positions, unless kept from the previous call
+nbody_status ensure_acc(nbody_ctx *c, const double *pos, const double *mass, int64_t n)
+{
+    if (c->acc_n == n) return NBODY_OK;
+    CKS(build(c, pos, mass, (int)n, false));
+    CKS(walk(c, (int)n, c->acc, nullptr, 0.0));
+    c->acc_n = n;
+    return NBODY_OK;
+}
+
+// One kick-drift-kick step (§2.4); `drifted` (may be null) is recorded on the context stream once
+// the positions of this step are final (after the drift).
+nbody_status step_once(nbody_ctx *c, double *pos, double *vel, const double *mass, int64_t n,
+                       cudaEvent_t drifted)
+{
+    const double h = 0.5 * c->p.dt;
+    CKS(begin_timing(c));
+    launch_kick_drift_bbox(pos, vel, c->acc, mass, (int)n, h, c->p.dt, c->partials, c->nblk,
+                           c->aos, c->stream);
+    CKS(check_launch(c, "kick/drift"));
+    if (drifted) CK(cudaEventRecord(drifted, c->stream));
+    CKS(build(c, pos, mass, (int)n, true));
+    CKS(walk(c, (int)n, c->acc, vel, h));
+    return end_timing(c);
+}
+
 nbody_status begin_timing(nbody_ctx *c)
 {
     if (!c->timing) return NBODY_OK;
@@ -507,6 +539,8 @@ nbody_status nbody_destroy(nbody_ctx *c)
     dfree(c->hpos);
     dfree(c->hvel);
     dfree(c->hmass);
+    if (c->xdrift) cudaEventDestroy(c->xdrift);
+    if (c->xstream) cudaStreamDestroy(c->xstream);
     free_nodes(c);
     if (c->h_word) cudaFreeHost(c->h_word);
     for (int k = 0; k < 6; ++k)
@@ -562,21 +596,8 @@ nbody_status nbody_step(nbody_ctx *c, double *d_pos, double *d_vel, const double
     if (nsteps < 0) return fail(c, NBODY_EINVAL, "nsteps < 0");
     if (n > 0 && (!d_pos || !d_vel || !d_mass)) return fail(c, NBODY_EINVAL, "null pointer");
     if (n == 0 || nsteps == 0) return NBODY_OK;
-    const double h = 0.5 * c->p.dt;
-    if (c->acc_n != n) {
-        CKS(build(c, d_pos, d_mass, (int)n, false));
-        CKS(walk(c, (int)n, c->acc, nullptr, 0.0));
-        c->acc_n = n;
-    }
-    for (int32_t k = 0; k < nsteps; ++k) {
-        CKS(begin_timing(c));
-        launch_kick_drift_bbox(d_pos, d_vel, c->acc, d_mass, (int)n, h, c->p.dt, c->partials,
-                               c->nblk, c->aos, c->stream);
-        CKS(check_launch(c, "kick/drift"));
-        CKS(build(c, d_pos, d_mass, (int)n, true));
-        CKS(walk(c, (int)n, c->acc, d_vel, h));
-        CKS(end_timing(c));
-    }
+    CKS(ensure_acc(c, d_pos, d_mass, n));
+    for (int32_t k = 0; k < nsteps; ++k) CKS(step_once(c, d_pos, d_vel, d_mass, n, nullptr));
     return NBODY_OK;
 }
 
@@ -607,16 +628,25 @@ nbody_status nbody_step_host(nbody_ctx *c, double *h_pos, double *h_vel, double 
     } else {
         c->acc_n = -1;
     }
-    CKS(nbody_step(c, c->hpos, c->hvel, c->hmass, n, nsteps));
-    if (c->acc_n != n) {  // nsteps == 0 without h_acc: nothing was computed
-        CKS(build(c, c->hpos, c->hmass, (int)n, false));
-        CKS(walk(c, (int)n, c->acc, nullptr, 0.0));
-        c->acc_n = n;
+    CKS(ensure_acc(c, c->hpos, c->hmass, n));
+    if (nsteps > 0) {
+        if (!c->xstream) {
+            CK(cudaStreamCreateWithFlags(&c->xstream, cudaStreamNonBlocking));
+            CK(cudaEventCreateWithFlags(&c->xdrift, cudaEventDisableTiming));
+        }
+        for (int32_t k = 0; k + 1 < nsteps; ++k)
+            CKS(step_once(c, c->hpos, c->hvel, c->hmass, n, nullptr));
+        // the last step: its positions go back to the host while its tree and walk run
+        CKS(step_once(c, c->hpos, c->hvel, c->hmass, n, c->xdrift));
+        CK(cudaStreamWaitEvent(c->xstream, c->xdrift, 0));
+        CK(cudaMemcpyAsync(h_pos, c->hpos, b3, cudaMemcpyDeviceToHost, c->xstream));
+    } else {
+        CK(cudaMemcpyAsync(h_pos, c->hpos, b3, cudaMemcpyDeviceToHost, c->stream));
     }
-    CK(cudaMemcpyAsync(h_pos, c->hpos, b3, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaMemcpyAsync(h_vel, c->hvel, b3, cudaMemcpyDeviceToHost, c->stream));
     if (h_acc) CK(cudaMemcpyAsync(h_acc, c->acc, b3, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
+    if (c->xstream) CK(cudaStreamSynchronize(c->xstream));
     c->acc_n = -1;  // the device copy belongs to this call only
     return NBODY_OK;
 }
