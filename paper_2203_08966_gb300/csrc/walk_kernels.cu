@@ -90,29 +90,6 @@ __device__ __forceinline__ void cell64q(double xj, double yj, double zj, double 
     az = __dadd_rn(az, __dsub_rn(__dmul_rn(s, dz), __dmul_rn(u, qz)));
 }
 
-// FP32 cell term with the quadrupole (the same expansion): c = (x - c0, y - c0, z - c0, G M),
-// q0 = G (xx, yy, zz, xy), q1 = G (xz, yz, -, -); on = 0 drops the term.
-template <bool kGuard>
-__device__ __forceinline__ void cell32q(const float4 &c, const float4 &q0, const float4 &q1,
-                                        float xi, float yi, float zi, float eps2, float on,
-                                        float &ax, float &ay, float &az)
-{
-    const float dx = c.x - xi, dy = c.y - yi, dz = c.z - zi;
-    const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
-    float ri = rsqrtf(r2);
-    if (kGuard) ri = r2 > 0.f ? ri : 0.f;
-    ri *= on;
-    const float ri2 = ri * ri, ri3 = ri * ri2, ri5 = ri3 * ri2, ri7 = ri5 * ri2;
-    const float qx = fmaf(q0.x, dx, fmaf(q0.w, dy, q1.x * dz));
-    const float qy = fmaf(q0.w, dx, fmaf(q0.y, dy, q1.y * dz));
-    const float qz = fmaf(q1.x, dx, fmaf(q1.y, dy, q0.z * dz));
-    const float dqd = fmaf(dx, qx, fmaf(dy, qy, dz * qz));
-    const float s = fmaf(c.w, ri3, 2.5f * dqd * ri7);
-    ax = fmaf(s, dx, fmaf(-ri5, qx, ax));
-    ay = fmaf(s, dy, fmaf(-ri5, qy, ay));
-    az = fmaf(s, dz, fmaf(-ri5, qz, az));
-}
-
 // One step of Kahan's compensated summation (Kahan 1965): s + c tracks the exact running sum.
 __device__ __forceinline__ void kahan_add(float &s, float &c, float t)
 {
@@ -182,14 +159,71 @@ struct GroupSmem {
     uint2 pm[kPCap];              // (body mask, 1 for a leaf body / 0 for a cell) per entry
 };
 
-// With quadrupoles, accepted cells go to their own buffers (their term needs G Q): centre of
-// mass and mass, then G (xx, yy, zz, xy) and G (xz, yz, -, -); the partial ones with a mask.
+// With quadrupoles, accepted cells go to their own buffers (their term needs G Q), in pairs for
+// the packed kernel: cells 2k and 2k+1 occupy five float4, (x0, x1, y0, y1), (z0, z1, w0, w1),
+// (xx0, xx1, yy0, yy1), (zz0, zz1, xy0, xy1), (xz0, xz1, yz0, yz1) with w = G M and the
+// quadrupole components times G; the partial ones with a body mask each.
 constexpr int kQCap = 32;
 struct QuadSmem {
-    float4 fc[kQCap], fq0[kQCap], fq1[kQCap];
-    float4 pc[kQCap], pq0[kQCap], pq1[kQCap];
+    float4 f[5 * kQCap / 2];
+    float4 p[5 * kQCap / 2];
     uint32_t pm[kQCap];
 };
+
+__device__ __forceinline__ void put_quad_entry(float4 *buf, int e, const float4 &c,
+                                               const float4 &q0, const float4 &q1)
+{
+    float *q = reinterpret_cast<float *>(buf + 5 * (e >> 1)) + (e & 1);
+    q[0] = c.x;
+    q[2] = c.y;
+    q[4] = c.z;
+    q[6] = c.w;
+    q[8] = q0.x;    // xx
+    q[10] = q0.y;   // yy
+    q[12] = q0.z;   // zz
+    q[14] = q0.w;   // xy
+    q[16] = q1.x;   // xz
+    q[18] = q1.y;   // yz
+}
+
+// Two quadrupole cell terms at once with packed FP32 arithmetic (the expansion of cell32q);
+// on = (on0, on1) drops a term with 0.
+template <bool kGuard>
+__device__ __forceinline__ void cell32q_x2(const float4 *e, float2 nx, float2 ny, float2 nz,
+                                           float2 eps2, float2 on, float2 &ax, float2 &ay,
+                                           float2 &az)
+{
+    const float4 a = e[0], b = e[1], q0 = e[2], q1 = e[3], q2 = e[4];
+    const float2 dx = __fadd2_rn(make_float2(a.x, a.y), nx);
+    const float2 dy = __fadd2_rn(make_float2(a.z, a.w), ny);
+    const float2 dz = __fadd2_rn(make_float2(b.x, b.y), nz);
+    float2 r2 = __ffma2_rn(dz, dz, eps2);
+    r2 = __ffma2_rn(dy, dy, r2);
+    r2 = __ffma2_rn(dx, dx, r2);
+    float2 ri = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+    if (kGuard) {
+        ri.x = r2.x > 0.f ? ri.x : 0.f;
+        ri.y = r2.y > 0.f ? ri.y : 0.f;
+    }
+    ri = __fmul2_rn(ri, on);
+    const float2 ri2 = __fmul2_rn(ri, ri);
+    const float2 ri3 = __fmul2_rn(ri, ri2);
+    const float2 ri5 = __fmul2_rn(ri3, ri2);
+    const float2 ri7 = __fmul2_rn(ri5, ri2);
+    const float2 qxx = make_float2(q0.x, q0.y), qyy = make_float2(q0.z, q0.w);
+    const float2 qzz = make_float2(q1.x, q1.y), qxy = make_float2(q1.z, q1.w);
+    const float2 qxz = make_float2(q2.x, q2.y), qyz = make_float2(q2.z, q2.w);
+    const float2 qx = __ffma2_rn(qxx, dx, __ffma2_rn(qxy, dy, __fmul2_rn(qxz, dz)));
+    const float2 qy = __ffma2_rn(qxy, dx, __ffma2_rn(qyy, dy, __fmul2_rn(qyz, dz)));
+    const float2 qz = __ffma2_rn(qxz, dx, __ffma2_rn(qyz, dy, __fmul2_rn(qzz, dz)));
+    const float2 dqd = __ffma2_rn(dx, qx, __ffma2_rn(dy, qy, __fmul2_rn(dz, qz)));
+    const float2 s = __ffma2_rn(make_float2(b.z, b.w), ri3,
+                                __fmul2_rn(__fmul2_rn(make_float2(2.5f, 2.5f), dqd), ri7));
+    const float2 nri5 = __fmul2_rn(make_float2(-1.f, -1.f), ri5);
+    ax = __ffma2_rn(s, dx, __ffma2_rn(nri5, qx, ax));
+    ay = __ffma2_rn(s, dy, __ffma2_rn(nri5, qy, ay));
+    az = __ffma2_rn(s, dz, __ffma2_rn(nri5, qz, az));
+}
 template <bool kQuad>
 __host__ __device__ constexpr size_t group_smem_bytes()
 {
@@ -323,31 +357,30 @@ struct GroupEval {
             terms = 0;
         }
     }
-    // quadrupole cells: every live body of the group (full) or the masked ones (part)
-    __device__ __forceinline__ void full_quad(const QuadSmem &Q, int cnt, const float4 &me,
-                                              float eps2)
+    // quadrupole cells, two at a time (counts padded to even by the caller): every live body of
+    // the group (full) or the masked ones (part)
+    __device__ __forceinline__ void full_quad(const QuadSmem &Q, int cnt, const float2 *nme,
+                                              float2 eps2)
     {
-        float ax = 0.f, ay = 0.f, az = 0.f;
-        for (int e = 0; e < cnt; ++e)
-            cell32q<kGuard>(Q.fc[e], Q.fq0[e], Q.fq1[e], me.x, me.y, me.z, eps2, 1.f, ax, ay, az);
-        acc.x.x += ax;
-        acc.y.x += ay;
-        acc.z.x += az;
+        const int np = (cnt + 1) >> 1;
+#pragma unroll 2
+        for (int k = 0; k < np; ++k)
+            cell32q_x2<kGuard>(Q.f + 5 * k, nme[0], nme[1], nme[2], eps2, make_float2(1.f, 1.f),
+                               acc.x, acc.y, acc.z);
         settle(cnt);
     }
-    __device__ __forceinline__ void part_quad(const QuadSmem &Q, int cnt, const float4 &me,
-                                              float eps2, int lane)
+    __device__ __forceinline__ void part_quad(const QuadSmem &Q, int cnt, const float2 *nme,
+                                              float2 eps2, int lane)
     {
-        float ax = 0.f, ay = 0.f, az = 0.f;
-        for (int e = 0; e < cnt; ++e) {
-            const uint32_t on = (Q.pm[e] >> lane) & 1u;
-            cell32q<kGuard>(Q.pc[e], Q.pq0[e], Q.pq1[e], me.x, me.y, me.z, eps2, (float)on, ax,
-                            ay, az);
-            pc += on;
+        const int np = (cnt + 1) >> 1;
+        const uint2 *pm2 = reinterpret_cast<const uint2 *>(Q.pm);
+        for (int k = 0; k < np; ++k) {
+            const uint2 m = pm2[k];
+            const uint32_t on0 = (m.x >> lane) & 1u, on1 = (m.y >> lane) & 1u;
+            cell32q_x2<kGuard>(Q.p + 5 * k, nme[0], nme[1], nme[2], eps2,
+                               make_float2((float)on0, (float)on1), acc.x, acc.y, acc.z);
+            pc += on0 + on1;
         }
-        acc.x.x += ax;
-        acc.y.x += ay;
-        acc.z.x += az;
         settle(cnt);
     }
     // cnt entries, padded to an even count by the caller (a zero-weight entry)
@@ -430,23 +463,16 @@ __device__ __forceinline__ void walk_group(const WalkArgs &a, GroupSmem &S, Quad
     // appends one entry per lane whose kind says so: full-group entries to f, others to p;
     // with quadrupoles accepted cells go to their own buffers, with their G Q (node: level-order
     // index of the cell)
-    auto emit = [&](int kind, const float4 &c, unsigned m, int node) {
+    auto emit = [&](int kind, const float4 &c, unsigned m, const float4 &q0, const float4 &q1) {
         if (kQuad) {
             const bool qf = kind == kFullCell, qp = kind == kPartCell;
             const unsigned qfb = __ballot_sync(kFull, qf), qpb = __ballot_sync(kFull, qp);
             if (qf || qp) {
-                const float4 q0 = ldg4(a.gq + 2 * (size_t)node);
-                const float4 q1 = ldg4(a.gq + 2 * (size_t)node + 1);
                 if (qf) {
-                    const int o = qfn + __popc(qfb & lt);
-                    Q.fc[o] = c;
-                    Q.fq0[o] = q0;
-                    Q.fq1[o] = q1;
+                    put_quad_entry(Q.f, qfn + __popc(qfb & lt), c, q0, q1);
                 } else {
                     const int o = qpn + __popc(qpb & lt);
-                    Q.pc[o] = c;
-                    Q.pq0[o] = q0;
-                    Q.pq1[o] = q1;
+                    put_quad_entry(Q.p, o, c, q0, q1);
                     Q.pm[o] = m;
                 }
             }
@@ -474,18 +500,24 @@ __device__ __forceinline__ void walk_group(const WalkArgs &a, GroupSmem &S, Quad
     // evaluates and empties both buffers (an odd count is padded with a zero-weight source)
     auto drain = [&]() {
         if (lane == 0) {
-            if (fn & 1) put_entry(S.f, fn, make_float4(0.f, 0.f, 0.f, 0.f));
+            const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (fn & 1) put_entry(S.f, fn, z);
             if (pn & 1) {
-                put_entry(S.p, pn, make_float4(0.f, 0.f, 0.f, 0.f));
+                put_entry(S.p, pn, z);
                 S.pm[pn] = make_uint2(0u, 0u);
+            }
+            if (kQuad && (qfn & 1)) put_quad_entry(Q.f, qfn, z, z, z);
+            if (kQuad && (qpn & 1)) {
+                put_quad_entry(Q.p, qpn, z, z, z);
+                Q.pm[qpn] = 0u;
             }
         }
         __syncwarp();
         if (fn > 0) ev.full(S, fn, nme, eps2);
         if (pn > 0) ev.part(S, pn, nme, eps2, lane);
         if (kQuad) {
-            if (qfn > 0) ev.full_quad(Q, qfn, me, eps2s);
-            if (qpn > 0) ev.part_quad(Q, qpn, me, eps2s, lane);
+            if (qfn > 0) ev.full_quad(Q, qfn, nme, eps2);
+            if (qpn > 0) ev.part_quad(Q, qpn, nme, eps2, lane);
             qfn = qpn = 0;
         }
         fn = pn = 0;
@@ -549,9 +581,14 @@ __device__ __forceinline__ void walk_group(const WalkArgs &a, GroupSmem &S, Quad
         const unsigned m = has ? em : 0u;
         float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
         int4 meta = make_int4(0, 0, 0, 0);
+        float4 q0 = make_float4(0.f, 0.f, 0.f, 0.f), q1 = q0;
         if (has) {
             c = ldg4(&a.gn[node].c);
             meta = __ldg(reinterpret_cast<const int4 *>(&a.gn[node].child));
+        }
+        if (kQuad && has) {  // the quadrupole (every node has one), in case it is accepted
+            q0 = ldg4(a.gq + 2 * (size_t)node);
+            q1 = ldg4(a.gq + 2 * (size_t)node + 1);
         }
 
         // ---- while the loads are in flight: evaluate what the previous step buffered
@@ -631,7 +668,7 @@ __device__ __forceinline__ void walk_group(const WalkArgs &a, GroupSmem &S, Quad
         }
 
         // ---- buffer the entries, push the children
-        emit(kind, c, emask, node);
+        emit(kind, c, emask, q0, q1);
         {
             const bool isp = pmask != 0u;
             const unsigned ob = __ballot_sync(kFull, isp);
@@ -666,7 +703,7 @@ __device__ __forceinline__ void walk_group(const WalkArgs &a, GroupSmem &S, Quad
                     if (d < 32u) mb &= ~(1u << d);
                     kb = (!h || mb == 0u) ? kNone : (mb == live_mask ? kFullLeaf : kPartLeaf);
                 }
-                emit(kb, s, mb, 0);
+                emit(kb, s, mb, s, s);
             }
         }
     }
