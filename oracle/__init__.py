@@ -11,6 +11,9 @@ Array conventions match the library: positions and velocities are (3, N) float64
 Parity status of each function (what pins it is in ``tests/test_oracle_pins.py``):
     bbox / quantise / keys / interleave  pinned (paper's worked 2-D example, brute force)
     sort_pairs                           pinned (Python sorted())
+    resort_insertion (§4.4 re-sort from  pinned (equals sort_pairs from any starting order;
+      last step's order)                 exchanges = brute-force inversion count; none when
+                                         the starting order is already sorted)
     tree build / records                 pinned (independent prefix-grouping construction,
                                          paper's octal key examples, invariants)
     moments                              pinned (root centre of mass = global centre of mass;
@@ -78,6 +81,7 @@ def _load():
         "orc_interleave": (ctypes.c_uint64, [_u32p, ctypes.c_int, ctypes.c_int]),
         "orc_keys": (None, [_f64p, i64, _f64p, _u64p]),
         "orc_sort_pairs": (None, [_u64p, i64, _u64p, _i64p]),
+        "orc_resort_insertion": (i64, [_u64p, _i64p, i64, _u64p, _i64p]),
         "orc_direct": (None, [_f64p, _f64p, i64, vp, i64, d, d, _f64p]),
         "orc_tree_build": (vp, [_f64p, _f64p, i64]),
         "orc_tree_free": (None, [vp]),
@@ -160,6 +164,19 @@ def sort_pairs(k):
     ids = np.zeros(k.shape[0], dtype=np.int64)
     _load().orc_sort_pairs(k, k.shape[0], ko, ids)
     return ko, ids
+
+
+def resort_insertion(k, prev):
+    """Insertion sort (§4.4) of the bodies taken in the order ``prev`` (last step's sorted ids)
+    by (key, id): sorted keys, sorted ids and the number of neighbour exchanges it made."""
+    k = np.ascontiguousarray(k, dtype=np.uint64)
+    prev = np.ascontiguousarray(prev, dtype=np.int64)
+    if prev.shape != k.shape:
+        raise ValueError("prev must be a permutation of the key indices")
+    ko = np.zeros_like(k)
+    ids = np.zeros(k.shape[0], dtype=np.int64)
+    swaps = int(_load().orc_resort_insertion(k, prev, k.shape[0], ko, ids))
+    return ko, ids, swaps
 
 
 def direct(pos, mass, G=1.0, eps=0.0, targets=None):

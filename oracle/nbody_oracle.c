@@ -133,6 +133,39 @@ void orc_sort_pairs(const uint64_t *keys, int64_t n, uint64_t *keys_out, int64_t
 }
 
 /* ------------------------------------------------------------------ */
+/* Re-sort from the previous order (§4.4, end: bodies move little in  */
+/* one step, so last step's sorted list is almost sorted and an       */
+/* insertion sort finishes it with few exchanges).                    */
+/* ------------------------------------------------------------------ */
+
+/* Insertion sort of the bodies taken in the order prev[0..n-1] (a permutation of 0..n-1, e.g. last
+ * step's sorted ids) by (keys[id], id) ascending: each element sinks left past every element that
+ * must follow it, one exchange of neighbours at a time.  Writes the sorted ids and keys; returns
+ * the number of exchanges, which equals the number of inverted pairs of the starting order. */
+int64_t orc_resort_insertion(const uint64_t *keys, const int64_t *prev, int64_t n,
+                             uint64_t *keys_out, int64_t *ids_out)
+{
+    int64_t swaps = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        ids_out[i] = prev[i];
+        keys_out[i] = keys[prev[i]];
+    }
+    for (int64_t i = 1; i < n; ++i) {
+        for (int64_t j = i; j > 0; --j) {
+            const uint64_t ka = keys_out[j - 1], kb = keys_out[j];
+            const int64_t ia = ids_out[j - 1], ib = ids_out[j];
+            if (ka < kb || (ka == kb && ia < ib)) break;
+            keys_out[j - 1] = kb;
+            keys_out[j] = ka;
+            ids_out[j - 1] = ib;
+            ids_out[j] = ia;
+            ++swaps;
+        }
+    }
+    return swaps;
+}
+
+/* ------------------------------------------------------------------ */
 /* Softened pair kernel (eq. `motion` + softening; eq. `approxforce`). */
 /* ------------------------------------------------------------------ */
 

@@ -85,6 +85,53 @@ def test_sort_pairs_matches_python_sort():
     assert list(ids) == [b for _, b in ref]
 
 
+# ---------------------------------------------------------------- re-sort from last step's order (§4.4)
+
+def _inversions(k, order):
+    """Brute force: pairs (a, b), a before b in `order`, that the (key, id) order puts the other
+    way round."""
+    c = [(int(k[i]), int(i)) for i in order]
+    return sum(1 for a in range(len(c)) for b in range(a + 1, len(c)) if c[a] > c[b])
+
+
+@pytest.mark.parametrize("start", ["random", "sorted", "reversed", "near"])
+def test_resort_insertion_equals_sort_and_counts_inversions(start):
+    rng = np.random.default_rng(11)
+    n = 400
+    k = rng.integers(0, 50, n).astype(np.uint64)       # many equal keys: ties go by id
+    ks, ids = oracle.sort_pairs(k)
+    if start == "random":
+        prev = rng.permutation(n)
+    elif start == "sorted":
+        prev = ids.copy()
+    elif start == "reversed":
+        prev = ids[::-1].copy()
+    else:  # last step's order after a few bodies moved
+        prev = ids.copy()
+        for a in rng.integers(0, n - 3, 12):
+            prev[a], prev[a + 2] = prev[a + 2], prev[a]
+    ko, io, swaps = oracle.resort_insertion(k, prev)
+    assert np.array_equal(ko, ks) and np.array_equal(io, ids)
+    assert swaps == _inversions(k, prev)
+    if start == "sorted":
+        assert swaps == 0
+    if start == "reversed":
+        assert swaps == n * (n - 1) // 2
+
+
+def test_resort_insertion_after_a_drift_is_cheap():
+    """After one small drift of a Plummer sphere last step's order is almost sorted: few
+    exchanges (the premise of §4.4), and the result is the sort of the new keys."""
+    pos, vel, _ = ics.plummer(20000, 9)
+    _, prev = oracle.sort_pairs(oracle.keys(pos))
+    pos2 = pos + 5e-4 * vel
+    k2 = oracle.keys(pos2)
+    ko, io, swaps = oracle.resort_insertion(k2, prev)
+    ks, ids = oracle.sort_pairs(k2)
+    assert np.array_equal(ko, ks) and np.array_equal(io, ids)
+    assert 0 < swaps < 20 * 20000     # a random order would need about n^2 / 4 = 1e8
+
+
 # ---------------------------------------------------------------- tree (Algorithm 2, §4.2, §4.7)
 
 def _tree_by_prefix(sorted_keys):
