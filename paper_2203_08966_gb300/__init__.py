@@ -25,6 +25,8 @@ FLAG_GROUP_MAC = 1  # NBODY_FLAG_GROUP_MAC: grouped acceptance test (Barnes 1990
 FLAG_CELL_GROUPS = 2  # NBODY_FLAG_CELL_GROUPS: FP32 walk groups follow the tree's cells
 FLAG_QUADRUPOLE = 4  # NBODY_FLAG_QUADRUPOLE: accepted cells add their quadrupole term
 PRECISIONS = {"fp64": FP64, "fp32": FP32, "fp32_kahan": FP32_KAHAN}
+# NBODY_SORT_*: how a build sorts (same order in every mode; re-sort from the previous order, §4.4)
+SORT_AUTO, SORT_FULL, SORT_RESORT = 0, 1, 2
 
 STATUS = {0: "NBODY_OK", 1: "NBODY_EINVAL", 2: "NBODY_ENOMEM", 3: "NBODY_ECUDA",
           4: "NBODY_ESTACK", 5: "NBODY_ETIMEOUT", 6: "NBODY_ESTATE"}
@@ -36,7 +38,8 @@ EXPORTS = ("nbody_create", "nbody_destroy", "nbody_set_params", "nbody_build_tre
            "nbody_get_counters", "nbody_enable_timing", "nbody_get_timings",
            "nbody_last_error", "nbody_get_launch_count", "nbody_sort_keys_noalloc",
            "nbody_forest_create", "nbody_forest_forces", "nbody_forest_step",
-           "nbody_autotune", "nbody_set_walk_shape", "nbody_get_walk_shape")
+           "nbody_autotune", "nbody_set_walk_shape", "nbody_get_walk_shape",
+           "nbody_set_sort_mode", "nbody_get_sort_stats")
 
 
 class NBodyError(RuntimeError):
@@ -99,6 +102,8 @@ def load_library(path: str = LIB_PATH):
         "nbody_autotune": [vp, vp, vp, i64, vp, vp],
         "nbody_get_walk_shape": [vp, vp, vp],
         "nbody_set_walk_shape": [vp, i32],
+        "nbody_set_sort_mode": [vp, i32],
+        "nbody_get_sort_stats": [vp, vp, vp],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -303,6 +308,18 @@ class Context:
         self._check(self._lib.nbody_get_walk_shape(self._h, ctypes.byref(k), ctypes.byref(t)),
                     "nbody_get_walk_shape")
         return int(k.value), int(t.value)
+
+    def set_sort_mode(self, mode):
+        """SORT_AUTO, SORT_FULL or SORT_RESORT (the order is the same in every mode)."""
+        self._check(self._lib.nbody_set_sort_mode(self._h, int(mode)), "nbody_set_sort_mode")
+
+    def sort_stats(self):
+        """(path, removed) of the last build: path 1 = re-sorted from the previous order,
+        0 = full sort, -1 = no build yet; removed = bodies the re-sort took out (-1: not tried)."""
+        path, removed = ctypes.c_int32(), ctypes.c_int64()
+        self._check(self._lib.nbody_get_sort_stats(self._h, ctypes.byref(path),
+                                                   ctypes.byref(removed)), "nbody_get_sort_stats")
+        return int(path.value), int(removed.value)
 
     def sync(self):
         self._check(self._lib.nbody_sync(self._h), "nbody_sync")

@@ -208,30 +208,8 @@ __global__ void __launch_bounds__(kBoxThreads) system_box_kernel(
 }
 
 // ------------------------------------------------------------------------------------------
-// Morton keys (§4.4): q = clamp(floor((x - o) * s), 0, 2^21 - 1) per axis, then the bits of
-// q_x, q_y, q_z interleaved with x most significant (a 63-bit key in one 64-bit word).
+// Morton keys (§4.4) of the bodies in the caller's order (morton_key), with ids = 0 .. n-1.
 // ------------------------------------------------------------------------------------------
-
-__device__ __forceinline__ uint32_t quantise(double x, double o, double s)
-{
-    double t = __dmul_rn(__dsub_rn(x, o), s);
-    if (!(t > 0.0)) return 0u;
-    double f = floor(t);
-    if (f >= (double)kQMax) return kQMax;
-    return (uint32_t)f;
-}
-
-// Spreads the low 21 bits of v so that bit b lands on bit 3b.
-__device__ __forceinline__ uint64_t spread3(uint64_t v)
-{
-    v &= 0x1fffffull;
-    v = (v | (v << 32)) & 0x001f00000000ffffull;
-    v = (v | (v << 16)) & 0x001f0000ff0000ffull;
-    v = (v | (v << 8)) & 0x100f00f00f00f00full;
-    v = (v | (v << 4)) & 0x10c30c30c30c30c3ull;
-    v = (v | (v << 2)) & 0x1249249249249249ull;
-    return v;
-}
 
 __device__ __forceinline__ int system_of(const Systems &ss, int i)
 {
@@ -243,11 +221,7 @@ __global__ void keys_kernel(const double *__restrict__ pos, int n, const Box *__
 {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const Box *b = box + system_of(ss, i);
-        const double s = b->s;
-        uint32_t qx = quantise(pos[i], b->o[0], s);
-        uint32_t qy = quantise(pos[(size_t)n + i], b->o[1], s);
-        uint32_t qz = quantise(pos[2 * (size_t)n + i], b->o[2], s);
-        keys[i] = (spread3(qx) << 2) | (spread3(qy) << 1) | spread3(qz);
+        keys[i] = morton_key(pos[i], pos[(size_t)n + i], pos[2 * (size_t)n + i], *b);
         ids[i] = (uint32_t)i;
     }
 }
@@ -265,6 +239,7 @@ constexpr int kSortItems = 16;                         // per thread
 constexpr int kSortTile = kSortThreads * kSortItems;   // 4096 keys per tile
 constexpr int kPasses = 8;       // key passes
 constexpr int kSysPasses = 2;    // forest: system passes (systems < 2^16)
+constexpr int kIdPasses = 4;     // at most: passes on the id bytes before the key passes
 constexpr size_t kDownSmem = (size_t)kSortTile * 8 + (size_t)kSortTile * 4 +
                              (size_t)kSortWarps * 256 * 4 + 256 * 4 + 256 * 4;
 
@@ -275,11 +250,15 @@ __device__ __forceinline__ unsigned lanemask_lt()
     return m;
 }
 
+// Digit totals of every pass: the 8 key bytes, then (id_passes > 0) the low id bytes.
 __global__ void __launch_bounds__(kSortThreads) radix_hist_kernel(const uint64_t *__restrict__ keys,
-                                                                 int n, uint32_t *hist)
+                                                                 const uint32_t *__restrict__ ids,
+                                                                 int n, int id_passes,
+                                                                 uint32_t *hist)
 {
-    __shared__ uint32_t sh[kPasses][256];
-    for (int k = threadIdx.x; k < kPasses * 256; k += blockDim.x) (&sh[0][0])[k] = 0;
+    __shared__ uint32_t sh[kPasses + kIdPasses][256];
+    const int rows = kPasses + id_passes;
+    for (int k = threadIdx.x; k < rows * 256; k += blockDim.x) (&sh[0][0])[k] = 0;
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const int stride = gridDim.x * blockDim.x;
@@ -293,25 +272,36 @@ __global__ void __launch_bounds__(kSortThreads) radix_hist_kernel(const uint64_t
             const unsigned peers = __match_any_sync(kFull, d);
             if (ok && (__ffs(peers) - 1) == lane) atomicAdd(&sh[p][d], __popc(peers));
         }
+        if (id_passes > 0) {
+            const uint32_t id = ok ? ids[i] : 0u;
+            for (int p = 0; p < id_passes; ++p) {
+                const unsigned d = ok ? (id >> (8 * p)) & 255u : 256u;
+                const unsigned peers = __match_any_sync(kFull, d);
+                if (ok && (__ffs(peers) - 1) == lane)
+                    atomicAdd(&sh[kPasses + p][d], __popc(peers));
+            }
+        }
     }
     __syncthreads();
-    for (int k = threadIdx.x; k < kPasses * 256; k += blockDim.x) {
+    for (int k = threadIdx.x; k < rows * 256; k += blockDim.x) {
         uint32_t v = (&sh[0][0])[k];
         if (v) atomicAdd(&hist[k], v);
     }
 }
 
-// Digit of an element: a byte of its key, or (forest system passes) a byte of the system of its
-// id.
-template <bool kSys>
+// Digit of an element: a byte of its key, a byte of the system of its id (forest passes) or a
+// byte of its id (passes that order equal keys by id when the ids are not ascending).
+enum : int { kDigitKey = 0, kDigitSys = 1, kDigitId = 2 };
+template <int kMode>
 __device__ __forceinline__ unsigned sort_digit(uint64_t key, uint32_t id, int shift,
                                                const uint16_t *sys)
 {
-    if (kSys) return ((unsigned)sys[id] >> shift) & 255u;
+    if (kMode == kDigitSys) return ((unsigned)sys[id] >> shift) & 255u;
+    if (kMode == kDigitId) return (id >> shift) & 255u;
     return (unsigned)((key >> shift) & 255u);
 }
 
-template <bool kSys>
+template <int kMode>
 __global__ void __launch_bounds__(kSortThreads) radix_upsweep_kernel(const uint64_t *__restrict__ keys,
                                                                     const uint32_t *__restrict__ ids,
                                                                     int n, int shift,
@@ -327,8 +317,10 @@ __global__ void __launch_bounds__(kSortThreads) radix_upsweep_kernel(const uint6
     for (int r = 0; r < kSortItems; ++r) {
         const int i = tile0 + r * 32 + lane;
         const bool ok = i < n;
-        const unsigned d = ok ? sort_digit<kSys>(kSys ? 0ull : keys[i], kSys ? ids[i] : 0u, shift, sys)
-                              : 256u;
+        const unsigned d =
+            ok ? sort_digit<kMode>(kMode == kDigitKey ? keys[i] : 0ull,
+                                   kMode != kDigitKey ? ids[i] : 0u, shift, sys)
+               : 256u;
         const unsigned peers = __match_any_sync(kFull, d);
         if (ok && (__ffs(peers) - 1) == lane) atomicAdd(&sh[d], __popc(peers));
     }
@@ -387,7 +379,7 @@ __global__ void __launch_bounds__(kSortThreads) radix_rowscan_kernel(uint32_t *c
     }
 }
 
-template <bool kSys>
+template <int kMode>
 __global__ void __launch_bounds__(kSortThreads) radix_downsweep_kernel(
     const uint64_t *__restrict__ keys_in, const uint32_t *__restrict__ ids_in,
     uint64_t *__restrict__ keys_out, uint32_t *__restrict__ ids_out, int n, int shift,
@@ -418,7 +410,7 @@ __global__ void __launch_bounds__(kSortThreads) radix_downsweep_kernel(
         const bool ok = i < n;
         k[r] = ok ? keys_in[i] : 0ull;
         id[r] = ok ? ids_in[i] : 0u;
-        const unsigned d = ok ? sort_digit<kSys>(k[r], id[r], shift, sys) : 256u;
+        const unsigned d = ok ? sort_digit<kMode>(k[r], id[r], shift, sys) : 256u;
         const unsigned peers = __match_any_sync(kFull, d);
         const uint32_t before = ok ? hist[d] : 0u;
         __syncwarp();
@@ -446,7 +438,7 @@ __global__ void __launch_bounds__(kSortThreads) radix_downsweep_kernel(
     for (int r = 0; r < kSortItems; ++r) {
         const int i = w0 + r * 32 + lane;
         if (i < n) {
-            const unsigned d = sort_digit<kSys>(k[r], id[r], shift, sys);
+            const unsigned d = sort_digit<kMode>(k[r], id[r], shift, sys);
             const uint32_t p = s_start[d] + s_warp[wid * 256 + d] + rank[r];
             s_keys[p] = k[r];
             s_ids[p] = id[r];
@@ -455,7 +447,7 @@ __global__ void __launch_bounds__(kSortThreads) radix_downsweep_kernel(
     __syncthreads();
     for (int i = threadIdx.x; i < tile_n; i += blockDim.x) {
         const uint64_t kk = s_keys[i];
-        const unsigned d = sort_digit<kSys>(kk, s_ids[i], shift, sys);
+        const unsigned d = sort_digit<kMode>(kk, s_ids[i], shift, sys);
         const int o = s_gofs[d] + i;
         keys_out[o] = kk;
         ids_out[o] = s_ids[i];
@@ -1092,45 +1084,94 @@ int sort_tiles(int n) { return (n + kSortTile - 1) / kSortTile; }
 
 cudaError_t sort_prepare()
 {
-    cudaError_t e = cudaFuncSetAttribute(radix_downsweep_kernel<false>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)kDownSmem);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(radix_downsweep_kernel<true>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDownSmem);
+    const void *fns[3] = {(const void *)radix_downsweep_kernel<kDigitKey>,
+                          (const void *)radix_downsweep_kernel<kDigitSys>,
+                          (const void *)radix_downsweep_kernel<kDigitId>};
+    for (const void *f : fns) {
+        const cudaError_t e =
+            cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDownSmem);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
-void launch_radix_sort(uint64_t *keys, uint32_t *ids, int n, const SortScratch &sc, cudaStream_t s)
+namespace {
+
+// The digit passes of one sort: `id_passes` passes on id bytes, the 8 key passes, then (forest)
+// the system passes; the result ends in (keys, ids) or (keys_alt, ids_alt) by the parity of the
+// pass count.
+void radix_passes(uint64_t *keys, uint32_t *ids, int n, int id_passes, const SortScratch &sc,
+                  cudaStream_t s, uint64_t **out_keys, uint32_t **out_ids)
 {
-    if (n <= 1) return;
     const int tiles = sort_tiles(n);
-    cudaMemsetAsync(sc.hist, 0, sizeof(uint32_t) * kPasses * 256, s);
-    radix_hist_kernel<<<grid_for(n, kSortThreads * 8, 152 * 4), kSortThreads, 0, s>>>(keys, n, sc.hist);
+    cudaMemsetAsync(sc.hist, 0, sizeof(uint32_t) * (kPasses + id_passes) * 256, s);
+    radix_hist_kernel<<<grid_for(n, kSortThreads * 8, 152 * 4), kSortThreads, 0, s>>>(
+        keys, ids, n, id_passes, sc.hist);
     uint64_t *kin = keys, *kout = sc.keys_alt;
     uint32_t *iin = ids, *iout = sc.ids_alt;
-    const int passes = kPasses + (sc.sys ? kSysPasses : 0);
+    const int sys_passes = sc.sys ? kSysPasses : 0;
+    const int passes = id_passes + kPasses + sys_passes;
     for (int p = 0; p < passes; ++p) {
-        const bool sys_pass = p >= kPasses;
-        const int shift = sys_pass ? 8 * (p - kPasses) : 8 * p;
-        const uint32_t *hist = sys_pass ? sc.sys_hist + 256 * (p - kPasses) : sc.hist + 256 * p;
-        if (sys_pass)
-            radix_upsweep_kernel<true><<<tiles, kSortThreads, 0, s>>>(kin, iin, n, shift, sc.counts,
-                                                                     tiles, sc.sys);
+        const int mode = p < id_passes ? kDigitId : (p < id_passes + kPasses ? kDigitKey : kDigitSys);
+        int shift;
+        const uint32_t *hist;
+        if (mode == kDigitId) {
+            shift = 8 * p;
+            hist = sc.hist + 256 * (kPasses + p);
+        } else if (mode == kDigitKey) {
+            shift = 8 * (p - id_passes);
+            hist = sc.hist + 256 * (p - id_passes);
+        } else {
+            shift = 8 * (p - id_passes - kPasses);
+            hist = sc.sys_hist + 256 * (p - id_passes - kPasses);
+        }
+        if (mode == kDigitId)
+            radix_upsweep_kernel<kDigitId><<<tiles, kSortThreads, 0, s>>>(kin, iin, n, shift,
+                                                                         sc.counts, tiles, nullptr);
+        else if (mode == kDigitKey)
+            radix_upsweep_kernel<kDigitKey><<<tiles, kSortThreads, 0, s>>>(kin, iin, n, shift,
+                                                                          sc.counts, tiles, nullptr);
         else
-            radix_upsweep_kernel<false><<<tiles, kSortThreads, 0, s>>>(kin, iin, n, shift,
-                                                                      sc.counts, tiles, nullptr);
+            radix_upsweep_kernel<kDigitSys><<<tiles, kSortThreads, 0, s>>>(kin, iin, n, shift,
+                                                                          sc.counts, tiles, sc.sys);
         radix_rowscan_kernel<<<256, kSortThreads, 0, s>>>(sc.counts, tiles, hist);
-        if (sys_pass)
-            radix_downsweep_kernel<true><<<tiles, kSortThreads, kDownSmem, s>>>(
-                kin, iin, kout, iout, n, shift, sc.counts, tiles, sc.sys);
-        else
-            radix_downsweep_kernel<false><<<tiles, kSortThreads, kDownSmem, s>>>(
+        if (mode == kDigitId)
+            radix_downsweep_kernel<kDigitId><<<tiles, kSortThreads, kDownSmem, s>>>(
                 kin, iin, kout, iout, n, shift, sc.counts, tiles, nullptr);
+        else if (mode == kDigitKey)
+            radix_downsweep_kernel<kDigitKey><<<tiles, kSortThreads, kDownSmem, s>>>(
+                kin, iin, kout, iout, n, shift, sc.counts, tiles, nullptr);
+        else
+            radix_downsweep_kernel<kDigitSys><<<tiles, kSortThreads, kDownSmem, s>>>(
+                kin, iin, kout, iout, n, shift, sc.counts, tiles, sc.sys);
         uint64_t *tk = kin; kin = kout; kout = tk;
         uint32_t *ti = iin; iin = iout; iout = ti;
     }
     count_launches(1 + 3 * passes);
+    *out_keys = kin;
+    *out_ids = iin;
+}
+
+}  // namespace
+
+void launch_radix_sort(uint64_t *keys, uint32_t *ids, int n, const SortScratch &sc, cudaStream_t s)
+{
+    if (n <= 1) return;
+    uint64_t *k;
+    uint32_t *i;
     // an even number of passes (8, or 8 + 2) leaves the result in the caller's buffers
+    radix_passes(keys, ids, n, 0, sc, s, &k, &i);
+}
+
+void launch_radix_sort_key_id(uint64_t *keys, uint32_t *ids, int n, int id_bits,
+                              const SortScratch &sc, cudaStream_t s, uint64_t **out_keys,
+                              uint32_t **out_ids)
+{
+    *out_keys = keys;
+    *out_ids = ids;
+    if (n <= 1) return;
+    const int id_passes = std::min(kIdPasses, std::max(1, (id_bits + 7) / 8));
+    radix_passes(keys, ids, n, id_passes, sc, s, out_keys, out_ids);
 }
 
 void launch_permute(const D4 *aos, const uint32_t *ids, int n, const Box *box, const Systems &ss,

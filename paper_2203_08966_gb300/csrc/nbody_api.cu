@@ -27,7 +27,7 @@ struct nbody_ctx {
     D4 *aos = nullptr;              // (x, y, z, m) records in the caller's order
     float4 *sbody32 = nullptr;
     uint32_t *node_off = nullptr;   // cap + 1
-    uint32_t *hist = nullptr;       // 8 x 256
+    uint32_t *hist = nullptr;       // 12 x 256
     uint32_t *counts = nullptr;     // 256 x sort tiles
     uint32_t *block_sums = nullptr; // scan tiles + 1
     double *partials = nullptr;     // bbox_partial_doubles() x bbox blocks
@@ -37,7 +37,8 @@ struct nbody_ctx {
     double *acc = nullptr;          // 3 x cap: a^(k) kept between steps
     uint32_t *pp = nullptr, *pc = nullptr;
     int *err = nullptr;             // device error word
-    uint32_t *h_word = nullptr;     // pinned host words: node count, deepest level
+    uint32_t *h_word = nullptr;     // pinned host words: node count, deepest level, then the
+                                    // re-sort's stats (kOrderStats words from h_word + 2)
     unsigned *info = nullptr;       // device word: deepest node level of the last build
 
     // octree
@@ -71,6 +72,14 @@ struct nbody_ctx {
     const void *gkey[3] = {nullptr, nullptr, nullptr};
     int64_t glaunches = 0;          // kernels per replayed step
     cudaEvent_t gev[2] = {};
+
+    // re-sort from the previous order (allocated on first use, capacity ord_cap bodies)
+    OrderScratch ord{};
+    int64_t ord_cap = 0;
+    int sort_mode = NBODY_SORT_AUTO;
+    int64_t order_n = -1;       // c->ids holds the sorted order of the last build of this n
+    int last_sort_path = -1;    // 1 re-sort, 0 full sort, -1 no build yet
+    int64_t last_removed = -1;
 
     // launch shape of the walk per precision class (FP32 forms, FP64), set by nbody_autotune
     int shape32 = kDefaultWalkShape, shape64 = kDefaultWalkShape;
@@ -120,6 +129,8 @@ nbody_status fail(nbody_ctx *c, nbody_status st, const char *fmt, ...)
     } while (0)
 
 // FP32 walks over groups that follow the tree's cells (the grouped acceptance test needs them).
+constexpr int kResortMinN = 1 << 16;  // NBODY_SORT_AUTO re-sorts from this many bodies
+
 bool cell_groups(const nbody_ctx *c)
 {
     return (c->p.flags & (NBODY_FLAG_GROUP_MAC | NBODY_FLAG_CELL_GROUPS)) != 0;
@@ -220,6 +231,42 @@ nbody_status ensure_nodes(nbody_ctx *c, int64_t need)
     return NBODY_OK;
 }
 
+void free_order(nbody_ctx *c)
+{
+    dfree(c->ord.keep);
+    dfree(c->ord.ends);
+    dfree(c->ord.seams);
+    dfree(c->ord.kept_off);
+    dfree(c->ord.stats);
+    dfree(c->ord.split);
+    dfree(c->ord.rk);
+    dfree(c->ord.xk);
+    dfree(c->ord.ri);
+    dfree(c->ord.xi);
+    c->ord_cap = 0;
+}
+
+// Scratch of the re-sort for the context's capacity (first use only).
+nbody_status ensure_order(nbody_ctx *c)
+{
+    if (c->ord_cap >= c->cap && c->ord.keep) return NBODY_OK;
+    free_order(c);
+    const size_t cap = (size_t)std::max<int64_t>(c->cap, 1);
+    const int tiles = order_tiles((int)cap);
+    CK(dalloc(&c->ord.keep, (size_t)tiles * 64));
+    CK(dalloc(&c->ord.ends, (size_t)tiles));
+    CK(dalloc(&c->ord.seams, (size_t)(tiles + 31) / 32));
+    CK(dalloc(&c->ord.kept_off, (size_t)tiles));
+    CK(dalloc(&c->ord.stats, (size_t)kOrderStats));
+    CK(dalloc(&c->ord.split, (size_t)order_merge_tiles((int)cap) + 1));
+    CK(dalloc(&c->ord.rk, cap));
+    CK(dalloc(&c->ord.xk, cap));
+    CK(dalloc(&c->ord.ri, cap));
+    CK(dalloc(&c->ord.xi, cap));
+    c->ord_cap = (int64_t)cap;
+    return NBODY_OK;
+}
+
 nbody_status check_launch(nbody_ctx *c, const char *what)
 {
     cudaError_t e = cudaGetLastError();
@@ -254,11 +301,38 @@ nbody_status build(nbody_ctx *c, const double *pos, const double *mass, int n,
     const Systems one{nullptr, nullptr, 1};
     if (!have_partials) launch_bbox_partials(pos, mass, n, c->partials, c->nblk, c->aos, s);
     launch_bbox_finalize(c->partials, c->nblk, c->box, c->tab, c->p.theta, s);
-    launch_keys(pos, n, c->box, one, c->keys, c->ids, s);
-    record(c, 1);
     SortScratch sc{c->keys_alt, c->ids_alt, c->hist, c->counts, sort_tiles((int)c->cap), nullptr,
                    nullptr};
-    launch_radix_sort(c->keys, c->ids, n, sc, s);
+    // re-sort from the last build's order (§4.4) when it is of the same n
+    bool resort = c->order_n == n && c->sort_mode != NBODY_SORT_FULL &&
+                  (c->sort_mode == NBODY_SORT_RESORT || n >= kResortMinN);
+    c->order_n = -1;
+    c->last_removed = -1;
+    if (resort) {
+        CKS(ensure_order(c));
+        launch_order_extract(c->aos, c->ids, n, c->box, c->keys, c->ord, s);
+        record(c, 1);
+        CKS(check_launch(c, "re-sort"));
+        CK(cudaMemcpyAsync(c->h_word + 2, c->ord.stats, sizeof(uint32_t) * kOrderStats,
+                           cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        const int64_t kept = (int64_t)c->h_word[2 + kOrderKept];
+        const bool gave_up = c->h_word[2 + kOrderGaveUp] != 0u;
+        if (kept < 0 || kept > n)
+            return fail(c, NBODY_ECUDA, "re-sort kept %lld of %d bodies", (long long)kept, n);
+        c->last_removed = n - kept;
+        if (gave_up || (c->sort_mode == NBODY_SORT_AUTO && 4 * (n - kept) > (int64_t)n))
+            resort = false;
+        else
+            launch_order_merge(c->keys, c->ids, n, (int)kept, c->ord, sc, s);
+    }
+    if (!resort) {
+        launch_keys(pos, n, c->box, one, c->keys, c->ids, s);
+        record(c, 1);
+        launch_radix_sort(c->keys, c->ids, n, sc, s);
+    }
+    c->last_sort_path = resort ? 1 : 0;
+    c->order_n = n;
     record(c, 2);
     launch_permute(c->aos, c->ids, n, c->box, one, c->p.G, c->sbody64, c->sbody32, s);
     CK(cudaMemsetAsync(c->info, 0, sizeof(unsigned), s));
@@ -470,7 +544,7 @@ nbody_status nbody_create(nbody_ctx **out, int64_t n_capacity, const nbody_param
         CK(dalloc(&c->aos, cap));
         CK(dalloc(&c->sbody32, cap));
         CK(dalloc(&c->node_off, cap + 1));
-        CK(dalloc(&c->hist, 8 * 256));
+        CK(dalloc(&c->hist, 12 * 256));
         CK(dalloc(&c->counts, (size_t)256 * sort_tiles((int)cap)));
         CK(dalloc(&c->block_sums, (size_t)scan_tiles((int)cap + 1) + 1));
         c->nblk = bbox_blocks((int64_t)cap);
@@ -485,7 +559,7 @@ nbody_status nbody_create(nbody_ctx **out, int64_t n_capacity, const nbody_param
         CK(dalloc(&c->cgroups_n, 1));
         CK(dalloc(&c->work, 1));
         CK(cudaMemset(c->err, 0, sizeof(int)));
-        CK(cudaMallocHost((void **)&c->h_word, 2 * sizeof(uint32_t)));
+        CK(cudaMallocHost((void **)&c->h_word, (2 + kOrderStats) * sizeof(uint32_t)));
         CK(dalloc(&c->info, 1));
         for (int k = 0; k < 6; ++k) CK(cudaEventCreate(&c->ev[k]));
         return NBODY_OK;
@@ -532,6 +606,7 @@ nbody_status nbody_destroy(nbody_ctx *c)
     dfree(c->groups);
     dfree(c->roots);
     dfree(c->nn);
+    free_order(c);
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     if (c->gstream) cudaStreamDestroy(c->gstream);
     for (int k = 0; k < 2; ++k)
@@ -902,6 +977,23 @@ nbody_status nbody_get_walk_shape(nbody_ctx *c, int32_t *shape, int32_t *threads
     const int k = c->p.precision == NBODY_FP64 ? c->shape64 : c->shape32;
     if (shape) *shape = k;
     if (threads_per_block) *threads_per_block = walk_shape_threads(c->p.precision, k);
+    return NBODY_OK;
+}
+
+nbody_status nbody_set_sort_mode(nbody_ctx *c, int32_t mode)
+{
+    if (!c) return NBODY_EINVAL;
+    if (mode < NBODY_SORT_AUTO || mode > NBODY_SORT_RESORT)
+        return fail(c, NBODY_EINVAL, "sort mode %d not in 0..2", (int)mode);
+    c->sort_mode = mode;
+    return NBODY_OK;
+}
+
+nbody_status nbody_get_sort_stats(nbody_ctx *c, int32_t *path, int64_t *removed)
+{
+    if (!c) return NBODY_EINVAL;
+    if (path) *path = c->last_sort_path;
+    if (removed) *removed = c->last_removed;
     return NBODY_OK;
 }
 

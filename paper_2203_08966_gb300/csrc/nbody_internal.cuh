@@ -40,6 +40,36 @@ struct Box {
     double c[3];      // origin of the FP32 coordinates: the centre of mass
 };
 
+// Morton keys (§4.4): q = clamp(floor((x - o) * s), 0, 2^21 - 1) per axis, then the bits of
+// q_x, q_y, q_z interleaved with x most significant (a 63-bit key in one 64-bit word).
+__device__ __forceinline__ uint32_t quantise(double x, double o, double s)
+{
+    double t = __dmul_rn(__dsub_rn(x, o), s);
+    if (!(t > 0.0)) return 0u;
+    double f = floor(t);
+    if (f >= (double)kQMax) return kQMax;
+    return (uint32_t)f;
+}
+
+// Spreads the low 21 bits of v so that bit b lands on bit 3b.
+__device__ __forceinline__ uint64_t spread3(uint64_t v)
+{
+    v &= 0x1fffffull;
+    v = (v | (v << 32)) & 0x001f00000000ffffull;
+    v = (v | (v << 16)) & 0x001f0000ff0000ffull;
+    v = (v | (v << 8)) & 0x100f00f00f00f00full;
+    v = (v | (v << 4)) & 0x10c30c30c30c30c3ull;
+    v = (v | (v << 2)) & 0x1249249249249249ull;
+    return v;
+}
+
+__device__ __forceinline__ uint64_t morton_key(double x, double y, double z, const Box &b)
+{
+    const double s = b.s;
+    return (spread3(quantise(x, b.o[0], s)) << 2) | (spread3(quantise(y, b.o[1], s)) << 1) |
+           spread3(quantise(z, b.o[2], s));
+}
+
 // Device error word bits.
 enum : int { kErrNodeCap = 1, kErrTimeout = 2, kErrStack = 4 };
 
@@ -86,7 +116,7 @@ void launch_keys(const double *pos, int n, const Box *box, const Systems &ss, ui
 struct SortScratch {
     uint64_t *keys_alt;
     uint32_t *ids_alt;
-    uint32_t *hist;       // 10 x 256 digit totals (8 key passes, 2 system passes)
+    uint32_t *hist;       // 12 x 256 digit totals (8 key passes, up to 4 id passes)
     uint32_t *counts;     // 256 x tiles
     int max_tiles;
     const uint16_t *sys;  // forest: two more stable passes on the system of every id
@@ -96,6 +126,12 @@ int sort_tiles(int n);
 cudaError_t sort_prepare(); // one-time function attributes
 void launch_radix_sort(uint64_t *keys, uint32_t *ids, int n, const SortScratch &sc,
                        cudaStream_t s);
+// Sort of (key, id) pairs by key, then id, for ids in no particular order (ids < 2^id_bits):
+// passes on the id bytes first, then the key passes.  The sorted pairs end in (keys, ids) or in
+// (sc.keys_alt, sc.ids_alt); *out_keys / *out_ids say which.
+void launch_radix_sort_key_id(uint64_t *keys, uint32_t *ids, int n, int id_bits,
+                              const SortScratch &sc, cudaStream_t s, uint64_t **out_keys,
+                              uint32_t **out_ids);
 
 void launch_permute(const D4 *aos, const uint32_t *ids, int n, const Box *box, const Systems &ss,
                     double G, D4 *sbody64, float4 *sbody32, cudaStream_t s);
@@ -184,6 +220,35 @@ void launch_clamp_count(const uint32_t *total, int64_t cap, uint32_t *nn, int *e
 // Forest: level-order index of every system's root.
 void launch_roots(const NodeArrays &na, const uint32_t *node_off, const Systems &ss, int *roots,
                   cudaStream_t s);
+
+// ---------------------------------------------------------------- order_kernels.cu
+// Re-sort from the previous step's order (§4.4): bodies move little in one step, so last step's
+// sorted list is almost sorted.  The result equals the stable sort by (key, caller's index):
+//   extract  keys of the bodies in the previous order (gathered through its permutation); every
+//            body in a descent of that sequence is removed, repeatedly, until the rest ascends
+//            (inside tiles in shared memory, then across tile seams);
+//   merge    the removed bodies are sorted by (key, id) and merged with the kept ones.
+struct OrderScratch {
+    uint32_t *keep;      // one bit per position of the previous order: still in the ascending rest
+    int2 *ends;          // per tile: first and last kept position (-1: none)
+    uint32_t *seams;     // one bit per tile: the seam before it needs the fix-up
+    uint32_t *kept_off;  // per tile: kept positions before it
+    unsigned *stats;     // kOrderKept, kOrderSeams, kOrderGaveUp
+    int *split;          // merge path: kept bodies before each merge tile
+    uint64_t *rk, *xk;   // kept / removed keys
+    uint32_t *ri, *xi;   // their ids
+};
+enum : int { kOrderKept = 0, kOrderSeams = 1, kOrderGaveUp = 2, kOrderStats = 4 };
+int order_tiles(int n);        // extract tiles (entries of ends and kept_off)
+int order_merge_tiles(int n);  // merge tiles (split has one more entry)
+// keys: out, the keys in the previous order (read again by launch_order_merge).  prev: the
+// previous sorted ids.  Writes stats (the host reads kept and gave-up before choosing a path).
+void launch_order_extract(const D4 *aos, const uint32_t *prev, int n, const Box *box,
+                          uint64_t *keys, const OrderScratch &o, cudaStream_t s);
+// kept: the count the extract wrote.  Leaves the sorted keys and ids in (keys, ids); sc is the
+// radix sort's scratch (sorts the removed bodies).
+void launch_order_merge(uint64_t *keys, uint32_t *ids, int n, int kept, const OrderScratch &o,
+                        const SortScratch &sc, cudaStream_t s);
 
 // ---------------------------------------------------------------- walk_kernels.cu
 struct WalkArgs {
