@@ -46,6 +46,15 @@ BYTES_KICK_KEYS = 80 + 48 + 32 + 24 + 12
 #   radix sort: digit histograms read the keys once (8 B); each of 8 passes reads the keys in the
 #   upsweep (8 B) and reads + writes keys and ids in the downsweep (24 B)
 BYTES_SORT = 8 + 8 * (8 + 24)
+# Re-sort from the previous order (§4.4) instead of keys + radix sort:
+#   extract: previous id read (4 B), the body's (x, y, z, m) record gathered (32 B), key written
+#   (8 B)
+BYTES_KICK_EXTRACT = 80 + 48 + 32 + 4 + 32 + 8
+#   split: key + id read, written to the kept or removed list (24 B); merge: both lists read,
+#   keys + ids written (24 B); plus, per removed body, the radix sort by (key, id) with 3 id
+#   passes (8 + 11 * 32 B)
+BYTES_RESORT_FIXED = 24 + 24
+BYTES_RESORT_PER_REMOVED = 8 + 11 * 32
 CPU_SAMPLE_N = 1 << 20             # bodies in the CPU-baseline sample
 CPU_SAMPLE_STEPS = 3               # timed oracle steps on that sample (about 10-15 s on 16 cores)
 REF_SAMPLE_N = 1 << 20             # bodies per step of the reference arm
@@ -62,6 +71,8 @@ def parse():
                     help="override N (smaller runs, profiling; --bodies under torchrun)")
     ap.add_argument("--precision", default="fp32_kahan", choices=["fp64", "fp32", "fp32_kahan"])
     ap.add_argument("--theta", type=float, default=None)
+    ap.add_argument("--sort", default="auto", choices=["auto", "full"],
+                    help="auto: re-sort from the previous step's order (§4.4); full: radix sort")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 512-system forest line")
@@ -399,6 +410,7 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
 
     ctx = nb.Context(n, 1.0, w["eps"], w["theta"], w["dt"], prec, stream=stream)
+    ctx.set_sort_mode(nb.SORT_FULL if args.sort == "full" else nb.SORT_AUTO)
     shape, shape_ms = ctx.autotune(tp, tm)   # launch shape of the walk, before any timing
     shape_threads = ctx.walk_shape()[1]
     ctx.enable_timing(True)
@@ -423,6 +435,12 @@ def run_ours(args):
         ev1.record(stream)
         torch.cuda.synchronize()
     launches = nb.launch_count() - l0
+    sort_path, sort_removed = ctx.sort_stats()   # of the last timed step
+    if sort_path == 1:
+        b_keys = BYTES_KICK_EXTRACT
+        b_sort = BYTES_RESORT_FIXED + BYTES_RESORT_PER_REMOVED * sort_removed / n
+    else:
+        b_keys, b_sort = BYTES_KICK_KEYS, BYTES_SORT
     if ws > 1:
         dist.barrier()
     ms = ev0.elapsed_time(ev1)
@@ -501,12 +519,14 @@ def run_ours(args):
         "phase_ms": {k: float(v / args.steps) for k, v in
                      zip(("kick_box_keys", "sort", "permute_split_moments", "walk", "step"),
                          phase)},
+        "sort": {"mode": args.sort, "path": "resort" if sort_path == 1 else "full",
+                 "removed_fraction": (sort_removed / n) if sort_removed >= 0 else None},
         "build_roofline": {
             "unit": "GB/s", "peak": peaks.get("hbm_gbs"), "peak_source": f"{peak_src} copy bandwidth",
-            "kick_box_keys": {"bytes_per_body": BYTES_KICK_KEYS,
-                              "achieved": BYTES_KICK_KEYS * n / (phase[0] / args.steps * 1e-3) / 1e9},
-            "sort": {"bytes_per_body": BYTES_SORT,
-                     "achieved": BYTES_SORT * n / (phase[1] / args.steps * 1e-3) / 1e9}},
+            "kick_box_keys": {"bytes_per_body": b_keys,
+                              "achieved": b_keys * n / (phase[0] / args.steps * 1e-3) / 1e9},
+            "sort": {"bytes_per_body": b_sort,
+                     "achieved": b_sort * n / (phase[1] / args.steps * 1e-3) / 1e9}},
         "interactions_per_step": inter,
         "interactions_per_s": inter / (walk_avg * 1e-3),
         "roofline": {"kernel": "walk32 (Kahan)" if args.precision == "fp32_kahan" else
