@@ -546,18 +546,18 @@ __device__ __forceinline__ void walk_group(const WalkArgs &a, GroupSmem &S, Quad
         // ---- pop up to 32 nodes from the top ranges (lane k reads the k-th range from the top)
         const int ne = min(sp, 32);
         uint32_t pk = 0, pmk = 0;
-        unsigned cnt = 0;
+        unsigned cm1 = 0;  // range size - 1 (0..7)
         if (lane < ne) {
             pk = S.st_node[sp - 1 - lane];
             pmk = S.st_mask[sp - 1 - lane];
-            cnt = (pk >> 28) + 1u;
+            cm1 = pk >> 28;
         }
-        // exclusive prefix sum of the range sizes (1..8) from their bits, one ballot per bit
-        const unsigned b0 = __ballot_sync(kFull, cnt & 1u), b1 = __ballot_sync(kFull, cnt & 2u);
-        const unsigned b2 = __ballot_sync(kFull, cnt & 4u), b3 = __ballot_sync(kFull, cnt & 8u);
-        const int excl = __popc(b0 & lt) + 2 * __popc(b1 & lt) + 4 * __popc(b2 & lt) +
-                         8 * __popc(b3 & lt);
-        const int total = __popc(b0) + 2 * __popc(b1) + 4 * __popc(b2) + 8 * __popc(b3);
+        // exclusive prefix sum of the range sizes: one per range before this lane's plus the
+        // sizes - 1 from their bits, one ballot per bit
+        const unsigned b0 = __ballot_sync(kFull, cm1 & 1u), b1 = __ballot_sync(kFull, cm1 & 2u);
+        const unsigned b2 = __ballot_sync(kFull, cm1 & 4u);
+        const int excl = min(lane, ne) + __popc(b0 & lt) + 2 * __popc(b1 & lt) + 4 * __popc(b2 & lt);
+        const int total = ne + __popc(b0) + 2 * __popc(b1) + 4 * __popc(b2);
         const bool touched = lane < ne && excl < 32;
         const int nt = __popc(__ballot_sync(kFull, touched));       // ranges touched: 0 .. nt-1
         const int last_excl = __shfl_sync(kFull, excl, nt - 1);
@@ -648,27 +648,33 @@ __device__ __forceinline__ void walk_group(const WalkArgs &a, GroupSmem &S, Quad
         }
 
         // ---- mixed cells: every body tests its own acceptance, two cells per pass
-        unsigned mx = kGroup ? 0u : __ballot_sync(kFull, kind == kMixed);
+        // (the cells' x, y, z, crit go through the full-entry buffer and the bodies' acceptance
+        // masks back through the mask buffer: both are empty between the drain and the emit)
+        const unsigned mx = kGroup ? 0u : __ballot_sync(kFull, kind == kMixed);
         unsigned myA = 0u;
-        const float crit_l = __int_as_float(meta.z);
-        while (mx) {
-            const int s1 = __ffs(mx) - 1;
-            mx &= mx - 1u;
-            const int s2 = mx ? __ffs(mx) - 1 : s1;
-            mx &= mx - 1u;
-            const float x1 = __shfl_sync(kFull, c.x, s1), x2 = __shfl_sync(kFull, c.x, s2);
-            const float y1 = __shfl_sync(kFull, c.y, s1), y2 = __shfl_sync(kFull, c.y, s2);
-            const float z1 = __shfl_sync(kFull, c.z, s1), z2 = __shfl_sync(kFull, c.z, s2);
-            const float k1 = __shfl_sync(kFull, crit_l, s1), k2 = __shfl_sync(kFull, crit_l, s2);
-            // the per-body test, both cells at once (each component rounded as the scalar form)
-            const float2 dx = __fadd2_rn(make_float2(x1, x2), nme[0]);
-            const float2 dy = __fadd2_rn(make_float2(y1, y2), nme[1]);
-            const float2 dz = __fadd2_rn(make_float2(z1, z2), nme[2]);
-            const float2 q = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
-            const unsigned A1 = __ballot_sync(kFull, q.x > k1);
-            const unsigned A2 = __ballot_sync(kFull, q.y > k2);
-            if (lane == s1) myA = A1;
-            if (lane == s2) myA = A2;
+        if (mx) {
+            const int nm = __popc(mx);
+            const int r = __popc(mx & lt);
+            if (kind == kMixed)
+                put_entry(S.f, r, make_float4(c.x, c.y, c.z, __int_as_float(meta.z)));
+            __syncwarp();
+            uint32_t *A = reinterpret_cast<uint32_t *>(S.pm);
+            for (int k = 0; k < nm; k += 2) {
+                const float4 u = S.f[k], v = S.f[k + 1];
+                const float2 dx = __fadd2_rn(make_float2(u.x, u.y), nme[0]);
+                const float2 dy = __fadd2_rn(make_float2(u.z, u.w), nme[1]);
+                const float2 dz = __fadd2_rn(make_float2(v.x, v.y), nme[2]);
+                const float2 q = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+                const unsigned A1 = __ballot_sync(kFull, q.x > v.z);
+                const unsigned A2 = __ballot_sync(kFull, q.y > v.w);
+                if (lane == 0) {
+                    A[k] = A1;
+                    A[k + 1] = A2;
+                }
+            }
+            __syncwarp();
+            if (kind == kMixed) myA = A[r];
+            __syncwarp();
         }
         unsigned pmask = kind == kOpen ? m : 0u;   // bodies that need this cell's children
         if (kind == kMixed) {
