@@ -227,18 +227,20 @@ nbody_status nbody_get_walk_shape(nbody_ctx *c, int32_t *shape, int32_t *threads
 
 /* ---- re-sort from the previous step's order (temporal coherence, §4.4) ---- */
 
-/* How a build sorts the bodies by (key, index).  Every mode gives the same order, bit for bit;
- * they differ only in cost.
+/* How a build sorts the bodies by (key, index) (forests: by (system, key, index)).  Every mode
+ * gives the same order, bit for bit; they differ only in cost.
  *   NBODY_SORT_AUTO    (default) when the context's last build was of the same n, start from
  *                      its sorted order: bodies move little in one step (§4.4), so that order
  *                      is almost sorted.  Every body in a descent of it is taken out (until the
  *                      rest ascends), the bodies taken out are radix-sorted and merged back.
- *                      Used from 65,536 bodies; when more than a quarter of the bodies are
- *                      taken out the build runs the full sort instead.
- *   NBODY_SORT_FULL    always the full 8-pass radix sort of the keys.
+ *                      Used from 65,536 bodies (a forest: in total); when more than a quarter of
+ *                      the bodies are taken out the build runs the full sort instead.
+ *   NBODY_SORT_FULL    always the full radix sort of the keys.
  *   NBODY_SORT_RESORT  as AUTO from any n > 0 and any number taken out (for tests).
  * Either re-sort falls back to the full sort when its repair of tile seams exceeds its step
- * limit.  Forest contexts always run the full sort.  Errors: EINVAL for an unknown mode. */
+ * limit.  The choice between re-sort and full sort is made on the device, so a forest step
+ * stays capturable as a CUDA graph (a change of mode recaptures it).  Errors: EINVAL for an
+ * unknown mode. */
 #define NBODY_SORT_AUTO 0
 #define NBODY_SORT_FULL 1
 #define NBODY_SORT_RESORT 2
@@ -246,7 +248,8 @@ nbody_status nbody_set_sort_mode(nbody_ctx *c, int32_t mode);
 
 /* How the last build sorted: *path (may be NULL) 1 when it re-sorted from the previous order,
  * 0 for the full sort, -1 before any build; *removed (may be NULL) the bodies the re-sort took
- * out of the previous order (-1 when the build ran the full sort without trying). */
+ * out of the previous order (-1 when the build ran the full sort without trying).  Waits for the
+ * context's stream when the device made the choice. */
 nbody_status nbody_get_sort_stats(nbody_ctx *c, int32_t *path, int64_t *removed);
 
 /* ---- forest: many independent systems advanced together ---- */

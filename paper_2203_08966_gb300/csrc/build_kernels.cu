@@ -217,8 +217,10 @@ __device__ __forceinline__ int system_of(const Systems &ss, int i)
 }
 
 __global__ void keys_kernel(const double *__restrict__ pos, int n, const Box *__restrict__ box,
-                            Systems ss, uint64_t *__restrict__ keys, uint32_t *__restrict__ ids)
+                            Systems ss, uint64_t *__restrict__ keys, uint32_t *__restrict__ ids,
+                            const int *__restrict__ gate)
 {
+    if (gate && *gate == 0) return;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const Box *b = box + system_of(ss, i);
         keys[i] = morton_key(pos[i], pos[(size_t)n + i], pos[2 * (size_t)n + i], *b);
@@ -240,6 +242,12 @@ constexpr int kSortTile = kSortThreads * kSortItems;   // 4096 keys per tile
 constexpr int kPasses = 8;       // key passes
 constexpr int kSysPasses = 2;    // forest: system passes (systems < 2^16)
 constexpr int kIdPasses = 4;     // at most: passes on the id bytes before the key passes
+constexpr int kHistRows = kPasses + kIdPasses + kSysPasses;  // key, id, system digit totals
+
+// Pairs to sort: n, or (d_n non-null) the count on the device, at most n (the grids are sized
+// for n and the blocks past the device count return at once).
+__device__ __forceinline__ int sort_count(int n, const int *d_n) { return d_n ? min(*d_n, n) : n; }
+__device__ __forceinline__ int sort_tiles_dev(int n) { return (n + kSortTile - 1) / kSortTile; }
 constexpr size_t kDownSmem = (size_t)kSortTile * 8 + (size_t)kSortTile * 4 +
                              (size_t)kSortWarps * 256 * 4 + 256 * 4 + 256 * 4;
 
@@ -250,16 +258,20 @@ __device__ __forceinline__ unsigned lanemask_lt()
     return m;
 }
 
-// Digit totals of every pass: the 8 key bytes, then (id_passes > 0) the low id bytes.
+// Digit totals of every pass: rows 0-7 the key bytes, rows 8.. the low id bytes (id_passes), rows
+// 12-13 the bytes of the system of each id (sys non-null: a subset of a forest's bodies).
 __global__ void __launch_bounds__(kSortThreads) radix_hist_kernel(const uint64_t *__restrict__ keys,
                                                                  const uint32_t *__restrict__ ids,
-                                                                 int n, int id_passes,
+                                                                 int n, const int *d_n,
+                                                                 int id_passes,
+                                                                 const uint16_t *__restrict__ sys,
                                                                  uint32_t *hist)
 {
-    __shared__ uint32_t sh[kPasses + kIdPasses][256];
-    const int rows = kPasses + id_passes;
-    for (int k = threadIdx.x; k < rows * 256; k += blockDim.x) (&sh[0][0])[k] = 0;
+    __shared__ uint32_t sh[kHistRows][256];
+    const int rows = sys ? kHistRows : kPasses + id_passes;
+    for (int k = threadIdx.x; k < kHistRows * 256; k += blockDim.x) (&sh[0][0])[k] = 0;
     __syncthreads();
+    n = sort_count(n, d_n);
     const int lane = threadIdx.x & 31;
     const int stride = gridDim.x * blockDim.x;
     for (int base = blockIdx.x * blockDim.x; base < n; base += stride) {
@@ -272,13 +284,22 @@ __global__ void __launch_bounds__(kSortThreads) radix_hist_kernel(const uint64_t
             const unsigned peers = __match_any_sync(kFull, d);
             if (ok && (__ffs(peers) - 1) == lane) atomicAdd(&sh[p][d], __popc(peers));
         }
-        if (id_passes > 0) {
+        if (id_passes > 0 || sys) {
             const uint32_t id = ok ? ids[i] : 0u;
             for (int p = 0; p < id_passes; ++p) {
                 const unsigned d = ok ? (id >> (8 * p)) & 255u : 256u;
                 const unsigned peers = __match_any_sync(kFull, d);
                 if (ok && (__ffs(peers) - 1) == lane)
                     atomicAdd(&sh[kPasses + p][d], __popc(peers));
+            }
+            if (sys) {
+                const unsigned sv = ok ? (unsigned)sys[id] : 0u;
+                for (int p = 0; p < kSysPasses; ++p) {
+                    const unsigned d = ok ? (sv >> (8 * p)) & 255u : 256u;
+                    const unsigned peers = __match_any_sync(kFull, d);
+                    if (ok && (__ffs(peers) - 1) == lane)
+                        atomicAdd(&sh[kPasses + kIdPasses + p][d], __popc(peers));
+                }
             }
         }
     }
@@ -304,10 +325,13 @@ __device__ __forceinline__ unsigned sort_digit(uint64_t key, uint32_t id, int sh
 template <int kMode>
 __global__ void __launch_bounds__(kSortThreads) radix_upsweep_kernel(const uint64_t *__restrict__ keys,
                                                                     const uint32_t *__restrict__ ids,
-                                                                    int n, int shift,
-                                                                    uint32_t *counts, int tiles,
+                                                                    int n, const int *d_n,
+                                                                    int shift, uint32_t *counts,
+                                                                    int tiles,
                                                                     const uint16_t *__restrict__ sys)
 {
+    n = sort_count(n, d_n);
+    if ((int)blockIdx.x >= sort_tiles_dev(n)) return;
     __shared__ uint32_t sh[256];
     sh[threadIdx.x] = 0;
     __syncthreads();
@@ -358,10 +382,13 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *t
 }
 
 // One block per digit: offsets of that digit's run in every tile, seeded by the number of keys
-// with a smaller digit (from the global histogram of this pass).
+// with a smaller digit (from the global histogram of this pass).  Rows are `tiles` apart; the
+// tiles in use follow from the pair count.
 __global__ void __launch_bounds__(kSortThreads) radix_rowscan_kernel(uint32_t *counts, int tiles,
+                                                                    int n, const int *d_n,
                                                                     const uint32_t *hist_pass)
 {
+    const int used = sort_tiles_dev(sort_count(n, d_n));
     const int d = blockIdx.x;
     uint32_t part = 0;
     for (int k = threadIdx.x; k < d; k += blockDim.x) part += hist_pass[k];
@@ -369,12 +396,12 @@ __global__ void __launch_bounds__(kSortThreads) radix_rowscan_kernel(uint32_t *c
     (void)block_exclusive_scan(part, &base);
     uint32_t *row = counts + (size_t)d * tiles;
     uint32_t carry = base;
-    for (int t0 = 0; t0 < tiles; t0 += blockDim.x) {
+    for (int t0 = 0; t0 < used; t0 += blockDim.x) {
         const int t = t0 + threadIdx.x;
-        const uint32_t v = t < tiles ? row[t] : 0u;
+        const uint32_t v = t < used ? row[t] : 0u;
         uint32_t tot;
         const uint32_t ex = block_exclusive_scan(v, &tot);
-        if (t < tiles) row[t] = carry + ex;
+        if (t < used) row[t] = carry + ex;
         carry += tot;
     }
 }
@@ -382,9 +409,11 @@ __global__ void __launch_bounds__(kSortThreads) radix_rowscan_kernel(uint32_t *c
 template <int kMode>
 __global__ void __launch_bounds__(kSortThreads) radix_downsweep_kernel(
     const uint64_t *__restrict__ keys_in, const uint32_t *__restrict__ ids_in,
-    uint64_t *__restrict__ keys_out, uint32_t *__restrict__ ids_out, int n, int shift,
-    const uint32_t *__restrict__ offsets, int tiles, const uint16_t *__restrict__ sys)
+    uint64_t *__restrict__ keys_out, uint32_t *__restrict__ ids_out, int n, const int *d_n,
+    int shift, const uint32_t *__restrict__ offsets, int tiles, const uint16_t *__restrict__ sys)
 {
+    n = sort_count(n, d_n);
+    if ((int)blockIdx.x >= sort_tiles_dev(n)) return;
     extern __shared__ __align__(16) unsigned char smem[];
     uint64_t *s_keys = reinterpret_cast<uint64_t *>(smem);
     uint32_t *s_ids = reinterpret_cast<uint32_t *>(s_keys + kSortTile);
@@ -1074,9 +1103,9 @@ void launch_system_boxes(const double *pos, const double *mass, int n, const Sys
 }
 
 void launch_keys(const double *pos, int n, const Box *box, const Systems &ss, uint64_t *keys,
-                 uint32_t *ids, cudaStream_t s)
+                 uint32_t *ids, cudaStream_t s, const int *gate)
 {
-    keys_kernel<<<grid_for(n, 256, kMaxGrid), 256, 0, s>>>(pos, n, box, ss, keys, ids);
+    keys_kernel<<<grid_for(n, 256, kMaxGrid), 256, 0, s>>>(pos, n, box, ss, keys, ids, gate);
     count_launches(1);
 }
 
@@ -1099,14 +1128,17 @@ namespace {
 
 // The digit passes of one sort: `id_passes` passes on id bytes, the 8 key passes, then (forest)
 // the system passes; the result ends in (keys, ids) or (keys_alt, ids_alt) by the parity of the
-// pass count.
+// pass count.  With sc.sys and no sc.sys_hist the system digit totals come from the data (a
+// subset of a forest's bodies).
 void radix_passes(uint64_t *keys, uint32_t *ids, int n, int id_passes, const SortScratch &sc,
                   cudaStream_t s, uint64_t **out_keys, uint32_t **out_ids)
 {
     const int tiles = sort_tiles(n);
-    cudaMemsetAsync(sc.hist, 0, sizeof(uint32_t) * (kPasses + id_passes) * 256, s);
+    const bool sys_data = sc.sys && !sc.sys_hist;
+    const int rows = sys_data ? kHistRows : kPasses + id_passes;
+    cudaMemsetAsync(sc.hist, 0, sizeof(uint32_t) * rows * 256, s);
     radix_hist_kernel<<<grid_for(n, kSortThreads * 8, 152 * 4), kSortThreads, 0, s>>>(
-        keys, ids, n, id_passes, sc.hist);
+        keys, ids, n, sc.d_n, id_passes, sys_data ? sc.sys : nullptr, sc.hist);
     uint64_t *kin = keys, *kout = sc.keys_alt;
     uint32_t *iin = ids, *iout = sc.ids_alt;
     const int sys_passes = sc.sys ? kSysPasses : 0;
@@ -1122,28 +1154,29 @@ void radix_passes(uint64_t *keys, uint32_t *ids, int n, int id_passes, const Sor
             shift = 8 * (p - id_passes);
             hist = sc.hist + 256 * (p - id_passes);
         } else {
-            shift = 8 * (p - id_passes - kPasses);
-            hist = sc.sys_hist + 256 * (p - id_passes - kPasses);
+            const int q = p - id_passes - kPasses;
+            shift = 8 * q;
+            hist = sys_data ? sc.hist + 256 * (kPasses + kIdPasses + q) : sc.sys_hist + 256 * q;
         }
         if (mode == kDigitId)
-            radix_upsweep_kernel<kDigitId><<<tiles, kSortThreads, 0, s>>>(kin, iin, n, shift,
-                                                                         sc.counts, tiles, nullptr);
+            radix_upsweep_kernel<kDigitId><<<tiles, kSortThreads, 0, s>>>(
+                kin, iin, n, sc.d_n, shift, sc.counts, tiles, nullptr);
         else if (mode == kDigitKey)
-            radix_upsweep_kernel<kDigitKey><<<tiles, kSortThreads, 0, s>>>(kin, iin, n, shift,
-                                                                          sc.counts, tiles, nullptr);
+            radix_upsweep_kernel<kDigitKey><<<tiles, kSortThreads, 0, s>>>(
+                kin, iin, n, sc.d_n, shift, sc.counts, tiles, nullptr);
         else
-            radix_upsweep_kernel<kDigitSys><<<tiles, kSortThreads, 0, s>>>(kin, iin, n, shift,
-                                                                          sc.counts, tiles, sc.sys);
-        radix_rowscan_kernel<<<256, kSortThreads, 0, s>>>(sc.counts, tiles, hist);
+            radix_upsweep_kernel<kDigitSys><<<tiles, kSortThreads, 0, s>>>(
+                kin, iin, n, sc.d_n, shift, sc.counts, tiles, sc.sys);
+        radix_rowscan_kernel<<<256, kSortThreads, 0, s>>>(sc.counts, tiles, n, sc.d_n, hist);
         if (mode == kDigitId)
             radix_downsweep_kernel<kDigitId><<<tiles, kSortThreads, kDownSmem, s>>>(
-                kin, iin, kout, iout, n, shift, sc.counts, tiles, nullptr);
+                kin, iin, kout, iout, n, sc.d_n, shift, sc.counts, tiles, nullptr);
         else if (mode == kDigitKey)
             radix_downsweep_kernel<kDigitKey><<<tiles, kSortThreads, kDownSmem, s>>>(
-                kin, iin, kout, iout, n, shift, sc.counts, tiles, nullptr);
+                kin, iin, kout, iout, n, sc.d_n, shift, sc.counts, tiles, nullptr);
         else
             radix_downsweep_kernel<kDigitSys><<<tiles, kSortThreads, kDownSmem, s>>>(
-                kin, iin, kout, iout, n, shift, sc.counts, tiles, sc.sys);
+                kin, iin, kout, iout, n, sc.d_n, shift, sc.counts, tiles, sc.sys);
         uint64_t *tk = kin; kin = kout; kout = tk;
         uint32_t *ti = iin; iin = iout; iout = ti;
     }

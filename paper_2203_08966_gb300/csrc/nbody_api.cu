@@ -27,7 +27,7 @@ struct nbody_ctx {
     D4 *aos = nullptr;              // (x, y, z, m) records in the caller's order
     float4 *sbody32 = nullptr;
     uint32_t *node_off = nullptr;   // cap + 1
-    uint32_t *hist = nullptr;       // 12 x 256
+    uint32_t *hist = nullptr;       // 14 x 256
     uint32_t *counts = nullptr;     // 256 x sort tiles
     uint32_t *block_sums = nullptr; // scan tiles + 1
     double *partials = nullptr;     // bbox_partial_doubles() x bbox blocks
@@ -69,7 +69,7 @@ struct nbody_ctx {
     // one forest step captured as a CUDA graph, replayed on its own stream
     cudaStream_t gstream = nullptr;
     cudaGraphExec_t gexec = nullptr;
-    const void *gkey[3] = {nullptr, nullptr, nullptr};
+    const void *gkey[4] = {nullptr, nullptr, nullptr, nullptr};
     int64_t glaunches = 0;          // kernels per replayed step
     cudaEvent_t gev[2] = {};
 
@@ -78,8 +78,8 @@ struct nbody_ctx {
     int64_t ord_cap = 0;
     int sort_mode = NBODY_SORT_AUTO;
     int64_t order_n = -1;       // c->ids holds the sorted order of the last build of this n
-    int last_sort_path = -1;    // 1 re-sort, 0 full sort, -1 no build yet
-    int64_t last_removed = -1;
+    int last_sort_path = -1;    // 0 full sort, 2 re-sort tried (the device's choice in ord.stats),
+                                // -1 no build yet
 
     // launch shape of the walk per precision class (FP32 forms, FP64), set by nbody_autotune
     int shape32 = kDefaultWalkShape, shape64 = kDefaultWalkShape;
@@ -287,6 +287,54 @@ void record(nbody_ctx *c, int k)
     if (c->timing) cudaEventRecord(c->ev[k], c->stream);
 }
 
+// Keys and sort of the bodies into c->keys / c->ids (keys computed from c->aos and c->box).
+// When the context's last build was of the same n, the re-sort from its order (§4.4) runs.  A
+// forest launches the full sort behind it for the case the device chooses that (its kernels
+// return at once otherwise) and reads nothing back, so its step stays capturable; a single
+// system reads the choice and launches only the chosen path.
+nbody_status sort_bodies(nbody_ctx *c, const double *pos, int n, const Systems &ss,
+                         const SortScratch &sc)
+{
+    cudaStream_t s = c->stream;
+    const bool resort = c->order_n == n && c->sort_mode != NBODY_SORT_FULL &&
+                        (c->sort_mode == NBODY_SORT_RESORT || n >= kResortMinN);
+    c->order_n = -1;
+    if (resort) {
+        CKS(ensure_order(c));
+        launch_order_extract(c->aos, c->ids, n, c->box, ss, c->sort_mode == NBODY_SORT_AUTO,
+                             c->keys, c->ord, s);
+        record(c, 1);
+        if (c->n_sys == 0) {
+            // a single system synchronises later in its build anyway: read the device's choice
+            // now and launch only that path
+            CK(cudaMemcpyAsync(c->h_word + 2, c->ord.stats, sizeof(uint32_t) * kOrderStats,
+                               cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            if (c->h_word[2 + kOrderResorted] != 0u) {
+                launch_order_merge(c->keys, c->ids, n, ss, c->ord, sc, s);
+            } else {
+                launch_keys(pos, n, c->box, ss, c->keys, c->ids, s);
+                launch_radix_sort(c->keys, c->ids, n, sc, s);
+            }
+        } else {
+            launch_order_merge(c->keys, c->ids, n, ss, c->ord, sc, s);
+            const int *full_n = order_full_count(c->ord);
+            launch_keys(pos, n, c->box, ss, c->keys, c->ids, s, full_n);
+            SortScratch sf = sc;
+            sf.d_n = full_n;
+            launch_radix_sort(c->keys, c->ids, n, sf, s);
+        }
+    } else {
+        launch_keys(pos, n, c->box, ss, c->keys, c->ids, s);
+        record(c, 1);
+        launch_radix_sort(c->keys, c->ids, n, sc, s);
+    }
+    CKS(check_launch(c, "sort"));
+    c->last_sort_path = resort ? 2 : 0;
+    c->order_n = n;
+    return NBODY_OK;
+}
+
 // Root box, keys, sort, permutation, node split and moments of (pos, mass).  When
 // `have_partials` the bbox partial reductions of pos are already in c->partials.
 nbody_status build(nbody_ctx *c, const double *pos, const double *mass, int n,
@@ -303,36 +351,7 @@ nbody_status build(nbody_ctx *c, const double *pos, const double *mass, int n,
     launch_bbox_finalize(c->partials, c->nblk, c->box, c->tab, c->p.theta, s);
     SortScratch sc{c->keys_alt, c->ids_alt, c->hist, c->counts, sort_tiles((int)c->cap), nullptr,
                    nullptr};
-    // re-sort from the last build's order (§4.4) when it is of the same n
-    bool resort = c->order_n == n && c->sort_mode != NBODY_SORT_FULL &&
-                  (c->sort_mode == NBODY_SORT_RESORT || n >= kResortMinN);
-    c->order_n = -1;
-    c->last_removed = -1;
-    if (resort) {
-        CKS(ensure_order(c));
-        launch_order_extract(c->aos, c->ids, n, c->box, c->keys, c->ord, s);
-        record(c, 1);
-        CKS(check_launch(c, "re-sort"));
-        CK(cudaMemcpyAsync(c->h_word + 2, c->ord.stats, sizeof(uint32_t) * kOrderStats,
-                           cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
-        const int64_t kept = (int64_t)c->h_word[2 + kOrderKept];
-        const bool gave_up = c->h_word[2 + kOrderGaveUp] != 0u;
-        if (kept < 0 || kept > n)
-            return fail(c, NBODY_ECUDA, "re-sort kept %lld of %d bodies", (long long)kept, n);
-        c->last_removed = n - kept;
-        if (gave_up || (c->sort_mode == NBODY_SORT_AUTO && 4 * (n - kept) > (int64_t)n))
-            resort = false;
-        else
-            launch_order_merge(c->keys, c->ids, n, (int)kept, c->ord, sc, s);
-    }
-    if (!resort) {
-        launch_keys(pos, n, c->box, one, c->keys, c->ids, s);
-        record(c, 1);
-        launch_radix_sort(c->keys, c->ids, n, sc, s);
-    }
-    c->last_sort_path = resort ? 1 : 0;
-    c->order_n = n;
+    CKS(sort_bodies(c, pos, n, one, sc));
     record(c, 2);
     launch_permute(c->aos, c->ids, n, c->box, one, c->p.G, c->sbody64, c->sbody32, s);
     CK(cudaMemsetAsync(c->info, 0, sizeof(unsigned), s));
@@ -429,10 +448,9 @@ nbody_status forest_build(nbody_ctx *c, const double *pos, const double *mass)
     const int n = (int)c->cap;
     const Systems ss = systems(c);
     launch_system_boxes(pos, mass, n, ss, c->box, c->tab, c->p.theta, c->aos, s);
-    launch_keys(pos, n, c->box, ss, c->keys, c->ids, s);
     SortScratch sc{c->keys_alt, c->ids_alt, c->hist, c->counts, sort_tiles(n), c->sys,
                    c->sys_hist};
-    launch_radix_sort(c->keys, c->ids, n, sc, s);
+    CKS(sort_bodies(c, pos, n, ss, sc));
     launch_permute(c->aos, c->ids, n, c->box, ss, c->p.G, c->sbody64, c->sbody32, s);
     CK(cudaMemsetAsync(c->info, 0, sizeof(unsigned), s));
     launch_count_nodes(c->keys, n, ss, c->node_off, c->info, s);
@@ -544,7 +562,7 @@ nbody_status nbody_create(nbody_ctx **out, int64_t n_capacity, const nbody_param
         CK(dalloc(&c->aos, cap));
         CK(dalloc(&c->sbody32, cap));
         CK(dalloc(&c->node_off, cap + 1));
-        CK(dalloc(&c->hist, 12 * 256));
+        CK(dalloc(&c->hist, 14 * 256));
         CK(dalloc(&c->counts, (size_t)256 * sort_tiles((int)cap)));
         CK(dalloc(&c->block_sums, (size_t)scan_tiles((int)cap + 1) + 1));
         c->nblk = bbox_blocks((int64_t)cap);
@@ -992,8 +1010,17 @@ nbody_status nbody_set_sort_mode(nbody_ctx *c, int32_t mode)
 nbody_status nbody_get_sort_stats(nbody_ctx *c, int32_t *path, int64_t *removed)
 {
     if (!c) return NBODY_EINVAL;
-    if (path) *path = c->last_sort_path;
-    if (removed) *removed = c->last_removed;
+    int32_t p = c->last_sort_path;
+    int64_t r = -1;
+    if (p == 2) {  // the device chose: read its words after the last build
+        CK(cudaMemcpyAsync(c->h_word + 2, c->ord.stats, sizeof(uint32_t) * kOrderStats,
+                           cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        p = c->h_word[2 + kOrderResorted] ? 1 : 0;
+        r = (int64_t)c->h_word[2 + kOrderRemoved];
+    }
+    if (path) *path = p;
+    if (removed) *removed = r;
     return NBODY_OK;
 }
 
@@ -1051,6 +1078,7 @@ nbody_status nbody_forest_create(nbody_ctx **out, int32_t n_systems, const int64
         // (Plummer-like systems need about 1.5) plus a full chain of 22 levels per system
         CKS(ensure_nodes(c, 4 * n + 22 * (int64_t)S + 1024));
         CKS(ensure_quad(c));
+        CKS(ensure_order(c));  // the re-sort's scratch: never allocated inside a (captured) step
         if (c->na.cap > kMaxGroupNodes)
             return fail(c, NBODY_EINVAL, "forest of %lld bodies exceeds the node index range",
                         (long long)n);
@@ -1103,7 +1131,8 @@ nbody_status nbody_forest_step(nbody_ctx *c, double *d_pos, double *d_vel, const
         CK(cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking));
         for (int k = 0; k < 2; ++k) CK(cudaEventCreateWithFlags(&c->gev[k], cudaEventDisableTiming));
     }
-    const void *key[3] = {d_pos, d_vel, d_mass};
+    // the captured step depends on the buffers and on the sort mode (re-sort or full sort)
+    const void *key[4] = {d_pos, d_vel, d_mass, reinterpret_cast<const void *>((intptr_t)c->sort_mode)};
     if (!c->gexec || memcmp(key, c->gkey, sizeof(key)) != 0) {
         if (c->gexec) {
             cudaGraphExecDestroy(c->gexec);

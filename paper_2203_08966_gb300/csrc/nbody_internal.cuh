@@ -110,17 +110,21 @@ void launch_kick_drift(double *pos, double *vel, const double *acc, int n, doubl
                        cudaStream_t s);
 void launch_system_boxes(const double *pos, const double *mass, int n, const Systems &ss,
                          Box *box, LevelTables *tab, double theta, D4 *aos, cudaStream_t s);
+// gate (may be null): a device count; the kernel does nothing when it is 0.
 void launch_keys(const double *pos, int n, const Box *box, const Systems &ss, uint64_t *keys,
-                 uint32_t *ids, cudaStream_t s);
+                 uint32_t *ids, cudaStream_t s, const int *gate = nullptr);
 
 struct SortScratch {
     uint64_t *keys_alt;
     uint32_t *ids_alt;
-    uint32_t *hist;       // 12 x 256 digit totals (8 key passes, up to 4 id passes)
+    uint32_t *hist;       // 14 x 256 digit totals (8 key passes, up to 4 id passes, 2 system
+                          // passes of a subset of a forest's bodies)
     uint32_t *counts;     // 256 x tiles
     int max_tiles;
     const uint16_t *sys;  // forest: two more stable passes on the system of every id
-    const uint32_t *sys_hist;  // their digit totals (2 x 256, fixed per forest)
+    const uint32_t *sys_hist;  // their digit totals (2 x 256, fixed per forest); null with sys:
+                               // counted from the data (the sort of a subset of the bodies)
+    const int *d_n = nullptr;  // non-null: the pair count is read on the device (at most n)
 };
 int sort_tiles(int n);
 cudaError_t sort_prepare(); // one-time function attributes
@@ -223,32 +227,52 @@ void launch_roots(const NodeArrays &na, const uint32_t *node_off, const Systems 
 
 // ---------------------------------------------------------------- order_kernels.cu
 // Re-sort from the previous step's order (§4.4): bodies move little in one step, so last step's
-// sorted list is almost sorted.  The result equals the stable sort by (key, caller's index):
+// sorted list is almost sorted.  The result equals the stable sort by (system, key, caller's
+// index):
 //   extract  keys of the bodies in the previous order (gathered through its permutation); every
 //            body in a descent of that sequence is removed, repeatedly, until the rest ascends
-//            (inside tiles in shared memory, then across tile seams);
-//   merge    the removed bodies are sorted by (key, id) and merged with the kept ones.
+//            (inside tiles in shared memory, then across tile seams); then the device decides:
+//            re-sort, or (the seam repair gave up, or with auto_limit more than a quarter of the
+//            bodies were removed) the full sort;
+//   merge    the removed bodies are sorted by (system, key, id) and merged with the kept ones.
+// Nothing is read back to the host: the kernels of the path not taken return at once, so a step
+// can be captured in a CUDA graph.
 struct OrderScratch {
     uint32_t *keep;      // one bit per position of the previous order: still in the ascending rest
     int2 *ends;          // per tile: first and last kept position (-1: none)
     uint32_t *seams;     // one bit per tile: the seam before it needs the fix-up
     uint32_t *kept_off;  // per tile: kept positions before it
-    unsigned *stats;     // kOrderKept, kOrderSeams, kOrderGaveUp
+    unsigned *stats;     // kOrder* words
     int *split;          // merge path: kept bodies before each merge tile
     uint64_t *rk, *xk;   // kept / removed keys
     uint32_t *ri, *xi;   // their ids
 };
-enum : int { kOrderKept = 0, kOrderSeams = 1, kOrderGaveUp = 2, kOrderStats = 4 };
+enum : int {
+    kOrderKept = 0,      // kept positions
+    kOrderSeams = 1,     // tile seams flagged for the repair
+    kOrderGaveUp = 2,    // the repair ran out of steps
+    kOrderRemoved = 3,   // removed positions
+    kOrderXn = 4,        // removed positions when re-sorting, else 0 (count of the removed sort)
+    kOrderFullN = 5,     // n when the full sort runs instead, else 0
+    kOrderResorted = 6,  // 1: re-sorted
+    kOrderStats = 8
+};
 int order_tiles(int n);        // extract tiles (entries of ends and kept_off)
 int order_merge_tiles(int n);  // merge tiles (split has one more entry)
 // keys: out, the keys in the previous order (read again by launch_order_merge).  prev: the
-// previous sorted ids.  Writes stats (the host reads kept and gave-up before choosing a path).
+// previous sorted ids.  auto_limit: fall back to the full sort above a quarter removed.
 void launch_order_extract(const D4 *aos, const uint32_t *prev, int n, const Box *box,
-                          uint64_t *keys, const OrderScratch &o, cudaStream_t s);
-// kept: the count the extract wrote.  Leaves the sorted keys and ids in (keys, ids); sc is the
+                          const Systems &ss, bool auto_limit, uint64_t *keys,
+                          const OrderScratch &o, cudaStream_t s);
+// Leaves the sorted keys and ids in (keys, ids) when the device chose the re-sort; sc is the
 // radix sort's scratch (sorts the removed bodies).
-void launch_order_merge(uint64_t *keys, uint32_t *ids, int n, int kept, const OrderScratch &o,
-                        const SortScratch &sc, cudaStream_t s);
+void launch_order_merge(uint64_t *keys, uint32_t *ids, int n, const Systems &ss,
+                        const OrderScratch &o, const SortScratch &sc, cudaStream_t s);
+// Device count for the full sort's kernels: n when the device chose the full sort, else 0.
+inline const int *order_full_count(const OrderScratch &o)
+{
+    return reinterpret_cast<const int *>(o.stats + kOrderFullN);
+}
 
 // ---------------------------------------------------------------- walk_kernels.cu
 struct WalkArgs {

@@ -178,3 +178,51 @@ def test_forest_rejects_single_system_calls():
     with nb.Context.forest(off, 1.0, 0.01, 0.5, 1e-3, nb.FP64) as ctx:
         with pytest.raises(nb.NBodyError):
             ctx.forces(dev(pos), dev(mass))
+
+
+@pytest.mark.parametrize("prec", [nb.FP64, nb.FP32_KAHAN])
+def test_forest_resort_steps_identical_to_full_sort(prec):
+    """Re-sorting from the previous step's order (§4.4) inside a forest, launched and replayed
+    from a graph, leaves the same states bit for bit as the full sort."""
+    pos, vel, mass, off = ics.forest(24, 12, 256, 4096)
+    n = int(off[-1])
+    out = []
+    for mode, graph in ((nb.SORT_FULL, False), (nb.SORT_RESORT, False), (nb.SORT_RESORT, True)):
+        tp, tv, tm = dev(pos), dev(vel), dev(mass)
+        with nb.Context.forest(off, 1.0, 0.01, 0.6, 1e-3, prec) as ctx:
+            ctx.set_sort_mode(mode)
+            ctx.forest_step(tp, tv, tm, 4, use_graph=graph)
+            ctx.sync()
+            path, _ = ctx.sort_stats()
+            assert path == (0 if mode == nb.SORT_FULL else 1)
+            out.append((tp.cpu().numpy(), tv.cpu().numpy(), ctx.keys(n)))
+    for o in out[1:]:
+        assert np.array_equal(o[0], out[0][0]) and np.array_equal(o[1], out[0][1])
+        assert np.array_equal(o[2][0], out[0][2][0]) and np.array_equal(o[2][1], out[0][2][1])
+
+
+def test_forest_resort_after_jumps_matches_oracle():
+    """Second build of a forest after a tenth of every system's bodies jumped across their
+    system: keys and order per system equal the oracle's, systems in order."""
+    pos, _, mass, off = FOREST
+    n = int(off[-1])
+    rng = np.random.default_rng(5)
+    p1 = pos.copy()
+    for lo, hi in systems(off):
+        if hi - lo > 2:
+            sel = lo + rng.choice(hi - lo, max(1, (hi - lo) // 10), replace=False)
+            c = pos[:, lo:hi].mean(axis=1, keepdims=True)
+            p1[:, sel] = 2 * c - p1[:, sel]
+    with nb.Context.forest(off, 1.0, 0.01, 0.5, 1e-3, nb.FP64) as ctx:
+        ctx.set_sort_mode(nb.SORT_RESORT)
+        ctx.forest_forces(dev(pos), dev(mass))
+        ctx.forest_forces(dev(p1), dev(mass))
+        ctx.sync()
+        assert ctx.sort_stats()[0] == 1
+        keys, ids = ctx.keys(n)
+    for lo, hi in systems(off):
+        if hi == lo:
+            continue
+        ko, io = oracle.sort_pairs(oracle.keys(p1[:, lo:hi]))
+        assert np.array_equal(ids[lo:hi], io + lo)
+        assert np.array_equal(keys[lo:hi], ko)
