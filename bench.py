@@ -77,6 +77,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 512-system forest line")
     ap.add_argument("--no-accuracy", action="store_true", help="skip the per-theta error report")
+    ap.add_argument("--batch-only", action="store_true",
+                    help="only the 512-system forest (FP32-Kahan), one JSON line with its figures")
+    ap.add_argument("--batch-steps", type=int, default=100, help="graph-replayed forest steps")
     return ap.parse_args()
 
 
@@ -220,7 +223,7 @@ def run_reference(args):
 
 # ------------------------------------------------------------------ GPU arm
 
-def measure_batch(nb, torch, dev, stream, steps=100):
+def measure_batch(nb, torch, dev, stream, steps=100, with_fp64=True):
     """The batched forest (512 Plummer systems, N_s log-uniform in [1024, 65536], eps 0.01,
     theta 0.6, dt 1e-3, FP32-Kahan forces): `steps` leapfrog steps replayed from one captured
     CUDA graph, timed with CUDA events on the context stream; plus the same steps launched
@@ -254,14 +257,17 @@ def measure_batch(nb, torch, dev, stream, steps=100):
     ms = ev[0].elapsed_time(ev[1])
     ms_launched = ev[2].elapsed_time(ev[3]) / k
     # the plain FP64 path on the same forest, one launched step after its starting forces
-    with nb.Context.forest(off, 1.0, w["eps"], w["theta"], w["dt"], nb.FP64, stream=stream) as c64:
-        c64.forest_step(tp, tv, tm, 1, use_graph=False)
-        c64.sync()
-        ev[0].record(stream)
-        c64.forest_step(tp, tv, tm, 1, use_graph=False)
-        ev[1].record(stream)
-        torch.cuda.synchronize()
-        ms64 = ev[0].elapsed_time(ev[1])
+    ms64 = None
+    if with_fp64:
+        with nb.Context.forest(off, 1.0, w["eps"], w["theta"], w["dt"], nb.FP64,
+                               stream=stream) as c64:
+            c64.forest_step(tp, tv, tm, 1, use_graph=False)
+            c64.sync()
+            ev[0].record(stream)
+            c64.forest_step(tp, tv, tm, 1, use_graph=False)
+            ev[1].record(stream)
+            torch.cuda.synchronize()
+            ms64 = ev[0].elapsed_time(ev[1])
     return {"metric": "batch steps/s", "value": steps / (ms * 1e-3), "unit": "steps/s",
             "workload": "forest_512", "systems": int(w["systems"]), "bodies": n,
             "bodies_per_s": n * steps / (ms * 1e-3), "ms_per_step": ms / steps,
@@ -397,6 +403,15 @@ def run_ours(args):
     if ws > 1:
         dist.barrier()
     nb.load_library()
+    if args.batch_only:
+        if rank == 0:
+            dev = torch.device("cuda", local)
+            b = measure_batch(nb, torch, dev, torch.cuda.current_stream(), args.batch_steps,
+                              with_fp64=False)
+            print(json.dumps({"batch": b}))
+        if ws > 1:
+            dist.destroy_process_group()
+        return
 
     w, pos, vel, mass = make_workload(args.workload, args.n)
     if args.theta is not None:
