@@ -170,36 +170,58 @@ __global__ void __launch_bounds__(kBoxThreads) bbox_finalize_kernel(const double
 }
 
 // Forest: leapfrog kick and drift of every body (eqs. leapkick1, leapdrift of §2.4).
-__global__ void kick_drift_kernel(double *__restrict__ pos, double *__restrict__ vel,
-                                  const double *__restrict__ acc, int n, double h, double dt)
+// Forest: one block per system reduces its bodies and writes its root box and level tables.
+// Forest: the partial box of one chunk of bodies per block (a chunk never crosses a system),
+// with a step's kick and drift fused in when vel is non-null (the same operations as
+// kick_drift_bbox_kernel), writing the (x, y, z, m) records.  chunks[b] = (first body, end,
+// system).
+__global__ void __launch_bounds__(kBoxThreads) forest_box_partials_kernel(
+    double *__restrict__ pos, double *__restrict__ vel, const double *__restrict__ acc,
+    const double *__restrict__ mass, int n, const int4 *__restrict__ chunks, double h, double dt,
+    double *__restrict__ partials, D4 *__restrict__ aos)
 {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int4 ch = chunks[blockIdx.x];
+    double v[kPart];
+    init10(v);
+    for (int i = ch.x + threadIdx.x; i < ch.y; i += blockDim.x) {
+        double r[3];
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
             const size_t k = (size_t)d * n + i;
-            const double vh = __dadd_rn(vel[k], __dmul_rn(acc[k], h));
-            vel[k] = vh;
-            pos[k] = __dadd_rn(pos[k], __dmul_rn(vh, dt));
+            if (vel) {
+                const double vh = __dadd_rn(vel[k], __dmul_rn(acc[k], h));
+                vel[k] = vh;
+                r[d] = __dadd_rn(pos[k], __dmul_rn(vh, dt));
+                pos[k] = r[d];
+            } else {
+                r[d] = pos[k];
+            }
         }
+        D4 b;
+        b.x = r[0];
+        b.y = r[1];
+        b.z = r[2];
+        b.w = mass[i];
+        add_body(v, b.x, b.y, b.z, b.w);
+        aos[i] = b;
     }
+    block_reduce10(v, partials + kPart * blockIdx.x);
 }
 
-// Forest: one block per system reduces its bodies and writes its root box and level tables.
-__global__ void __launch_bounds__(kBoxThreads) system_box_kernel(
-    const double *__restrict__ pos, const double *__restrict__ mass, int n, Systems ss, Box *box,
-    LevelTables *tab, double theta, D4 *__restrict__ aos)
+// Forest: one block per system, its root box from its chunks' partials (chunks chunk_start[k]
+// .. chunk_start[k + 1] - 1; none for an empty system).
+__global__ void __launch_bounds__(kBoxThreads) forest_box_finalize_kernel(
+    const double *__restrict__ partials, const int *__restrict__ chunk_start, Box *box,
+    LevelTables *tab, double theta)
 {
     const int k = blockIdx.x;
     double v[kPart];
     init10(v);
-    for (int i = ss.start[k] + threadIdx.x; i < ss.start[k + 1]; i += blockDim.x) {
-        D4 b;
-        b.x = pos[i];
-        b.y = pos[(size_t)n + i];
-        b.z = pos[2 * (size_t)n + i];
-        b.w = mass[i];
-        add_body(v, b.x, b.y, b.z, b.w);
-        aos[i] = b;
+    for (int b = chunk_start[k] + threadIdx.x; b < chunk_start[k + 1]; b += blockDim.x) {
+        const double *p = partials + kPart * b;
+        for (int e = 0; e < 3; ++e) v[e] = fmin(v[e], p[e]);
+        for (int e = 3; e < 6; ++e) v[e] = fmax(v[e], p[e]);
+        for (int e = 6; e < kPart; ++e) v[e] = __dadd_rn(v[e], p[e]);
     }
     __shared__ double r[kPart];
     block_reduce10(v, r);
@@ -1088,18 +1110,17 @@ void launch_bbox_finalize(const double *partials, int nblk, Box *box, LevelTable
     count_launches(1);
 }
 
-void launch_kick_drift(double *pos, double *vel, const double *acc, int n, double h, double dt,
-                       cudaStream_t s)
+void launch_forest_boxes(double *pos, double *vel, const double *acc, const double *mass, int n,
+                         const int4 *chunks, int nchunks, const int *chunk_start, int n_sys,
+                         double h, double dt, double *partials, Box *box, LevelTables *tab,
+                         double theta, D4 *aos, cudaStream_t s)
 {
-    kick_drift_kernel<<<grid_for(n, 256, kMaxGrid), 256, 0, s>>>(pos, vel, acc, n, h, dt);
-    count_launches(1);
-}
-
-void launch_system_boxes(const double *pos, const double *mass, int n, const Systems &ss,
-                         Box *box, LevelTables *tab, double theta, D4 *aos, cudaStream_t s)
-{
-    system_box_kernel<<<ss.count, kBoxThreads, 0, s>>>(pos, mass, n, ss, box, tab, theta, aos);
-    count_launches(1);
+    if (nchunks > 0)
+        forest_box_partials_kernel<<<nchunks, kBoxThreads, 0, s>>>(pos, vel, acc, mass, n, chunks,
+                                                                   h, dt, partials, aos);
+    forest_box_finalize_kernel<<<n_sys, kBoxThreads, 0, s>>>(partials, chunk_start, box, tab,
+                                                             theta);
+    count_launches(nchunks > 0 ? 2 : 1);
 }
 
 void launch_keys(const double *pos, int n, const Box *box, const Systems &ss, uint64_t *keys,

@@ -58,6 +58,10 @@ struct nbody_ctx {
     int4 *groups = nullptr;         // walk groups: (first body, count, system, 0)
     int n_groups = 0;
     int *roots = nullptr;           // level-order root of every system
+    int4 *box_chunks = nullptr;     // (first body, end, system) chunks for the per-system boxes
+    int *box_chunk_start = nullptr; // n_sys + 1: first chunk of every system
+    int n_box_chunks = 0;
+    double *box_partials = nullptr; // partial boxes, one per chunk
     uint32_t *nn = nullptr;         // node count the forest's kernels use (device)
     // walk groups that follow the tree's cells (FP32 walks with NBODY_FLAG_CELL_GROUPS or
     // NBODY_FLAG_GROUP_MAC), rebuilt on the device with every tree
@@ -442,12 +446,16 @@ nbody_status walk(nbody_ctx *c, int n, double *acc, double *vel, double h)
 
 Systems systems(const nbody_ctx *c) { return Systems{c->sys, c->sys_start, c->n_sys}; }
 
-nbody_status forest_build(nbody_ctx *c, const double *pos, const double *mass)
+// vel non-null: a step's kick and drift (half kick h) come first, fused with the boxes.
+nbody_status forest_build(nbody_ctx *c, double *pos, const double *mass, double *vel = nullptr,
+                          double h = 0.0)
 {
     cudaStream_t s = c->stream;
     const int n = (int)c->cap;
     const Systems ss = systems(c);
-    launch_system_boxes(pos, mass, n, ss, c->box, c->tab, c->p.theta, c->aos, s);
+    launch_forest_boxes(pos, vel, c->acc, mass, n, c->box_chunks, c->n_box_chunks,
+                        c->box_chunk_start, c->n_sys, h, c->p.dt, c->box_partials, c->box, c->tab,
+                        c->p.theta, c->aos, s);
     SortScratch sc{c->keys_alt, c->ids_alt, c->hist, c->counts, sort_tiles(n), c->sys,
                    c->sys_hist};
     CKS(sort_bodies(c, pos, n, ss, sc));
@@ -479,9 +487,7 @@ nbody_status forest_step_once(nbody_ctx *c, double *pos, double *vel, const doub
 {
     const int n = (int)c->cap;
     const double h = 0.5 * c->p.dt;
-    launch_kick_drift(pos, vel, c->acc, n, h, c->p.dt, c->stream);
-    CKS(check_launch(c, "kick/drift"));
-    CKS(forest_build(c, pos, mass));
+    CKS(forest_build(c, pos, mass, vel, h));
     return walk(c, n, c->acc, vel, h);
 }
 
@@ -624,6 +630,9 @@ nbody_status nbody_destroy(nbody_ctx *c)
     dfree(c->groups);
     dfree(c->roots);
     dfree(c->nn);
+    dfree(c->box_chunks);
+    dfree(c->box_chunk_start);
+    dfree(c->box_partials);
     free_order(c);
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     if (c->gstream) cudaStreamDestroy(c->gstream);
@@ -936,7 +945,8 @@ nbody_status nbody_autotune(nbody_ctx *c, const double *d_pos, const double *d_m
     }
     const bool timing = c->timing;
     c->timing = false;
-    nbody_status st = c->n_sys ? forest_build(c, d_pos, d_mass) : build(c, d_pos, d_mass, (int)n,
+    nbody_status st = c->n_sys ? forest_build(c, const_cast<double *>(d_pos), d_mass)
+                               : build(c, d_pos, d_mass, (int)n,
                                                                         false);
     float ms[kWalkShapes] = {0.f, 0.f, 0.f};
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -1046,10 +1056,15 @@ nbody_status nbody_forest_create(nbody_ctx **out, int32_t n_systems, const int64
         std::vector<uint16_t> sys((size_t)n);
         std::vector<int> start((size_t)S + 1);
         std::vector<uint32_t> hist(2 * 256, 0u);
-        std::vector<int4> groups;
+        std::vector<int4> groups, chunks;
+        std::vector<int> chunk_start((size_t)S + 1);
         for (int k = 0; k < S; ++k) {
             const int64_t lo = h_offsets[k], hi = h_offsets[k + 1];
             start[k] = (int)lo;
+            chunk_start[k] = (int)chunks.size();
+            for (int64_t b = lo; b < hi; b += kForestBoxChunk)
+                chunks.push_back(make_int4((int)b, (int)std::min<int64_t>(b + kForestBoxChunk, hi),
+                                           k, 0));
             for (int64_t i = lo; i < hi; ++i) sys[(size_t)i] = (uint16_t)k;
             hist[k & 255] += (uint32_t)(hi - lo);
             hist[256 + ((k >> 8) & 255)] += (uint32_t)(hi - lo);
@@ -1057,7 +1072,17 @@ nbody_status nbody_forest_create(nbody_ctx **out, int32_t n_systems, const int64
                 groups.push_back(make_int4((int)b, (int)std::min<int64_t>(32, hi - b), k, 0));
         }
         start[S] = (int)n;
+        chunk_start[S] = (int)chunks.size();
         c->n_groups = (int)groups.size();
+        c->n_box_chunks = (int)chunks.size();
+        CK(dalloc(&c->box_chunks, chunks.size()));
+        CK(dalloc(&c->box_chunk_start, (size_t)S + 1));
+        CK(dalloc(&c->box_partials, (size_t)bbox_partial_doubles() * std::max<size_t>(1, chunks.size())));
+        if (!chunks.empty())
+            CK(cudaMemcpy(c->box_chunks, chunks.data(), sizeof(int4) * chunks.size(),
+                          cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(c->box_chunk_start, chunk_start.data(), sizeof(int) * (S + 1),
+                      cudaMemcpyHostToDevice));
         CK(dalloc(&c->sys, (size_t)n));
         CK(dalloc(&c->sys_start, (size_t)S + 1));
         CK(dalloc(&c->sys_hist, 2 * 256));
@@ -1100,7 +1125,7 @@ nbody_status nbody_forest_forces(nbody_ctx *c, const double *d_pos, const double
     if (c->n_sys == 0) return fail(c, NBODY_ESTATE, "not a forest context");
     if (!d_pos || !d_mass || !d_acc) return fail(c, NBODY_EINVAL, "null pointer");
     CKS(begin_timing(c));
-    CKS(forest_build(c, d_pos, d_mass));
+    CKS(forest_build(c, const_cast<double *>(d_pos), d_mass));  // positions only read
     CKS(walk(c, (int)c->cap, d_acc, nullptr, 0.0));
     return end_timing(c);
 }

@@ -105,11 +105,14 @@ void launch_kick_drift_bbox(double *pos, double *vel, const double *acc, const d
                             cudaStream_t s);
 void launch_bbox_finalize(const double *partials, int nblk, Box *box, LevelTables *tab,
                           double theta, cudaStream_t s);
-// Forest: kick + drift of all bodies, then one box (and level tables) per system.
-void launch_kick_drift(double *pos, double *vel, const double *acc, int n, double h, double dt,
-                       cudaStream_t s);
-void launch_system_boxes(const double *pos, const double *mass, int n, const Systems &ss,
-                         Box *box, LevelTables *tab, double theta, D4 *aos, cudaStream_t s);
+constexpr int kForestBoxChunk = 4096;  // forest: bodies per partial-box block
+// Forest: a step's kick and drift (vel non-null) fused with the per-system root boxes (chunks of
+// at most kForestBoxChunk bodies inside one system, partial boxes per chunk, then one block per
+// system), writing the (x, y, z, m) records.
+void launch_forest_boxes(double *pos, double *vel, const double *acc, const double *mass, int n,
+                         const int4 *chunks, int nchunks, const int *chunk_start, int n_sys,
+                         double h, double dt, double *partials, Box *box, LevelTables *tab,
+                         double theta, D4 *aos, cudaStream_t s);
 // gate (may be null): a device count; the kernel does nothing when it is 0.
 void launch_keys(const double *pos, int n, const Box *box, const Systems &ss, uint64_t *keys,
                  uint32_t *ids, cudaStream_t s, const int *gate = nullptr);
