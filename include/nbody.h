@@ -24,8 +24,9 @@
  *     The caller owns every buffer it passes and must keep it alive until the call's work on
  *     the context stream has completed; the library never frees caller memory.
  *   - All work is enqueued on the context's CUDA stream.  Entry points that must read a
- *     device-side size (the node count of the tree) synchronise that stream once per build;
- *     every other call returns without waiting.  Results in device buffers are valid once the
+ *     device-side size (the node count of the tree) synchronise that stream once per build,
+ *     and once more when the build re-sorts from the previous order (the device's choice of
+ *     path, see nbody_set_sort_mode); every other call returns without waiting.  Results in device buffers are valid once the
  *     stream has reached the call; nbody_sync() waits for it and reports device-side errors.
  *   - Errors are returned as nbody_status codes; nbody_last_error() gives a one-line message.
  *     A failed call leaves caller buffers in an unspecified state but the context usable,
@@ -130,8 +131,8 @@ nbody_status nbody_set_params(nbody_ctx *c, const nbody_params *p);
 
 /* Builds the octree of d_pos/d_mass (n bodies): root box, Morton keys, sort, node split and
  * moments (Algorithm 2, "Build Tree" and the leaves-to-root pass).  Synchronises the stream
- * once to learn the node count.  Errors: EINVAL, ENOMEM (tree larger than the device can
- * hold), ECUDA. */
+ * once to learn the node count (twice when it re-sorts from the previous build's order).
+ * Errors: EINVAL, ENOMEM (tree larger than the device can hold), ECUDA. */
 nbody_status nbody_build_tree(nbody_ctx *c, const double *d_pos, const double *d_mass,
                               int64_t n);
 
@@ -145,7 +146,8 @@ nbody_status nbody_forces(nbody_ctx *c, const double *d_pos, const double *d_mas
 /* Advances d_pos/d_vel in place by nsteps kick-drift-kick steps of the context's dt (§2.4):
  * v += a dt/2; r += v dt; a = BH(r); v += a dt/2.  The acceleration at the current positions
  * is kept in the context between calls; the first call after create, set_params or a change
- * of n computes it first.  Synchronises once per step (node count).  nsteps >= 0. */
+ * of n computes it first.  Synchronises once per step (node count), twice when the step
+ * re-sorts from the previous order.  nsteps >= 0. */
 nbody_status nbody_step(nbody_ctx *c, double *d_pos, double *d_vel, const double *d_mass,
                         int64_t n, int32_t nsteps);
 
@@ -191,8 +193,8 @@ nbody_status nbody_get_counters(nbody_ctx *c, uint32_t *h_pp, uint32_t *h_pc);
 
 /* Device time in milliseconds of the phases of the last build/force/step call (for
  * nbody_step: of its last step), measured with CUDA events recorded on the context stream:
- * [0] kick/drift + box + keys, [1] radix sort, [2] permutation + node split + moments,
- * [3] walk, [4] whole call.  Recorded only while timing is enabled with nbody_enable_timing;
+ * [0] kick/drift + box + keys (re-sort: + the extract phase), [1] sort (radix sort, or the
+ * re-sort's merge phase), [2] permutation + node split + moments, [3] walk, [4] whole call.  Recorded only while timing is enabled with nbody_enable_timing;
  * nbody_get_timings waits for the last call's final event. */
 nbody_status nbody_enable_timing(nbody_ctx *c, int32_t on);
 nbody_status nbody_get_timings(nbody_ctx *c, float *h_ms5);
@@ -277,8 +279,8 @@ nbody_status nbody_forest_forces(nbody_ctx *c, const double *d_pos, const double
 /* nsteps kick-drift-kick steps of every system (§2.4), in place on d_pos / d_vel.  The first
  * call (and the first after nbody_set_params) computes the starting accelerations.  use_graph:
  * 0 launches every kernel of every step; 1 captures one step as a CUDA graph on a stream the
- * context owns (again whenever d_pos, d_vel or d_mass differ from the captured ones, or after
- * nbody_set_params) and replays it nsteps times, ordered after the work already on the
+ * context owns (again whenever d_pos, d_vel or d_mass differ from the captured ones, after
+ * nbody_set_params, or after a change of sort mode) and replays it nsteps times, ordered after the work already on the
  * context stream, with the context stream waiting for the replays.  Timing events are not
  * recorded by replayed steps. */
 nbody_status nbody_forest_step(nbody_ctx *c, double *d_pos, double *d_vel, const double *d_mass,
