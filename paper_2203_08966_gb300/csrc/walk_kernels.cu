@@ -35,22 +35,6 @@ __device__ __forceinline__ float rsqrt_ftz(float x)
     return r;
 }
 
-// FP32 softened pair term: a += w (s - x) / (|s - x|^2 + eps^2)^(3/2), w = G m (eq. `motion`).
-// kGuard: a zero separation with zero softening contributes nothing (as in the oracle).
-template <bool kGuard>
-__device__ __forceinline__ void pair32(const float4 &s, float xi, float yi, float zi, float eps2,
-                                       float &tx, float &ty, float &tz)
-{
-    const float dx = s.x - xi, dy = s.y - yi, dz = s.z - zi;
-    const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
-    float rinv = rsqrt_ftz(r2);
-    if (kGuard) rinv = r2 > 0.f ? rinv : 0.f;
-    const float f = s.w * (rinv * rinv) * rinv;
-    tx = f * dx;
-    ty = f * dy;
-    tz = f * dz;
-}
-
 // FP64 pair term with every operation separately rounded in the order of the plain definition:
 // dx = xj - xi, r2 = ((dx dx + dy dy) + dz dz) + eps^2, 1 / sqrt(r2), (G m) (1/r)^3.
 __device__ __forceinline__ void pair64(double xj, double yj, double zj, double mj, double xi,
