@@ -452,6 +452,8 @@ def run_ours(args):
         torch.cuda.synchronize()
     launches = nb.launch_count() - l0
     sort_path, sort_removed = ctx.sort_stats()   # of the last timed step
+    # measured FP32 FMA rate of this GPU (outside the timed region): the walk's fraction of it
+    ffma_tflops = nb.measure_fp32_rate(stream)
     if sort_path == 1:
         b_keys = BYTES_KICK_EXTRACT
         b_sort = BYTES_RESORT_FIXED + BYTES_RESORT_PER_REMOVED * sort_removed / n
@@ -555,6 +557,10 @@ def run_ours(args):
                                      "dram__bytes_write.sum)",
                      "peak_source": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x "
                                     f"{peak_mhz:.0f} MHz ({peak_src} max SM clock)",
+                     "ffma_probe": {"tflops": ffma_tflops, "frac": achieved / ffma_tflops
+                                    if ffma_tflops > 0 else None,
+                                    "source": "nbody_measure_fp32_rate: independent FP32 FMA "
+                                              "chains on every SM, CUDA events"},
                      "walk_ms": walk_avg},
         "clocks": clk,
         "gpu_launches": int(launches),

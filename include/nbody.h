@@ -313,6 +313,15 @@ nbody_status nbody_sort_keys_noalloc(const double *d_pos, const double *d_mass, 
                                      uint64_t *d_keys_sorted, uint32_t *d_ids_sorted,
                                      void *cuda_stream);
 
+/* ---- measurement aid ---- */
+
+/* No counterpart in the paper: the FP32 fused multiply-add rate the current device sustains,
+ * in TFLOP/s (2 flops per FMA), from a timed kernel of independent FMA chains on every SM
+ * (about 10 ms; enqueued on cuda_stream, NULL = the legacy default stream; the call waits for
+ * it).  It is the measured counterpart of the nominal FP32 peak against which the walk's useful
+ * FP32 rate is read.  Errors: EINVAL when h_tflops is NULL; ENOMEM, ECUDA. */
+nbody_status nbody_measure_fp32_rate(void *cuda_stream, double *h_tflops);
+
 /* Copies the last error message (NUL-terminated, truncated to cap bytes). */
 nbody_status nbody_last_error(nbody_ctx *c, char *buf, int64_t cap);
 

@@ -39,7 +39,7 @@ EXPORTS = ("nbody_create", "nbody_destroy", "nbody_set_params", "nbody_build_tre
            "nbody_last_error", "nbody_get_launch_count", "nbody_sort_keys_noalloc",
            "nbody_forest_create", "nbody_forest_forces", "nbody_forest_step",
            "nbody_autotune", "nbody_set_walk_shape", "nbody_get_walk_shape",
-           "nbody_set_sort_mode", "nbody_get_sort_stats")
+           "nbody_set_sort_mode", "nbody_get_sort_stats", "nbody_measure_fp32_rate")
 
 
 class NBodyError(RuntimeError):
@@ -104,6 +104,7 @@ def load_library(path: str = LIB_PATH):
         "nbody_set_walk_shape": [vp, i32],
         "nbody_set_sort_mode": [vp, i32],
         "nbody_get_sort_stats": [vp, vp, vp],
+        "nbody_measure_fp32_rate": [vp, vp],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -395,3 +396,17 @@ def launch_count() -> int:
     if st != 0:
         raise NBodyError(st, "nbody_get_launch_count")
     return int(v.value)
+
+
+def measure_fp32_rate(stream=None) -> float:
+    """FP32 fused multiply-add rate of the current device in TFLOP/s (a measurement aid; see
+    nbody_measure_fp32_rate in include/nbody.h)."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    v = ctypes.c_double()
+    st = load_library().nbody_measure_fp32_rate(ctypes.c_void_p(stream.cuda_stream),
+                                                ctypes.byref(v))
+    if st != 0:
+        raise NBodyError(st, "nbody_measure_fp32_rate")
+    return float(v.value)

@@ -1008,6 +1008,15 @@ nbody_status nbody_get_walk_shape(nbody_ctx *c, int32_t *shape, int32_t *threads
     return NBODY_OK;
 }
 
+nbody_status nbody_measure_fp32_rate(void *cuda_stream, double *h_tflops)
+{
+    if (!h_tflops) return NBODY_EINVAL;
+    *h_tflops = 0.0;
+    const cudaError_t e = measure_fp32_rate((cudaStream_t)cuda_stream, h_tflops);
+    if (e == cudaErrorMemoryAllocation) return NBODY_ENOMEM;
+    return e == cudaSuccess ? NBODY_OK : NBODY_ECUDA;
+}
+
 nbody_status nbody_set_sort_mode(nbody_ctx *c, int32_t mode)
 {
     if (!c) return NBODY_EINVAL;

@@ -277,6 +277,11 @@ inline const int *order_full_count(const OrderScratch &o)
     return reinterpret_cast<const int *>(o.stats + kOrderFullN);
 }
 
+// ---------------------------------------------------------------- probe_kernels.cu
+// The FP32 fused multiply-add rate of the current device in TFLOP/s (a timed kernel of
+// independent FMA chains on every SM; the call waits for it).
+cudaError_t measure_fp32_rate(cudaStream_t s, double *tflops);
+
 // ---------------------------------------------------------------- walk_kernels.cu
 struct WalkArgs {
     const WalkNode *wn;

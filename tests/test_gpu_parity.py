@@ -239,3 +239,12 @@ def test_repeated_builds_reuse_context():
             ref, _, _ = oracle.bh(pos, mass, 1.0, 0.01, 0.6)
             assert np.array_equal(a, ref)
             assert np.array_equal(ctx.tree(), oracle.Tree(pos, mass).records())
+
+
+def test_fp32_rate_probe_is_plausible():
+    """The FMA-rate probe (the measured counterpart of the nominal FP32 peak) reports a rate
+    between a tenth and twice the nominal SMs x 128 lanes x 2 flop x the maximum SM clock."""
+    props = torch.cuda.get_device_properties(0)
+    rate = nb.measure_fp32_rate()
+    nominal = props.multi_processor_count * 128 * 2 * 2.1e9 / 1e12
+    assert 0.1 * nominal < rate < 2.0 * nominal, (rate, nominal)
