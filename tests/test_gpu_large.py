@@ -75,6 +75,25 @@ def test_two_plummer_16m_bench_configuration():
     print(f"two_plummer_16m FP32-Kahan rel. RMS vs oracle BH: {err:.2e}")
 
 
+def test_two_plummer_16m_resort_after_steps():
+    """Two leapfrog steps of the benchmark configuration: every build after the first re-sorts
+    from the previous build's order (§4.4); the order after the steps is the oracle's sort of the
+    new positions, key for key and index for index."""
+    w = ics.WORKLOADS["two_plummer_16m"]
+    pos, vel, mass = ics.two_plummer(w["n"], seeds=w["seeds"])
+    n = mass.shape[0]
+    tp, tv, tm = (torch.from_numpy(a).to(DEV) for a in (pos, vel, mass))
+    with nb.Context(n, 1.0, w["eps"], w["theta"], w["dt"], nb.FP32_KAHAN) as ctx:
+        ctx.step(tp, tv, tm, 2)
+        ctx.sync()
+        path, removed = ctx.sort_stats()
+        assert path == 1 and 0 < removed < n // 10
+        keys, ids = ctx.keys(n)
+    ko, io = oracle.sort_pairs(oracle.keys(tp.cpu().numpy()))
+    assert np.array_equal(keys, ko)
+    assert np.array_equal(ids.astype(np.int64), io)
+
+
 def test_disk_bulge_64m_deep_tree():
     """The deep, imbalanced stress case: exponential disk + Hernquist bulge, N = 67,108,864,
     eps = 0.001, theta = 0.5 (keys, order and tree in full; FP32-Kahan forces on sampled
