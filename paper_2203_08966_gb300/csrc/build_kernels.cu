@@ -58,15 +58,57 @@ __device__ __forceinline__ void init10(double v[kPart])
     v[6] = v[7] = v[8] = v[9] = 0.0;
 }
 
-__device__ __forceinline__ void add_body(double v[kPart], double x, double y, double z, double m)
+// Order-preserving image of a finite double as a signed 64-bit integer (and back): a body's
+// contribution to the box's min / max runs on the integer units instead of the FP64 pipe, which
+// the kick, the drift and the mass-weighted sums already keep busy.  The extremes are the same
+// values (-0 orders below +0, which changes neither the box's cube nor any key).
+__device__ __forceinline__ long long dord(double x)
 {
-    v[0] = fmin(v[0], x); v[3] = fmax(v[3], x);
-    v[1] = fmin(v[1], y); v[4] = fmax(v[4], y);
-    v[2] = fmin(v[2], z); v[5] = fmax(v[5], z);
-    v[6] = __dadd_rn(v[6], m);
-    v[7] = __fma_rn(m, x, v[7]);
-    v[8] = __fma_rn(m, y, v[8]);
-    v[9] = __fma_rn(m, z, v[9]);
+    const long long b = __double_as_longlong(x);
+    return b >= 0 ? b : (b ^ 0x7fffffffffffffffll);
+}
+
+__device__ __forceinline__ double dord_inv(long long o)
+{
+    return __longlong_as_double(o >= 0 ? o : (o ^ 0x7fffffffffffffffll));
+}
+
+// One thread's share of a box: integer images of the min and max corner, FP64 sums of m, m x,
+// m y, m z (in the thread's body order).
+struct BoxPart {
+    long long lo[3], hi[3];
+    double s[4];
+};
+
+__device__ __forceinline__ void box_init(BoxPart &p)
+{
+    for (int d = 0; d < 3; ++d) {
+        p.lo[d] = dord(DBL_MAX);
+        p.hi[d] = dord(-DBL_MAX);
+    }
+    p.s[0] = p.s[1] = p.s[2] = p.s[3] = 0.0;
+}
+
+__device__ __forceinline__ void add_body(BoxPart &p, double x, double y, double z, double m)
+{
+    const long long ox = dord(x), oy = dord(y), oz = dord(z);
+    p.lo[0] = min(p.lo[0], ox); p.hi[0] = max(p.hi[0], ox);
+    p.lo[1] = min(p.lo[1], oy); p.hi[1] = max(p.hi[1], oy);
+    p.lo[2] = min(p.lo[2], oz); p.hi[2] = max(p.hi[2], oz);
+    p.s[0] = __dadd_rn(p.s[0], m);
+    p.s[1] = __fma_rn(m, x, p.s[1]);
+    p.s[2] = __fma_rn(m, y, p.s[2]);
+    p.s[3] = __fma_rn(m, z, p.s[3]);
+}
+
+// The thread's share as the 10 partials of block_reduce10.
+__device__ __forceinline__ void box_values(const BoxPart &p, double v[kPart])
+{
+    for (int d = 0; d < 3; ++d) {
+        v[d] = dord_inv(p.lo[d]);
+        v[3 + d] = dord_inv(p.hi[d]);
+    }
+    for (int k = 0; k < 4; ++k) v[6 + k] = p.s[k];
 }
 
 // aos (may be null): the bodies as (x, y, z, m) records in the caller's order, which the
@@ -76,17 +118,19 @@ __global__ void __launch_bounds__(kBoxThreads) bbox_partials_kernel(const double
                                                                     int n, double *partials,
                                                                     D4 *__restrict__ aos)
 {
-    double v[kPart];
-    init10(v);
+    BoxPart bp;
+    box_init(bp);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         D4 b;
         b.x = pos[i];
         b.y = pos[(size_t)n + i];
         b.z = pos[2 * (size_t)n + i];
         b.w = mass[i];
-        add_body(v, b.x, b.y, b.z, b.w);
+        add_body(bp, b.x, b.y, b.z, b.w);
         if (aos) aos[i] = b;
     }
+    double v[kPart];
+    box_values(bp, v);
     block_reduce10(v, partials + kPart * blockIdx.x);
 }
 
@@ -97,8 +141,8 @@ __global__ void __launch_bounds__(kBoxThreads) kick_drift_bbox_kernel(
     const double *__restrict__ mass, int n, double h, double dt, double *partials,
     D4 *__restrict__ aos)
 {
-    double v[kPart];
-    init10(v);
+    BoxPart bp;
+    box_init(bp);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         double x[3];
 #pragma unroll
@@ -110,7 +154,7 @@ __global__ void __launch_bounds__(kBoxThreads) kick_drift_bbox_kernel(
             pos[k] = x[d];
         }
         const double m = mass[i];
-        add_body(v, x[0], x[1], x[2], m);
+        add_body(bp, x[0], x[1], x[2], m);
         D4 b;
         b.x = x[0];
         b.y = x[1];
@@ -118,6 +162,8 @@ __global__ void __launch_bounds__(kBoxThreads) kick_drift_bbox_kernel(
         b.w = m;
         aos[i] = b;
     }
+    double v[kPart];
+    box_values(bp, v);
     block_reduce10(v, partials + kPart * blockIdx.x);
 }
 
@@ -181,8 +227,8 @@ __global__ void __launch_bounds__(kBoxThreads) forest_box_partials_kernel(
     double *__restrict__ partials, D4 *__restrict__ aos)
 {
     const int4 ch = chunks[blockIdx.x];
-    double v[kPart];
-    init10(v);
+    BoxPart bp;
+    box_init(bp);
     for (int i = ch.x + threadIdx.x; i < ch.y; i += blockDim.x) {
         double r[3];
 #pragma unroll
@@ -202,9 +248,11 @@ __global__ void __launch_bounds__(kBoxThreads) forest_box_partials_kernel(
         b.y = r[1];
         b.z = r[2];
         b.w = mass[i];
-        add_body(v, b.x, b.y, b.z, b.w);
+        add_body(bp, b.x, b.y, b.z, b.w);
         aos[i] = b;
     }
+    double v[kPart];
+    box_values(bp, v);
     block_reduce10(v, partials + kPart * blockIdx.x);
 }
 
