@@ -42,13 +42,13 @@ struct Box {
 
 // Morton keys (§4.4): q = clamp(floor((x - o) * s), 0, 2^21 - 1) per axis, then the bits of
 // q_x, q_y, q_z interleaved with x most significant (a 63-bit key in one 64-bit word).
+// floor((x - o) * s) clamped to [0, 2^21 - 1], the subtraction and the product each rounded to
+// nearest.  The conversion rounds down and saturates (negative and NaN give 0, values past the
+// unsigned range its maximum), so the clamp is one integer min.
 __device__ __forceinline__ uint32_t quantise(double x, double o, double s)
 {
-    double t = __dmul_rn(__dsub_rn(x, o), s);
-    if (!(t > 0.0)) return 0u;
-    double f = floor(t);
-    if (f >= (double)kQMax) return kQMax;
-    return (uint32_t)f;
+    const double t = __dmul_rn(__dsub_rn(x, o), s);
+    return min(__double2uint_rd(t), kQMax);
 }
 
 // Spreads the low 21 bits of v so that bit b lands on bit 3b.
