@@ -817,8 +817,7 @@ __global__ void link_leaves_kernel(const uint64_t *__restrict__ keys, NodeArrays
 // Moments of the internal cells of one level, from their children (one level deeper, already
 // done): m = sum m_c, r = (sum m_c r_c) / m over the children in octant order, every product and
 // sum separately rounded.  Launched for the levels from the deepest up to the root.
-__global__ void moments_level_kernel(int level, NodeArrays na, const Box *__restrict__ box,
-                                     const LevelTables *__restrict__ tab, Systems ss, double G)
+__global__ void moments_level_kernel(int level, NodeArrays na, double G)
 {
     // the nodes of this level are level-order indices [start(level), start(level + 1)); the
     // children of each cell are a contiguous level-order run (in octant order)
@@ -841,13 +840,8 @@ __global__ void moments_level_kernel(int level, NodeArrays na, const Box *__rest
         m.y = __ddiv_rn(sy, s);
         m.z = __ddiv_rn(sz, s);
         na.com_lo[t] = m;
-        const int k = system_of(ss, ch.z);
-        const Box *bx = box + k;
         const int j = na.inv[t];
-        na.com64[j] = m;
-        na.wn[j].c = make_float4((float)(m.x - bx->c[0]), (float)(m.y - bx->c[1]),
-                                 (float)(m.z - bx->c[2]), (float)(G * m.w));
-        na.wn[j].crit = tab[k].crit32[level];
+        na.com64[j] = m;  // its FP32 copy for the walk is made by group_nodes_kernel
         if (na.q_lo) {
             // parallel-axis sum: each child's quadrupole plus its mass at its offset
             double q[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
@@ -936,25 +930,36 @@ __global__ void __launch_bounds__(kLayThreads) level_tile_rank_kernel(
 
 // GroupNode records at their level-order positions.  The first child of an internal cell is
 // the next node in pre-order; its children count is the population of the child mask.
+// The level-order copy the FP32 walk reads.  Leaves keep the FP32 (x - c, y - c, z - c, G m)
+// link_leaves wrote; a cell's is made here from its FP64 moments (off the FP64-bound moment
+// pass), with its level's FP32 acceptance threshold.
 __global__ void group_nodes_kernel(const uint32_t *__restrict__ d_nn, int64_t cap,
-                                   const WalkNode *__restrict__ wn,
+                                   const WalkNode *__restrict__ wn, const D4 *__restrict__ com64,
+                                   const uint8_t *__restrict__ level,
                                    const uint8_t *__restrict__ mask, const int *__restrict__ order,
+                                   const Box *__restrict__ box,
+                                   const LevelTables *__restrict__ tab, Systems ss, double G,
                                    GroupNode *gn)
 {
     const int n_nodes = (int)min((int64_t)*d_nn, cap);
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n_nodes; j += gridDim.x * blockDim.x) {
         const WalkNode w = wn[j];
         GroupNode g;
-        g.c = w.c;
         g.pre = j;
         if (w.count != 0) {
+            g.c = w.c;
             g.child = w.first;
             g.n = -w.count;
             g.crit = 0.f;
         } else {
+            const D4 m = com64[j];
+            const int k = system_of(ss, w.first);
+            const Box *bx = box + k;
+            g.c = make_float4((float)(m.x - bx->c[0]), (float)(m.y - bx->c[1]),
+                              (float)(m.z - bx->c[2]), (float)(G * m.w));
             g.child = j + 1 < n_nodes ? order[j + 1] : n_nodes;  // out of range: the walk refuses it
             g.n = max(1, __popc((unsigned)mask[j]));
-            g.crit = w.crit;
+            g.crit = tab[k].crit32[level[j]];
         }
         gn[order[j]] = g;
     }
@@ -1341,15 +1346,16 @@ void launch_moments(const uint64_t *keys, int max_level, const D4 *sbody64, cons
         // have (8^lev cells per system) and a grid-stride loop over the level's range
         const int64_t widest = lev < 10 ? ((int64_t)ss.count << (3 * lev)) : cap;
         const int g = grid_for(std::min<int64_t>(widest, cap), 256, kMaxGrid * 2);
-        moments_level_kernel<<<g, 256, 0, s>>>(lev, na, box, tab, ss, G);
+        moments_level_kernel<<<g, 256, 0, s>>>(lev, na, G);
     }
     count_launches(1 + max(0, depth));
 }
 
-void launch_group_nodes(const NodeArrays &na, GroupNode *gn, cudaStream_t s)
+void launch_group_nodes(const NodeArrays &na, const Box *box, const LevelTables *tab,
+                        const Systems &ss, double G, GroupNode *gn, cudaStream_t s)
 {
-    group_nodes_kernel<<<grid_for(na.cap, 256, kMaxGrid * 4), 256, 0, s>>>(na.d_nn, na.cap, na.wn,
-                                                                          na.mask, na.order, gn);
+    group_nodes_kernel<<<grid_for(na.cap, 256, kMaxGrid * 4), 256, 0, s>>>(
+        na.d_nn, na.cap, na.wn, na.com64, na.level, na.mask, na.order, box, tab, ss, G, gn);
     count_launches(1);
 }
 

@@ -381,7 +381,7 @@ nbody_status build(nbody_ctx *c, const double *pos, const double *mass, int n,
     launch_emit_nodes(c->keys, n, one, c->node_off, c->na, c->err, s);
     launch_level_order(c->na, s);
     launch_moments(c->keys, max_level, c->sbody64, c->box, c->tab, one, c->p.G, c->na, s);
-    if (group) launch_group_nodes(c->na, c->gn, s);
+    if (group) launch_group_nodes(c->na, c->box, c->tab, one, c->p.G, c->gn, s);
     if (group && cell_groups(c)) {
         CK(cudaMemsetAsync(c->cgroups_n, 0, sizeof(unsigned), s));
         launch_cell_groups(c->na, c->node_off, one, n, 32, c->cgroups, c->cgroups_n, c->cap + 1,
@@ -470,7 +470,7 @@ nbody_status forest_build(nbody_ctx *c, double *pos, const double *mass, double 
     launch_emit_nodes(c->keys, n, ss, c->node_off, c->na, c->err, s);
     launch_level_order(c->na, s);
     launch_moments(c->keys, kMaxLevel, c->sbody64, c->box, c->tab, ss, c->p.G, c->na, s);
-    if (c->p.precision != NBODY_FP64) launch_group_nodes(c->na, c->gn, s);
+    if (c->p.precision != NBODY_FP64) launch_group_nodes(c->na, c->box, c->tab, ss, c->p.G, c->gn, s);
     launch_roots(c->na, c->node_off, ss, c->roots, s);
     if (c->p.precision != NBODY_FP64 && cell_groups(c)) {
         CK(cudaMemsetAsync(c->cgroups_n, 0, sizeof(unsigned), s));

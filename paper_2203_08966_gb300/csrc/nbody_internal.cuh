@@ -212,8 +212,10 @@ constexpr int64_t kMaxGroupNodes = (int64_t)1 << 28;
 
 int layout_tiles(int64_t n_nodes);
 int layout_scan_len(int64_t n_nodes);
-// GroupNode records at their level-order positions (after the moments).
-void launch_group_nodes(const NodeArrays &na, GroupNode *gn, cudaStream_t s);
+// GroupNode records at their level-order positions (after the moments); a cell's FP32 centre of
+// mass relative to its system's origin and its level's FP32 threshold are made here.
+void launch_group_nodes(const NodeArrays &na, const Box *box, const LevelTables *tab,
+                        const Systems &ss, double G, GroupNode *gn, cudaStream_t s);
 // Walk groups that follow the tree: every cell of at most gmax bodies whose parent holds more
 // (consecutive such siblings merged while they fit in gmax), buckets of more than gmax bodies cut
 // into chunks.  (first body, count, system, 0) entries, *ngroups of them (zeroed by the caller);
