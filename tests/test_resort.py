@@ -150,3 +150,21 @@ def test_sort_mode_rejects_unknown():
         with pytest.raises(nb.NBodyError):
             ctx.set_sort_mode(3)
         assert ctx.sort_stats() == (-1, -1)
+
+
+@pytest.mark.parametrize("n", [2, 100, 2049])
+def test_resort_small_systems_steps_identical_to_full_sort(n):
+    """Forced re-sorts (every build re-sorts, whatever the size) over leapfrog steps of small
+    systems leave the same FP64 states, bit for bit, as the full sort."""
+    pos, vel, mass = ics.plummer(max(n, 2), 61)
+    pos, vel, mass = pos[:, :n].copy(), vel[:, :n].copy(), mass[:n].copy()
+    out = []
+    for mode in (nb.SORT_RESORT, nb.SORT_FULL):
+        tp, tv, tm = dev(pos), dev(vel), dev(mass)
+        with nb.Context(n, 1.0, 0.01, 0.5, 1e-3, nb.FP64) as ctx:
+            ctx.set_sort_mode(mode)
+            ctx.step(tp, tv, tm, 5)
+            ctx.sync()
+            assert ctx.sort_stats()[0] == (1 if mode == nb.SORT_RESORT else 0)
+            out.append((tp.cpu().numpy(), tv.cpu().numpy()))
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
