@@ -529,7 +529,8 @@ def run_ours(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp64": "f64", "fp32": "f32", "fp32_kahan": "f32"}[args.precision],
         "data": "synthetic",
-        "config": {"workload": f"{args.workload}", "n": n, "theta": w["theta"], "eps": w["eps"],
+        "config": {"workload": args.workload if not args.n else
+                   f"{args.workload} recipe at n = {n}", "n": n, "theta": w["theta"], "eps": w["eps"],
                    "dt": w["dt"], "precision": args.precision,
                    "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas{ws}",
                    "walk_shape": {"chosen": shape, "threads_per_block": shape_threads,
