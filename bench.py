@@ -35,7 +35,7 @@ sys.path.insert(0, ROOT)
 
 import ics  # noqa: E402
 
-METRIC = "Barnes-Hut bodies/s per step at N=16M theta=0.5"
+METRIC = "Barnes-Hut bodies/s per step at N=16M θ=0.5 (FP32 vs FP64); batch steps/s"
 FLOP_PER_INTERACTION = 20          # softened monopole pair term, counting rsqrt as 2 flops
 FP32_LANES_PER_SM = 128            # FP32 FMA lanes per SM (Blackwell)
 # Algorithmic bytes per body of the build phases (compulsory reads + writes):
@@ -77,6 +77,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 512-system forest line")
     ap.add_argument("--no-accuracy", action="store_true", help="skip the per-theta error report")
+    ap.add_argument("--no-fp64", action="store_true",
+                    help="skip the plain FP64 step on the same workload (the FP64 side of the metric)")
     ap.add_argument("--batch-only", action="store_true",
                     help="only the 512-system forest (FP32-Kahan), one JSON line with its figures")
     ap.add_argument("--batch-steps", type=int, default=100, help="graph-replayed forest steps")
@@ -479,6 +481,26 @@ def run_ours(args):
     peak_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     peak_tf = sms * FP32_LANES_PER_SM * 2 * peak_mhz * 1e6 / 1e12
 
+    # the FP64 side of the metric: one plain FP64 step of the same workload (after its starting
+    # forces and one warm-up step), CUDA events on the context stream
+    fp64 = None
+    if ws == 1 and not args.no_fp64:
+        p64, v64 = torch.from_numpy(pos).to(dev), torch.from_numpy(vel).to(dev)
+        with nb.Context(n, 1.0, w["eps"], w["theta"], w["dt"], nb.FP64, stream=stream) as c64:
+            c64.step(p64, v64, tm, 1)
+            c64.sync()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            c64.step(p64, v64, tm, 1)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms64 = e0.elapsed_time(e1)
+        del p64, v64
+        fp64 = {"value": n / (ms64 * 1e-3), "unit": "bodies/s", "ms_per_step": ms64,
+                "precision": "fp64", "steps": 1,
+                "note": "the plain FP64 path (walk, forces and accumulation in FP64) on the same "
+                        "workload; FP32-Kahan over FP64 = value / this value"}
+
     batch = None
     accuracy = None
     if ws == 1 and not args.no_batch:
@@ -567,6 +589,7 @@ def run_ours(args):
         "gpu_launches": int(launches),
         "e2e": e2e,
         "cpu_baseline": cpu,
+        "fp64": fp64,
         "batch": batch,
         "accuracy": accuracy,
     }
