@@ -87,7 +87,7 @@ def test_keys_sort_box_tree_moments_bit_exact(name):
 
 
 @pytest.mark.parametrize("name", sorted(CASES))
-@pytest.mark.parametrize("theta", [0.0, 0.5, 0.7])
+@pytest.mark.parametrize("theta", [0.0, 0.3, 0.5, 0.7, 1.0])
 def test_fp64_forces_and_counters_bit_exact(name, theta):
     pos, _, mass = CASES[name]
     n = mass.shape[0]
@@ -101,12 +101,13 @@ def test_fp64_forces_and_counters_bit_exact(name, theta):
     assert np.array_equal(a, ref)
 
 
+@pytest.mark.parametrize("theta", [0.3, 0.5, 1.0])
 @pytest.mark.parametrize("prec", [nb.FP32, nb.FP32_KAHAN])
 @pytest.mark.parametrize("name", sorted(CASES))
-def test_fp32_forces_within_tolerance(name, prec):
+def test_fp32_forces_within_tolerance(name, prec, theta):
     pos, _, mass = CASES[name]
     n = mass.shape[0]
-    theta, eps = 0.5, 0.01
+    eps = 0.01
     ref, rpp, rpc = oracle.bh(pos, mass, 1.0, eps, theta)
     with nb.Context(n, 1.0, eps, theta, 1e-3, prec) as ctx:
         a = ctx.forces(dev(pos), dev(mass)).cpu().numpy()
@@ -125,6 +126,22 @@ def test_fp32_forces_within_tolerance(name, prec):
     # FP32 acceptance tests may flip only for cells right at l/d = theta
     agree = np.mean((pp == rpp) & (pc == rpc))
     assert agree >= 0.99
+
+
+@pytest.mark.parametrize("name", ["plummer_4096", "coincident_bucket", "outlier"])
+def test_fp32_without_softening(name):
+    """eps = 0: coincident bodies (the level-21 bucket) meet at zero separation, which adds
+    nothing, as in the oracle; every other term is the unsoftened kernel."""
+    pos, _, mass = CASES[name]
+    n = mass.shape[0]
+    ref, rpp, rpc = oracle.bh(pos, mass, 1.0, 0.0, 0.5)
+    with nb.Context(n, 1.0, 0.0, 0.5, 1e-3, nb.FP32_KAHAN) as ctx:
+        a = ctx.forces(dev(pos), dev(mass)).cpu().numpy()
+        ctx.sync()
+        pp, pc = ctx.counters(n)
+    assert np.isfinite(a).all()
+    assert rel_rms(a, ref) <= FP32_TOL
+    assert np.mean((pp == rpp) & (pc == rpc)) >= 0.99
 
 
 def test_theta_zero_equals_direct_sum_on_gpu():
