@@ -16,8 +16,8 @@
 // permutation; a start far from sorted only makes the removed set large.  Every loop is
 // bounded: a tile still descending after 32 removal rounds is removed whole, and the seam repair
 // gives up after a fixed number of steps.  The choice between this and the full sort (repair gave
-// up, or too many removed) is made on the device: the kernels of the path not taken return at
-// once, and nothing waits for the host.
+// up, or too many removed) is made on the device and the kernels of the path not taken return at
+// once, so a caller may launch both paths without reading the choice back (a forest step does).
 #include "nbody_internal.cuh"
 
 namespace nb {
