@@ -22,6 +22,11 @@
  *   - Pre-order serialisation with an 8-bit child mask (§4.2).
  *   - Kick-drift-kick leapfrog, eqs. `leapkick1`, `leapdrift`, `leapkick2` (§2.4).
  *   - Energy, §2.3 (pair sum taken over i < j, softened like the force).
+ *   - Quadrupole cell terms, eq. `truncmultipole` (§2.1), softened like the monopole.
+ *   - Re-sort of last step's sorted order by insertion sort (§4.4, end: bodies move little in
+ *     one step, so the list stays almost sorted).
+ *   - Grouped acceptance test (Barnes 1990; not in the paper): one interaction list per group of
+ *     bodies, cells tested against the group's bounding box.
  *
  * Readings where the paper is silent or garbled (all mirrored in the project's design notes):
  *   root box = tight FP64 min corner, side = largest extent (1 if all bodies coincide);
