@@ -95,3 +95,27 @@ def test_group_mac_flag_rejected_for_fp64_without_gpu(lib_path):
     assert lib.nbody_create(ctypes.byref(h), 10, ctypes.byref(unknown), None) == 1
     cells64 = nb.Params(1.0, 0.01, 0.5, 1e-3, nb.FP64, nb.FLAG_CELL_GROUPS)
     assert lib.nbody_create(ctypes.byref(h), 10, ctypes.byref(cells64), None) == 1
+
+
+def test_header_is_plain_c_and_a_c_program_links(lib_path, tmp_path):
+    """The boundary is a C ABI: the header compiles as strict C99, and a C program that takes
+    the address of every entry point links against the library (nothing is run)."""
+    names = sorted(_declared())
+    src = tmp_path / "abi.c"
+    src.write_text("#include \"nbody.h\"\n"
+                   "#include <stdio.h>\n"
+                   "typedef void (*fn_t)(void);\n"
+                   "int main(void) {\n"
+                   "    fn_t fns[] = {" + ", ".join(f"(fn_t)&{n}" for n in names) + "};\n"
+                   "    nbody_params p = {1.0, 0.01, 0.5, 1e-3, NBODY_FP32_KAHAN, 0u};\n"
+                   "    printf(\"%d %d %f\\n\", (int)(sizeof fns / sizeof fns[0]), fns[0] != 0,\n"
+                   "           p.theta);\n"
+                   "    return 0;\n"
+                   "}\n")
+    inc = os.path.join(ROOT, "include")
+    libdir = os.path.dirname(lib_path)
+    r = subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic", "-I", inc,
+                        str(src), "-o", str(tmp_path / "abi"), "-L", libdir,
+                        "-l:" + os.path.basename(lib_path), "-Wl,-rpath," + libdir],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
