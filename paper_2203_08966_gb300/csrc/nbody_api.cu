@@ -68,6 +68,12 @@ struct nbody_ctx {
     int4 *cgroups = nullptr;
     unsigned *cgroups_n = nullptr;
     unsigned *work = nullptr;       // group counter of the persistent FP32 walk
+    // the shared far walk of 256-body spans (single systems, FP32 per-body walk), allocated on
+    // first use: per-span lists (span_meta, span_off, span_pool) and per-warp scratch
+    int4 *span_meta = nullptr;
+    uint32_t *span_off = nullptr, *span_pool = nullptr, *span_tmp = nullptr;
+    unsigned *span_next = nullptr;
+    int64_t span_n = 0, span_pool_cap = 0, span_tmp_warps = 0;
     float *dscratch = nullptr;      // FP32 direct sum: sources + partial sums (grown on demand)
     int64_t dscratch_cap = 0;       // floats
     // one forest step captured as a CUDA graph, replayed on its own stream
@@ -271,6 +277,48 @@ nbody_status ensure_order(nbody_ctx *c)
     return NBODY_OK;
 }
 
+void free_spans(nbody_ctx *c)
+{
+    dfree(c->span_meta);
+    dfree(c->span_off);
+    dfree(c->span_pool);
+    dfree(c->span_tmp);
+    dfree(c->span_next);
+    c->span_n = c->span_pool_cap = c->span_tmp_warps = 0;
+}
+
+// Whether the FP32 walk of this context runs the shared far walk of the spans: single systems
+// with the per-body acceptance test and monopole cells.
+bool use_spans(const nbody_ctx *c)
+{
+    return c->n_sys == 0 && c->p.precision != NBODY_FP64 &&
+           (c->p.flags & (NBODY_FLAG_GROUP_MAC | NBODY_FLAG_CELL_GROUPS | NBODY_FLAG_QUADRUPOLE)) == 0;
+}
+
+// Span scratch for n bodies (grown on demand; never inside a captured forest step).  The pool
+// holds the spans' far lists and frontiers: about 4 / theta^2 node indices per body (clamped to
+// 8 .. 48), plenty at the benchmark's theta; a span that finds no room walks from the root.
+nbody_status ensure_spans(nbody_ctx *c, int n)
+{
+    const int64_t spans = ((int64_t)n + kSpanBodies - 1) / kSpanBodies;
+    const double th = std::max(c->p.theta, 0.05);
+    const int64_t per_body = std::min<int64_t>(48, std::max<int64_t>(8, (int64_t)(4.0 / (th * th))));
+    const int64_t pool = std::max<int64_t>(1024, per_body * n);
+    const int64_t warps = span_far_warps(n);
+    if (spans <= c->span_n && pool <= c->span_pool_cap && warps <= c->span_tmp_warps)
+        return NBODY_OK;
+    free_spans(c);
+    CK(dalloc(&c->span_meta, (size_t)spans));
+    CK(dalloc(&c->span_off, (size_t)spans));
+    CK(dalloc(&c->span_pool, (size_t)pool));
+    CK(dalloc(&c->span_tmp, (size_t)warps * (kSpanFarTmp + 2 * kSpanFrTmp)));
+    CK(dalloc(&c->span_next, 2));
+    c->span_n = spans;
+    c->span_pool_cap = pool;
+    c->span_tmp_warps = warps;
+    return NBODY_OK;
+}
+
 nbody_status check_launch(nbody_ctx *c, const char *what)
 {
     cudaError_t e = cudaGetLastError();
@@ -431,6 +479,19 @@ nbody_status walk(nbody_ctx *c, int n, double *acc, double *vel, double h)
     a.group_mac = (c->p.flags & NBODY_FLAG_GROUP_MAC) != 0;
     a.q64 = c->na.q64;
     a.gq = c->p.precision != NBODY_FP64 ? c->na.gq : nullptr;
+    a.span_meta = nullptr;
+    a.span_off = a.span_pool = a.span_tmp = nullptr;
+    a.span_next = nullptr;
+    a.span_pool_cap = 0;
+    if (use_spans(c)) {
+        CKS(ensure_spans(c, n));
+        a.span_meta = c->span_meta;
+        a.span_off = c->span_off;
+        a.span_pool = c->span_pool;
+        a.span_pool_cap = c->span_pool_cap;
+        a.span_tmp = c->span_tmp;
+        a.span_next = c->span_next;
+    }
     launch_walk(c->p.precision, a, c->p.precision == NBODY_FP64 ? c->shape64 : c->shape32,
                 c->stream);
     record(c, 4);
@@ -624,6 +685,7 @@ nbody_status nbody_destroy(nbody_ctx *c)
     dfree(c->cgroups);
     dfree(c->cgroups_n);
     dfree(c->work);
+    free_spans(c);
     dfree(c->sys);
     dfree(c->sys_start);
     dfree(c->sys_hist);

@@ -313,7 +313,23 @@ struct WalkArgs {
     const float4 *gq;     // G * quadrupoles (level order) for the FP32 walk, null without them
     const unsigned *d_ngroups;  // groups built on the device: their count (n_groups = capacity)
     unsigned *work;       // FP32 walk: group counter of the persistent warps (zeroed per launch)
+    // spans of kSpanBodies consecutive bodies sharing one far walk (single systems, per-body
+    // test, monopole cells); span_meta null: every group walks from the root
+    int4 *span_meta;      // per span: far count (-1: walk from the root), frontier count, far
+                          // leaves, far cells
+    uint32_t *span_off;   // per span: offset of its far list (then its frontier) in span_pool
+    uint32_t *span_pool;  // level-order node indices
+    int64_t span_pool_cap;
+    uint32_t *span_tmp;   // per far-walk warp: kSpanFarTmp + 2 kSpanFrTmp words
+    unsigned *span_next;  // [0] pool words handed out, [1] span counter (zeroed per launch)
 };
+// Spans of the shared far walk: 8 groups of 32 bodies.  A span's far list holds at most
+// kSpanFarTmp nodes and its frontier at most kSpanFrTmp (else its groups walk from the root).
+constexpr int kSpanBodies = 256;
+constexpr int kSpanFarTmp = 8192;
+constexpr int kSpanFrTmp = 2048;
+// Far-walk warps launched (the span_tmp slices needed), for n bodies.
+int span_far_warps(int n);
 // Launch shapes of the walks (see walk_shape_threads); results do not depend on the shape.
 constexpr int kWalkShapes = 3;
 constexpr int kDefaultWalkShape = 1;

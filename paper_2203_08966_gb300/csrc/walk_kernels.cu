@@ -114,7 +114,9 @@ __device__ __forceinline__ void write_out(const WalkArgs &a, int i, double ax, d
 }
 
 // ------------------------------------------------------------------------------------------
-// FP32 group walk.  One warp owns a group of 32 Morton-consecutive bodies and walks the
+// FP32 group walk with the grouped acceptance test or quadrupole cells (the per-body test with
+// monopole cells, the default, runs the span-shared form further down, pb_walk32_kernel, built on
+// the same classification).  One warp owns a group of 32 Morton-consecutive bodies and walks the
 // level-order tree for all of them at once, 32 nodes per step (one node per lane).  Each node is
 // tested against the group's bounding box first.  Per body the acceptance test is
 // d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) > crit with dx = c.x - x in FP32 (MAC l/d < theta of
@@ -735,6 +737,567 @@ __global__ void __launch_bounds__(kWarps * 32) group_walk32_kernel(WalkArgs a)
     }
 }
 
+// ------------------------------------------------------------------------------------------
+// Per-body acceptance test, monopole cells: the default FP32 walk of a single system, in two
+// kernels.
+//
+// Neighbouring groups share most of their walks: a cell far from a span of 256 consecutive bodies
+// (eight groups) is accepted by every body of the span, and the cells above it are opened by every
+// body.  far_walk32_kernel walks the tree once per span and tests cells against the span's
+// bounding box with the bounds of the group walk (below): cells that every body of the span
+// accepts and leaves outside the span go to the span's far list, one entry for all its bodies;
+// cells that every body opens are descended; every other node (a cell that the span's bodies
+// decide differently, a leaf holding a body of the span, a bucket) goes to the span's frontier,
+// sorted deepest level first.  Each body's own walk reaches exactly these nodes, with all their
+// ancestors opened, so a group evaluates the far list as full-group entries and walks on from the
+// frontier with its own bounding box and body masks (walk_group_pb): every body keeps exactly its
+// own interaction list.  A span whose lists do not fit in the scratch is marked, and its groups
+// walk from the root.
+//
+// The group walk is arranged for few instructions per step:
+//   - a stack entry is one 8-byte pair (child range, body mask): one load per popped range;
+//   - the interaction buffers are evaluated only when the next step might not fit in them;
+//   - partial entries are kept apart by kind, leaves from the front of their buffer and cells
+//     from its back, so the per-body counts need no per-entry kind flag;
+//   - a mixed cell's per-body acceptance masks stay in registers.
+// Stack bound.  Children are pushed in reverse lane order.  Popped nodes reach the lanes in stack
+// order, so while the stack is sorted by level (deepest on top) the lane order is non-increasing
+// in level and the reversed pushes keep the stack sorted.  A step that pops a level-l node then has
+// popped every deeper entry, so after it the stack holds only the level-(l+1) ranges that this
+// step pushed (at most 32), a count that only falls until the next such step: at most 32 ranges
+// for each level 1..21.  Frontier chunks (deepest first) are taken only when the stack is empty.
+// ------------------------------------------------------------------------------------------
+
+constexpr int kPbStack = 22 * 32;  // at least 32 ranges for each level 1..21 (see above)
+constexpr int kPbF = 64;           // full-group entries
+constexpr int kPbP = 64;           // partial entries: leaves at 0.., cells at ..kPbP-1
+
+struct PbSmem {
+    uint2 st[kPbStack];   // (first node | (count - 1) << 28, bodies that still need the range)
+    float4 f[kPbF];       // full-group sources, pair-interleaved (put_entry)
+    float4 p[kPbP];       // partial sources, pair-interleaved
+    uint32_t pm[kPbP];    // their body masks
+    float4 mx[32];        // this step's mixed cells (x, y, z, crit), pair-interleaved
+};
+
+// Along one axis: the smallest |c - x| over x in [lo, hi] as the FP32 subtraction rounds it (0
+// inside; rounding is monotone, so the ends bound every body), and the largest.
+__device__ __forceinline__ void axis_bounds_pb(float c, float lo, float hi, float &dmin,
+                                               float &dmax)
+{
+    const float a = c - lo, b = c - hi;  // a >= b
+    dmin = fmaxf(fmaxf(b, -a), 0.f);
+    dmax = fmaxf(fabsf(a), fabsf(b));
+}
+
+// d^2 bounds of a cell at c from the bodies in the box [lo, hi] (the per-body expression
+// fmaf(dx, dx, fmaf(dy, dy, dz * dz)) is monotone in |dx|, |dy|, |dz|).
+__device__ __forceinline__ void box_d2(const float4 &c, float lox, float loy, float loz, float hix,
+                                       float hiy, float hiz, float &dmin2, float &dmax2)
+{
+    float nx, ny, nz, fx, fy, fz;
+    axis_bounds_pb(c.x, lox, hix, nx, fx);
+    axis_bounds_pb(c.y, loy, hiy, ny, fy);
+    axis_bounds_pb(c.z, loz, hiz, nz, fz);
+    dmin2 = fmaf(nx, nx, fmaf(ny, ny, nz * nz));
+    dmax2 = fmaf(fx, fx, fmaf(fy, fy, fz * fz));
+}
+
+// Partial entries k0 .. k1-1 (pairs): the bodies outside an entry's mask take it with weight 0.
+// Returns how many of them this lane's body takes.
+template <bool kKahan, bool kGuard>
+__device__ __forceinline__ uint32_t eval_partial(const float4 *__restrict__ p,
+                                                 const uint32_t *__restrict__ pm, int k0, int k1,
+                                                 unsigned lanebit, const float2 *nme, float2 eps2,
+                                                 Acc3x2<kKahan> &acc)
+{
+    uint32_t cnt = 0;
+    const uint2 *pm2 = reinterpret_cast<const uint2 *>(pm);
+#pragma unroll 2
+    for (int k = k0; k < k1; ++k) {
+        const float4 a = p[2 * k];
+        float4 b = p[2 * k + 1];
+        const uint2 q = pm2[k];
+        const bool on0 = (q.x & lanebit) != 0u, on1 = (q.y & lanebit) != 0u;
+        b.z = on0 ? b.z : 0.f;
+        b.w = on1 ? b.w : 0.f;
+        pair32x2<kGuard>(a, b, nme[0], nme[1], nme[2], eps2, acc.x, acc.y, acc.z);
+        cnt += (uint32_t)on0 + (uint32_t)on1;
+    }
+    return cnt;
+}
+
+template <bool kKahan, bool kGuard>
+__device__ __forceinline__ void walk_group_pb(const WalkArgs &a, PbSmem &S, int lane, int g0,
+                                              int gcount, int root)
+{
+    const int i = g0 + lane;
+    const int n_nodes = (int)*a.d_nn;
+    const unsigned lt = lanemask_lt_w();
+    const unsigned lanebit = 1u << lane;
+    const unsigned live = gcount >= 32 ? kFull : ((1u << gcount) - 1u);
+    // lanes past the group's end stand on its last body so that they do not widen its box
+    const float4 me = ldg4(a.sbody32 + g0 + min(lane, gcount - 1));
+    const float lox = warp_fmin(me.x), loy = warp_fmin(me.y), loz = warp_fmin(me.z);
+    const float hix = warp_fmax(me.x), hiy = warp_fmax(me.y), hiz = warp_fmax(me.z);
+    const float eps2s = (float)(a.eps * a.eps);
+    const float2 eps2 = make_float2(eps2s, eps2s);
+    const float2 nme[3] = {make_float2(-me.x, -me.x), make_float2(-me.y, -me.y),
+                           make_float2(-me.z, -me.z)};
+
+    Acc3x2<kKahan> acc;
+    int terms = 0;                 // terms in the current FP32 partials (warp-uniform)
+    uint32_t ufl = 0, ufc = 0;     // full-group leaves / cells (the same for every live body)
+    uint32_t npl = 0, npc = 0;     // partial leaves / cells taken by this lane's body
+    int sp = 0, fn = 0, pl = 0, pc = 0;  // stack depth and buffer fills (warp-uniform)
+
+    auto fold_if_due = [&](int added) {
+        terms += added;
+        if (terms >= Acc3x2<kKahan>::kFold) {
+            acc.fold();
+            terms = 0;
+        }
+    };
+    // evaluates and empties the buffers (odd counts padded with a zero-weight source)
+    auto drain = [&]() {
+        if (lane == 0) {
+            const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (fn & 1) put_entry(S.f, fn, z);
+            if (pl & 1) {
+                put_entry(S.p, pl, z);
+                S.pm[pl] = 0u;
+            }
+            if (pc & 1) {
+                put_entry(S.p, kPbP - 1 - pc, z);
+                S.pm[kPbP - 1 - pc] = 0u;
+            }
+        }
+        __syncwarp();
+        const int nf = (fn + 1) >> 1;
+#pragma unroll 2
+        for (int k = 0; k < nf; ++k)
+            pair32x2<kGuard>(S.f[2 * k], S.f[2 * k + 1], nme[0], nme[1], nme[2], eps2, acc.x,
+                             acc.y, acc.z);
+        fold_if_due(2 * nf);
+        const int nl = (pl + 1) >> 1;
+        npl += eval_partial<kKahan, kGuard>(S.p, S.pm, 0, nl, lanebit, nme, eps2, acc);
+        fold_if_due(2 * nl);
+        const int c0 = (kPbP - ((pc + 1) & ~1)) >> 1;
+        npc += eval_partial<kKahan, kGuard>(S.p, S.pm, c0, kPbP / 2, lanebit, nme, eps2, acc);
+        fold_if_due(kPbP - 2 * c0);
+        fn = pl = pc = 0;
+        __syncwarp();
+    };
+    // appends one entry per lane with a nonzero mask: to f when every live body takes it, else
+    // to the partial leaves or cells
+    auto emit = [&](bool leaf, const float4 &c, unsigned emask) {
+        const bool full = emask == live;
+        const bool part = emask != 0u && !full;
+        const unsigned fb = __ballot_sync(kFull, full);
+        const unsigned pb = __ballot_sync(kFull, part);
+        const unsigned lb = __ballot_sync(kFull, leaf);
+        const unsigned plb = pb & lb, pcb = pb & ~lb;
+        if (full) put_entry(S.f, fn + __popc(fb & lt), c);
+        if (part) {
+            const int o = leaf ? pl + __popc(plb & lt) : kPbP - 1 - pc - __popc(pcb & lt);
+            put_entry(S.p, o, c);
+            S.pm[o] = emask;
+        }
+        const int nf = __popc(fb), nfl = __popc(fb & lb);
+        fn += nf;
+        pl += __popc(plb);
+        pc += __popc(pcb);
+        ufl += nfl;
+        ufc += nf - nfl;
+    };
+
+    // start: the span's far list and frontier, or the root's children (the root is never
+    // tested; none when the root is a leaf, i.e. a single body)
+    int far_n = -1, fr_n = 0, fr_next = 0;
+    const uint32_t *far = nullptr;
+    if (a.span_meta && !a.groups) {
+        const int si = g0 / kSpanBodies;
+        const int4 m = a.span_meta[si];
+        if (m.x >= 0) {
+            far = a.span_pool + a.span_off[si];
+            far_n = m.x;
+            fr_n = m.y;
+            ufl = (uint32_t)m.z;
+            ufc = (uint32_t)m.w;
+        }
+    }
+    if (far) {
+        for (int base = 0; base < far_n; base += 32) {
+            const int cnt = min(32, far_n - base);
+            if (fn > kPbF - 32) drain();
+            if (lane < cnt) put_entry(S.f, fn + lane, ldg4(&a.gn[__ldg(far + base + lane)].c));
+            fn += cnt;
+        }
+    } else if (root >= 0 && root < n_nodes) {
+        const int4 r = __ldg(reinterpret_cast<const int4 *>(&a.gn[root].child));
+        if (r.y > 0) {
+            if (lane == 0) S.st[0] = make_uint2((uint32_t)r.x | ((uint32_t)(r.y - 1) << 28), live);
+            sp = 1;
+        }
+    }
+    const uint32_t *fr = far ? far + far_n : nullptr;
+
+    // every node is popped at most once per group, so more steps than nodes means a malformed
+    // tree: stop with the error word set rather than loop
+    int steps_left = n_nodes;
+    while (sp > 0 || fr_next < fr_n) {
+        if (sp > kPbStack - 32 || --steps_left < 0) {  // cannot happen (see the stack bound)
+            if (lane == 0) atomicOr(a.err, kErrStack);
+            break;
+        }
+        __syncwarp();
+        uint32_t ek, em;
+        int off, items;
+        if (sp > 0) {
+            // ---- pop up to 32 nodes from the top ranges (lane k reads the k-th from the top)
+            const int ne = min(sp, 32);
+            uint2 e = make_uint2(0u, 0u);
+            if (lane < ne) e = S.st[sp - 1 - lane];
+            const unsigned cm1 = e.x >> 28;  // range size - 1 (0..7); 0 past ne
+            // exclusive prefix sum of the range sizes: one per range before this lane's plus
+            // the sizes - 1 from their bits, one ballot per bit
+            const unsigned b0 = __ballot_sync(kFull, cm1 & 1u), b1 = __ballot_sync(kFull, cm1 & 2u);
+            const unsigned b2 = __ballot_sync(kFull, cm1 & 4u);
+            const int excl =
+                min(lane, ne) + __popc(b0 & lt) + 2 * __popc(b1 & lt) + 4 * __popc(b2 & lt);
+            const int total = ne + __popc(b0) + 2 * __popc(b1) + 4 * __popc(b2);
+            const bool touched = lane < ne && excl < 32;
+            const int nt = __popc(__ballot_sync(kFull, touched));  // ranges touched: 0 .. nt-1
+            const int end = excl + (int)cm1 + 1;
+            const bool split = __shfl_sync(kFull, end, nt - 1) > 32;  // the deepest is cut
+            const unsigned starts = __reduce_or_sync(kFull, touched ? (1u << excl) : 0u);
+            const unsigned le = starts & (lane == 31 ? kFull : ((2u << lane) - 1u));
+            const int k = __popc(le) - 1;
+            off = lane - (31 - __clz(le));
+            ek = __shfl_sync(kFull, e.x, k & 31);
+            em = __shfl_sync(kFull, e.y, k & 31);
+            __syncwarp();  // every popped entry is read before the stack is written again
+            if (split && lane == nt - 1) {  // its first (32 - excl) nodes are taken
+                const int taken = 32 - excl;
+                S.st[sp - nt] = make_uint2(((e.x & kIdxMask) + (uint32_t)taken) |
+                                               ((uint32_t)((int)cm1 - taken) << 28),
+                                           e.y);
+            }
+            sp -= nt - (split ? 1 : 0);
+            items = min(total, 32);
+        } else {
+            // ---- the next frontier chunk (deepest first), for every live body
+            items = min(32, fr_n - fr_next);
+            ek = lane < items ? __ldg(fr + fr_next + lane) : 0u;
+            em = live;
+            off = 0;
+            fr_next += items;
+        }
+
+        // ---- load the popped nodes (one per lane; idle lanes read node 0 and take nothing)
+        const int node0 = (int)(ek & kIdxMask) + off;
+        const bool has0 = lane < items;
+        const bool bad = has0 && node0 >= n_nodes;
+        if (bad) atomicOr(a.err, kErrStack);
+        const bool has = has0 && !bad;
+        const int node = has ? node0 : 0;
+        const unsigned m = has ? em : 0u;
+        const float4 c = ldg4(&a.gn[node].c);
+        const int4 meta = __ldg(reinterpret_cast<const int4 *>(&a.gn[node].child));
+
+        // ---- while the loads are in flight: evaluate the buffers if this step might not fit
+        if (fn > kPbF - 32 || pl + pc > kPbP - 34) drain();
+
+        // ---- classify
+        const bool leaf = meta.y < 0;
+        const float crit = __int_as_float(meta.z);
+        float dmin2, dmax2;
+        box_d2(c, lox, loy, loz, hix, hiy, hiz, dmin2, dmax2);
+        const bool acc_all = dmin2 > crit;    // every body of the group accepts the cell
+        const bool open_all = dmax2 <= crit;  // every body opens it
+        const unsigned d = (unsigned)(meta.x - g0);
+        const unsigned self = d < 32u ? (1u << d) : 0u;
+        unsigned emask, pmask;
+        if (leaf) {
+            emask = meta.y == -1 ? (m & ~self) : 0u;  // buckets below
+            pmask = 0u;
+        } else {
+            emask = acc_all ? m : 0u;
+            pmask = open_all ? m : 0u;
+        }
+        const bool mixed = !leaf && !acc_all && !open_all && m != 0u;
+
+        // ---- mixed cells: every body tests its own acceptance, two cells per pass
+        const unsigned mxb = __ballot_sync(kFull, mixed);
+        if (mxb) {
+            const int nm = __popc(mxb);
+            const int r = __popc(mxb & lt);
+            if (mixed) put_entry(S.mx, r, make_float4(c.x, c.y, c.z, crit));
+            __syncwarp();
+            unsigned myA = 0u;
+            for (int t = 0; t < nm; t += 2) {
+                const float4 u = S.mx[t], v = S.mx[t + 1];
+                const float2 dx = __fadd2_rn(make_float2(u.x, u.y), nme[0]);
+                const float2 dy = __fadd2_rn(make_float2(u.z, u.w), nme[1]);
+                const float2 dz = __fadd2_rn(make_float2(v.x, v.y), nme[2]);
+                const float2 q = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+                const unsigned A1 = __ballot_sync(kFull, q.x > v.z);
+                const unsigned A2 = __ballot_sync(kFull, q.y > v.w);
+                myA = r == t ? A1 : (r == t + 1 ? A2 : myA);
+            }
+            __syncwarp();  // the cells are read before the next step writes them
+            if (mixed) {
+                emask = m & myA;
+                pmask = m & ~myA;
+            }
+        }
+
+        // ---- buffer the entries, push the children (reverse lane order: deepest on top)
+        emit(leaf, c, emask);
+        {
+            const unsigned ob = __ballot_sync(kFull, pmask != 0u);
+            const int no = __popc(ob);
+            if (pmask)
+                S.st[sp + no - 1 - __popc(ob & lt)] =
+                    make_uint2((uint32_t)meta.x | ((uint32_t)(meta.y - 1) << 28), pmask);
+            sp += no;
+        }
+
+        // ---- level-21 buckets (rare): every member but the body itself, 32 members at a time
+        unsigned bk = __ballot_sync(kFull, leaf && meta.y < -1 && m != 0u);
+        while (bk) {
+            const int src = __ffs(bk) - 1;
+            bk &= bk - 1u;
+            const int b0i = __shfl_sync(kFull, meta.x, src);
+            const int nb = -__shfl_sync(kFull, meta.y, src);
+            const unsigned sm = __shfl_sync(kFull, m, src);
+            for (int base = 0; base < nb; base += 32) {
+                if (fn > kPbF - 32 || pl + pc > kPbP - 34) drain();
+                const bool h = base + lane < nb;
+                const int b = min(b0i + base + lane, b0i + nb - 1);
+                const float4 s = ldg4(a.sbody32 + b);
+                const unsigned db = (unsigned)(b - g0);
+                const unsigned mb = h ? (sm & ~(db < 32u ? (1u << db) : 0u)) : 0u;
+                emit(true, s, mb);
+            }
+        }
+    }
+    drain();
+    const float3 r = acc.result();
+    if (lane < gcount)
+        write_out(a, i, (double)r.x, (double)r.y, (double)r.z, ufl + npl, ufc + npc);
+}
+
+template <int kWarps, bool kKahan, bool kGuard>
+__global__ void __launch_bounds__(kWarps * 32) pb_walk32_kernel(WalkArgs a)
+{
+    extern __shared__ __align__(16) unsigned char pb_smem[];
+    PbSmem &S = reinterpret_cast<PbSmem *>(pb_smem)[threadIdx.x >> 5];
+    const int lane = threadIdx.x & 31;
+    // persistent warps: each takes the next group from the shared counter until none is left
+    for (;;) {
+        unsigned gi = 0;
+        if (lane == 0) gi = atomicAdd(a.work, 1u);
+        gi = __shfl_sync(kFull, gi, 0);
+        int g0, gcount, root;
+        if (!group_of(a, (int)gi, g0, gcount, root)) break;  // uniform per warp
+        walk_group_pb<kKahan, kGuard>(a, S, lane, g0, gcount, root);
+        __syncwarp();
+    }
+}
+
+// ---- the far walk of the spans (see above) ------------------------------------------------
+
+struct FarSmem {
+    uint2 st[kPbStack];   // (first node | (count - 1) << 28, level of the range's nodes)
+    uint32_t cnt[kLevels];
+};
+
+// One warp per span, persistent.  Far list and frontier go to the warp's own scratch first
+// (span_tmp: kSpanFarTmp + 2 kSpanFrTmp words per warp), then to the shared pool at an offset
+// reserved from span_next, the frontier sorted by level, deepest first (counting sort, stable).
+// A span whose lists exceed the scratch or the pool gets far count -1: its groups walk from the root.
+template <int kWarps>
+__global__ void __launch_bounds__(kWarps * 32) far_walk32_kernel(WalkArgs a)
+{
+    __shared__ FarSmem smem[kWarps];
+    FarSmem &S = smem[threadIdx.x >> 5];
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = lanemask_lt_w();
+    const size_t wg = (size_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
+    uint32_t *tfar = a.span_tmp + wg * (kSpanFarTmp + 2 * kSpanFrTmp);
+    uint32_t *tfr = tfar + kSpanFarTmp;   // frontier nodes
+    uint32_t *tlev = tfr + kSpanFrTmp;    // their levels
+    const int n_nodes = (int)*a.d_nn;
+    const int n_spans = (a.n + kSpanBodies - 1) / kSpanBodies;
+    for (;;) {
+        unsigned si = 0;
+        if (lane == 0) si = atomicAdd(a.span_next + 1, 1u);
+        si = __shfl_sync(kFull, si, 0);
+        if ((int)si >= n_spans) break;
+        const int s0 = (int)si * kSpanBodies, s1 = min(s0 + kSpanBodies, a.n);
+        float lx = INFINITY, ly = INFINITY, lz = INFINITY;
+        float hx = -INFINITY, hy = -INFINITY, hz = -INFINITY;
+        for (int b = s0 + lane; b < s1; b += 32) {
+            const float4 q = ldg4(a.sbody32 + b);
+            lx = fminf(lx, q.x);
+            ly = fminf(ly, q.y);
+            lz = fminf(lz, q.z);
+            hx = fmaxf(hx, q.x);
+            hy = fmaxf(hy, q.y);
+            hz = fmaxf(hz, q.z);
+        }
+        lx = warp_fmin(lx);
+        ly = warp_fmin(ly);
+        lz = warp_fmin(lz);
+        hx = warp_fmax(hx);
+        hy = warp_fmax(hy);
+        hz = warp_fmax(hz);
+
+        int sp = 0, fn = 0, frn = 0;
+        uint32_t nfl = 0, nfc = 0;
+        bool over = false;
+        {
+            const int4 r = __ldg(reinterpret_cast<const int4 *>(&a.gn[0].child));
+            if (r.y > 0) {
+                if (lane == 0) S.st[0] = make_uint2((uint32_t)r.x | ((uint32_t)(r.y - 1) << 28), 1u);
+                sp = 1;
+            }
+        }
+        int steps_left = n_nodes;
+        while (sp > 0) {
+            if (sp > kPbStack - 32 || --steps_left < 0) {  // cannot happen (see the stack bound)
+                if (lane == 0) atomicOr(a.err, kErrStack);
+                over = true;
+                break;
+            }
+            __syncwarp();
+            // ---- pop up to 32 nodes (as in walk_group_pb)
+            const int ne = min(sp, 32);
+            uint2 e = make_uint2(0u, 0u);
+            if (lane < ne) e = S.st[sp - 1 - lane];
+            const unsigned cm1 = e.x >> 28;
+            const unsigned b0 = __ballot_sync(kFull, cm1 & 1u), b1 = __ballot_sync(kFull, cm1 & 2u);
+            const unsigned b2 = __ballot_sync(kFull, cm1 & 4u);
+            const int excl =
+                min(lane, ne) + __popc(b0 & lt) + 2 * __popc(b1 & lt) + 4 * __popc(b2 & lt);
+            const int total = ne + __popc(b0) + 2 * __popc(b1) + 4 * __popc(b2);
+            const bool touched = lane < ne && excl < 32;
+            const int nt = __popc(__ballot_sync(kFull, touched));
+            const int end = excl + (int)cm1 + 1;
+            const bool split = __shfl_sync(kFull, end, nt - 1) > 32;
+            const unsigned starts = __reduce_or_sync(kFull, touched ? (1u << excl) : 0u);
+            const unsigned le = starts & (lane == 31 ? kFull : ((2u << lane) - 1u));
+            const int k = __popc(le) - 1;
+            const int off = lane - (31 - __clz(le));
+            const uint32_t ek = __shfl_sync(kFull, e.x, k & 31);
+            const uint32_t lev = __shfl_sync(kFull, e.y, k & 31);
+            __syncwarp();
+            if (split && lane == nt - 1) {
+                const int taken = 32 - excl;
+                S.st[sp - nt] = make_uint2(((e.x & kIdxMask) + (uint32_t)taken) |
+                                               ((uint32_t)((int)cm1 - taken) << 28),
+                                           e.y);
+            }
+            sp -= nt - (split ? 1 : 0);
+
+            const int node0 = (int)(ek & kIdxMask) + off;
+            const bool has0 = lane < min(total, 32);
+            const bool bad = has0 && node0 >= n_nodes;
+            if (bad) atomicOr(a.err, kErrStack);
+            const bool has = has0 && !bad;
+            const int node = has ? node0 : 0;
+            const float4 c = ldg4(&a.gn[node].c);
+            const int4 meta = __ldg(reinterpret_cast<const int4 *>(&a.gn[node].child));
+
+            // ---- classify against the span's box
+            const bool leaf = meta.y < 0;
+            float dmin2, dmax2;
+            box_d2(c, lx, ly, lz, hx, hy, hz, dmin2, dmax2);
+            const float crit = __int_as_float(meta.z);
+            bool to_far, to_push;
+            if (leaf) {  // a single body outside the span: every body of the span takes it
+                to_far = meta.y == -1 && (meta.x < s0 || meta.x >= s1);
+                to_push = false;
+            } else {
+                to_far = dmin2 > crit;
+                to_push = !to_far && dmax2 <= crit;
+            }
+            to_far = to_far && has;
+            to_push = to_push && has;
+            const bool to_fr = has && !to_far && !to_push;
+
+            const unsigned fb = __ballot_sync(kFull, to_far), rb = __ballot_sync(kFull, to_fr);
+            const unsigned lfb = fb & __ballot_sync(kFull, leaf);
+            if (fn + __popc(fb) > kSpanFarTmp || frn + __popc(rb) > kSpanFrTmp) {
+                over = true;
+                break;
+            }
+            if (to_far) tfar[fn + __popc(fb & lt)] = (uint32_t)node;
+            if (to_fr) {
+                const int o = frn + __popc(rb & lt);
+                tfr[o] = (uint32_t)node;
+                tlev[o] = lev;
+            }
+            fn += __popc(fb);
+            frn += __popc(rb);
+            nfl += __popc(lfb);
+            nfc += __popc(fb & ~lfb);
+            const unsigned ob = __ballot_sync(kFull, to_push);
+            const int no = __popc(ob);
+            if (to_push)
+                S.st[sp + no - 1 - __popc(ob & lt)] =
+                    make_uint2((uint32_t)meta.x | ((uint32_t)(meta.y - 1) << 28), lev + 1u);
+            sp += no;
+        }
+        // ---- reserve room in the pool and copy: far list, then the frontier by level, deepest
+        // first
+        unsigned off = 0;
+        const int tot = fn + frn;
+        if (!over && lane == 0) off = atomicAdd(a.span_next, (unsigned)tot);
+        off = __shfl_sync(kFull, off, 0);
+        if (!over && (int64_t)off + tot > a.span_pool_cap) over = true;
+        if (over) {
+            if (lane == 0) a.span_meta[si] = make_int4(-1, 0, 0, 0);
+            continue;
+        }
+        uint32_t *dst = a.span_pool + off;
+        for (int q = lane; q < fn; q += 32) dst[q] = tfar[q];
+        if (lane < kLevels) S.cnt[lane] = 0u;
+        __syncwarp();
+        for (int base = 0; base < frn; base += 32) {
+            const int q = base + lane;
+            const uint32_t lv = q < frn ? tlev[q] : 0xffu;
+            const unsigned peers = __match_any_sync(kFull, lv);
+            if (q < frn && lane == __ffs(peers) - 1) S.cnt[lv] += __popc(peers);
+            __syncwarp();
+        }
+        if (lane == 0) {
+            uint32_t run = 0;
+            for (int lv = kLevels - 1; lv >= 0; --lv) {
+                const uint32_t cn = S.cnt[lv];
+                S.cnt[lv] = run;
+                run += cn;
+            }
+        }
+        __syncwarp();
+        for (int base = 0; base < frn; base += 32) {
+            const int q = base + lane;
+            const bool valid = q < frn;
+            const uint32_t lv = valid ? tlev[q] : 0xffu;
+            const unsigned peers = __match_any_sync(kFull, lv);
+            if (valid) dst[fn + S.cnt[lv] + __popc(peers & lt)] = tfr[q];
+            __syncwarp();
+            if (valid && lane == __ffs(peers) - 1) S.cnt[lv] += __popc(peers);
+            __syncwarp();
+        }
+        if (lane == 0) {
+            a.span_off[si] = off;
+            a.span_meta[si] = make_int4(fn, frn, (int)nfl, (int)nfc);
+        }
+    }
+}
+
 // FP64 walk, operation for operation the plain per-particle definition: the MAC is
 // l^2 < theta^2 d^2 with l^2 of the cell's level and d the distance to its FP64 centre of mass.
 template <int kThreads>
@@ -952,15 +1515,44 @@ void launch_group_variant(const WalkArgs &a, int64_t groups, cudaStream_t s)
 }
 
 template <int kWarps, bool kKahan, bool kGuard>
+int pb_persistent_blocks(int64_t groups)
+{
+    static int resident = 0;  // per kernel instance, per process
+    if (resident == 0) {
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &per_sm, pb_walk32_kernel<kWarps, kKahan, kGuard>, kWarps * 32,
+            sizeof(PbSmem) * kWarps);
+        resident = std::max(1, sms) * std::max(1, per_sm);
+    }
+    return (int)std::min<int64_t>((groups + kWarps - 1) / kWarps, resident);
+}
+
+constexpr int kFarWarps = 4;       // warps per block of the far walk
+constexpr int kFarBlocksPerSm = 4;
+
+template <int kWarps, bool kKahan, bool kGuard>
 void launch_group(const WalkArgs &a, int64_t groups, cudaStream_t s)
 {
     const bool quad = a.gq != nullptr;
+    if (!a.group_mac && !quad) {
+        if (a.span_meta && !a.groups) {
+            cudaMemsetAsync(a.span_next, 0, 2 * sizeof(unsigned), s);
+            far_walk32_kernel<kFarWarps><<<span_far_warps(a.n) / kFarWarps, kFarWarps * 32, 0, s>>>(a);
+            count_launches(1);
+        }
+        const int blocks = pb_persistent_blocks<kWarps, kKahan, kGuard>(groups);
+        pb_walk32_kernel<kWarps, kKahan, kGuard>
+            <<<blocks, kWarps * 32, sizeof(PbSmem) * kWarps, s>>>(a);
+        return;
+    }
     if (a.group_mac) {
         if (quad) launch_group_variant<kWarps, kKahan, kGuard, true, true>(a, groups, s);
         else launch_group_variant<kWarps, kKahan, kGuard, true, false>(a, groups, s);
     } else {
-        if (quad) launch_group_variant<kWarps, kKahan, kGuard, false, true>(a, groups, s);
-        else launch_group_variant<kWarps, kKahan, kGuard, false, false>(a, groups, s);
+        launch_group_variant<kWarps, kKahan, kGuard, false, true>(a, groups, s);
     }
 }
 
@@ -979,20 +1571,21 @@ void launch_group(const WalkArgs &a, int64_t groups, bool kahan, bool guard, cud
 template <int kWarps, bool kKahan, bool kGuard>
 cudaError_t allow_group_smem_kg()
 {
-    const void *fns[4] = {(const void *)group_walk32_kernel<kWarps, kKahan, kGuard, false, false>,
-                          (const void *)group_walk32_kernel<kWarps, kKahan, kGuard, true, false>,
+    // the per-body test with monopole cells runs pb_walk32_kernel
+    const void *fns[3] = {(const void *)group_walk32_kernel<kWarps, kKahan, kGuard, true, false>,
                           (const void *)group_walk32_kernel<kWarps, kKahan, kGuard, false, true>,
                           (const void *)group_walk32_kernel<kWarps, kKahan, kGuard, true, true>};
-    const int bytes[4] = {(int)(group_smem_bytes<false>() * kWarps),
-                          (int)(group_smem_bytes<false>() * kWarps),
+    const int bytes[3] = {(int)(group_smem_bytes<false>() * kWarps),
                           (int)(group_smem_bytes<true>() * kWarps),
                           (int)(group_smem_bytes<true>() * kWarps)};
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < 3; ++k) {
         const cudaError_t e =
             cudaFuncSetAttribute(fns[k], cudaFuncAttributeMaxDynamicSharedMemorySize, bytes[k]);
         if (e != cudaSuccess) return e;
     }
-    return cudaSuccess;
+    return cudaFuncSetAttribute((const void *)pb_walk32_kernel<kWarps, kKahan, kGuard>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(sizeof(PbSmem) * kWarps));
 }
 
 template <int kWarps>
@@ -1015,6 +1608,20 @@ void launch_w64(const WalkArgs &a, int64_t groups, cudaStream_t s)
 
 }  // namespace
 
+int span_far_warps(int n)
+{
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        sms = std::max(1, sms);
+    }
+    const int spans = (n + kSpanBodies - 1) / kSpanBodies;
+    const int blocks = std::max(1, std::min((spans + kFarWarps - 1) / kFarWarps, sms * kFarBlocksPerSm));
+    return blocks * kFarWarps;
+}
+
 cudaError_t walk_prepare()
 {
     cudaError_t e = allow_group_smem<2>();
@@ -1034,7 +1641,9 @@ int walk_shape_threads(int precision, int shape)
 void launch_walk(int precision, const WalkArgs &a, int shape, cudaStream_t s)
 {
     if (a.n <= 0) return;
-    const bool guard = !(a.eps > 0.0);
+    // FP32 walks: zero separations (a body and its own bucket, or eps^2 that rounds to zero in
+    // FP32) are guarded
+    const bool guard = !((float)(a.eps * a.eps) > 0.f);
     const int64_t groups = a.groups ? (int64_t)a.n_groups : ((int64_t)a.n + 31) / 32;
     if (groups <= 0) return;
     if (shape < 0 || shape >= kWalkShapes) shape = kDefaultWalkShape;
