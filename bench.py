@@ -303,7 +303,9 @@ def measure_accuracy(nb, torch, dev, stream, n_targets=16384):
                 "p99": float(np.sqrt(np.quantile(num / den, 0.99)))}
 
     direct_rate = {}
-    for name, prec in (("fp64", nb.FP64), ("fp32", nb.FP32)):
+    fp64_peak = nb.measure_fp64_rate(stream)
+    fp32_peak = nb.measure_fp32_rate(stream)
+    for name, prec in (("fp64", nb.FP64), ("fp64_fast", nb.FP64_FAST), ("fp32", nb.FP32)):
         with nb.Context(n, 1.0, w["eps"], 0.5, w["dt"], prec, stream=stream) as ctx:
             a = ctx.direct_forces(tp, tm, tt)   # warm-up
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -313,8 +315,10 @@ def measure_accuracy(nb, torch, dev, stream, n_targets=16384):
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1)
             pairs = float(n_targets) * (n - 1)
-            direct_rate[name] = {"ms": ms, "pairs": pairs,
-                                 "tflops": pairs * FLOP_PER_INTERACTION / (ms * 1e-3) / 1e12}
+            tf = pairs * FLOP_PER_INTERACTION / (ms * 1e-3) / 1e12
+            peak = fp32_peak if name == "fp32" else fp64_peak
+            direct_rate[name] = {"ms": ms, "pairs": pairs, "tflops": tf,
+                                 "frac_of_fma_probe": tf / peak if peak > 0 else None}
             if name == "fp64":
                 direct = a.cpu().numpy()
     out = {"workload": "plummer_1m", "n": n, "eps": w["eps"], "targets": n_targets,
@@ -323,7 +327,8 @@ def measure_accuracy(nb, torch, dev, stream, n_targets=16384):
     for theta in (0.3, 0.5, 0.7):
         row = {}
         res = {}
-        for name, prec, flags in (("fp64", nb.FP64, 0), ("fp32_kahan", nb.FP32_KAHAN, 0),
+        for name, prec, flags in (("fp64", nb.FP64, 0), ("fp64_fast", nb.FP64_FAST, 0),
+                                  ("fp32", nb.FP32, 0), ("fp32_kahan", nb.FP32_KAHAN, 0),
                                   ("fp32_kahan_group_mac", nb.FP32_KAHAN, nb.FLAG_GROUP_MAC),
                                   ("fp32_kahan_quadrupole", nb.FP32_KAHAN, nb.FLAG_QUADRUPOLE)):
             with nb.Context(n, 1.0, w["eps"], theta, w["dt"], prec, stream=stream,
@@ -339,7 +344,37 @@ def measure_accuracy(nb, torch, dev, stream, n_targets=16384):
                          "interactions_per_body": float((pp.astype(np.float64).sum() +
                                                          pc.astype(np.float64).sum()) / n)}
         row["fp32_kahan_vs_fp64_bh"] = rel(res["fp32_kahan"], res["fp64"])
+        row["fp32_vs_fp64_bh"] = rel(res["fp32"], res["fp64"])
+        row["fp64_fast_vs_fp64_bh"] = rel(res["fp64_fast"], res["fp64"])
         out["theta"][str(theta)] = row
+    out["energy"] = measure_energy_drift(nb, torch, dev, stream)
+    return out
+
+
+def measure_energy_drift(nb, torch, dev, stream):
+    """Relative energy drift |E_10 - E_0| / |E_0| and momentum change of 10 KDK steps on the
+    4096-body Plummer configuration (eps 0.01, theta 0.5, dt 1e-3), energies of the GPU states
+    computed by the oracle (§2.3), beside the oracle's own Barnes-Hut run."""
+    import oracle
+    oracle.build()
+    w = ics.WORKLOADS["plummer_4k"]
+    pos, vel, mass = ics.plummer(w["n"], w["seed"])
+    e0 = oracle.energy(pos, vel, mass, 1.0, w["eps"])[2]
+    p0 = oracle.momentum(vel, mass)
+    acc0, _, _ = oracle.bh(pos, mass, 1.0, w["eps"], w["theta"])
+    rp, rv, _ = oracle.kdk(pos, vel, mass, acc0, 1.0, w["eps"], w["theta"], w["dt"], w["steps"])
+    out = {"workload": "plummer_4k", "steps": w["steps"], "dt": w["dt"],
+           "oracle_bh": {"drift": (oracle.energy(rp, rv, mass, 1.0, w["eps"])[2] - e0) / abs(e0),
+                         "dP": float(np.linalg.norm(oracle.momentum(rv, mass) - p0))}}
+    for name, prec in (("fp64", nb.FP64), ("fp64_fast", nb.FP64_FAST), ("fp32", nb.FP32),
+                       ("fp32_kahan", nb.FP32_KAHAN)):
+        tp, tv = torch.from_numpy(pos).to(dev), torch.from_numpy(vel).to(dev)
+        with nb.Context(w["n"], 1.0, w["eps"], w["theta"], w["dt"], prec, stream=stream) as ctx:
+            ctx.step(tp, tv, torch.from_numpy(mass).to(dev), w["steps"])
+            ctx.sync()
+        p, v = tp.cpu().numpy(), tv.cpu().numpy()
+        out[name] = {"drift": (oracle.energy(p, v, mass, 1.0, w["eps"])[2] - e0) / abs(e0),
+                     "dP": float(np.linalg.norm(oracle.momentum(v, mass) - p0))}
     return out
 
 
@@ -481,25 +516,42 @@ def run_ours(args):
     peak_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     peak_tf = sms * FP32_LANES_PER_SM * 2 * peak_mhz * 1e6 / 1e12
 
-    # the FP64 side of the metric: one plain FP64 step of the same workload (after its starting
-    # forces and one warm-up step), CUDA events on the context stream
+    # the FP64 side of the metric: one step of each FP64 form on the same workload (after its
+    # starting forces and one warm-up step), CUDA events on the context stream, with the walk's
+    # useful FP64 rate against the measured FP64 FMA rate
     fp64 = None
     if ws == 1 and not args.no_fp64:
-        p64, v64 = torch.from_numpy(pos).to(dev), torch.from_numpy(vel).to(dev)
-        with nb.Context(n, 1.0, w["eps"], w["theta"], w["dt"], nb.FP64, stream=stream) as c64:
-            c64.step(p64, v64, tm, 1)
-            c64.sync()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            c64.step(p64, v64, tm, 1)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            ms64 = e0.elapsed_time(e1)
-        del p64, v64
-        fp64 = {"value": n / (ms64 * 1e-3), "unit": "bodies/s", "ms_per_step": ms64,
-                "precision": "fp64", "steps": 1,
-                "note": "the plain FP64 path (walk, forces and accumulation in FP64) on the same "
-                        "workload; FP32-Kahan over FP64 = value / this value"}
+        fp64_peak = nb.measure_fp64_rate(stream)
+        fp64 = {"fp64_fma_probe_tflops": fp64_peak,
+                "fp64_peak_source": "nbody_measure_fp64_rate: independent FP64 FMA chains on "
+                                    "every SM, CUDA events"}
+        for name, prec in (("fp64", nb.FP64), ("fp64_fast", nb.FP64_FAST)):
+            p64, v64 = torch.from_numpy(pos).to(dev), torch.from_numpy(vel).to(dev)
+            with nb.Context(n, 1.0, w["eps"], w["theta"], w["dt"], prec, stream=stream) as c64:
+                c64.step(p64, v64, tm, 1)
+                c64.sync()
+                c64.enable_timing(True)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                c64.step(p64, v64, tm, 1)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms64 = e0.elapsed_time(e1)
+                wms = float(c64.timings()[3])
+                pp64, pc64 = c64.counters(n)
+            del p64, v64
+            i64 = float(pp64.astype(np.float64).sum() + pc64.astype(np.float64).sum())
+            ach = i64 * FLOP_PER_INTERACTION / (wms * 1e-3) / 1e12
+            fp64[name] = {"value": n / (ms64 * 1e-3), "unit": "bodies/s", "ms_per_step": ms64,
+                          "walk_ms": wms, "interactions": i64,
+                          "roofline": {"bound": "alu", "achieved": ach, "peak": fp64_peak,
+                                       "unit": "TFLOP/s", "frac": ach / fp64_peak if
+                                       fp64_peak > 0 else None}}
+        fp64["note"] = ("fp64: the bit-exact FP64 path (every pair term separately rounded, "
+                        "correctly rounded square root and division, the oracle's order); "
+                        "fp64_fast: the same FP64 acceptance test and interaction lists, pair "
+                        "terms with fused multiply-adds and one rsqrt.  FP32-Kahan over FP64 = "
+                        "value / fp64_fast.value (the faster FP64 form)")
 
     batch = None
     accuracy = None

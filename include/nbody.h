@@ -51,7 +51,7 @@ typedef enum {
     NBODY_EINVAL = 1,    /* bad argument (null pointer, size, parameter) */
     NBODY_ENOMEM = 2,    /* device or host allocation failed */
     NBODY_ECUDA = 3,     /* a CUDA runtime call or kernel launch failed */
-    NBODY_ESTACK = 4,    /* a traversal overran its node stack (reported by nbody_sync) */
+    NBODY_ESTACK = 4,    /* a walk ran out of stack entries or steps (reported by nbody_sync) */
     NBODY_ETIMEOUT = 5,  /* a bounded device-side wait gave up */
     NBODY_ESTATE = 6     /* call out of order (e.g. introspection before any build) */
 } nbody_status;
@@ -59,7 +59,12 @@ typedef enum {
 typedef enum {
     NBODY_FP64 = 0,        /* pair interactions, walk and accumulation in FP64 */
     NBODY_FP32 = 1,        /* FP32 pair interactions, MAC and accumulation */
-    NBODY_FP32_KAHAN = 2   /* FP32 pair interactions with compensated (Kahan) accumulation */
+    NBODY_FP32_KAHAN = 2,  /* FP32 pair interactions with compensated (Kahan) accumulation */
+    NBODY_FP64_FAST = 3    /* FP64 with the FP64 acceptance test of NBODY_FP64 (the same
+                            * interaction lists and counters) but each pair term evaluated with
+                            * fused multiply-adds and one reciprocal square root (rsqrt) instead
+                            * of separately rounded operations, a square root and a division:
+                            * results differ from NBODY_FP64 by rounding */
     /* FP64 sums each body's terms in the order of its own recursive walk.  The FP32 forms give
      * every body the interaction list that the per-body FP32 acceptance test decides, but
      * evaluate the walk for 32 Morton-consecutive bodies at a time and sum the terms in another
@@ -69,7 +74,8 @@ typedef enum {
 /* Physical and numerical parameters.  G: gravitational constant; eps: Plummer softening length
  * (§2.1); theta: opening angle of the acceptance test l/d < theta (§3); dt: leapfrog time step
  * (§2.4); precision: nbody_precision; flags: a combination of NBODY_FLAG_GROUP_MAC and
- * NBODY_FLAG_CELL_GROUPS (FP32 forms only) and NBODY_FLAG_QUADRUPOLE, or 0. */
+ * NBODY_FLAG_CELL_GROUPS (FP32 forms only), NBODY_FLAG_QUADRUPOLE and NBODY_FLAG_CHECK_FINITE,
+ * or 0. */
 /* Flag: the grouped acceptance test of Barnes (1990) instead of the paper's per-body test
  * (FP32 forms only; EINVAL with NBODY_FP64).  Bodies are taken in Morton order in groups of 32;
  * a cell is accepted for all bodies of a group when l/d_min < theta, d_min being the distance
@@ -86,7 +92,7 @@ typedef enum {
  * need compact groups. */
 #define NBODY_FLAG_CELL_GROUPS 2u
 
-/* Flag: accepted cells add their quadrupole term (§2.1, the truncated multipole expansion about
+/* Flag: accepted cells add their quadrupole term (§2.2, the truncated multipole expansion about
  * the cell's centre of mass, where the dipole vanishes), softened like the monopole: with
  * d = r_J - r_i and r_s^2 = |d|^2 + eps^2,
  *   a_i += G (M d / r_s^3 - Q d / r_s^5 + 5/2 (d.Q.d) d / r_s^7),
@@ -95,6 +101,13 @@ typedef enum {
  * Quadrupoles are built bottom-up (parallel-axis sums), so the FP64 path matches a body-by-body
  * evaluation to rounding rather than bit for bit. */
 #define NBODY_FLAG_QUADRUPOLE 4u
+
+/* Flag: every build first checks that all positions and masses are finite (one extra pass over
+ * them).  A single-system call that finds a NaN or an infinity returns NBODY_EINVAL before the
+ * node split and the walk; a forest step, which never waits on the host, reports it at the next
+ * nbody_sync.  Without the flag non-finite inputs are a precondition violation: the library
+ * still keeps every access in bounds, but the results are undefined. */
+#define NBODY_FLAG_CHECK_FINITE 8u
 
 typedef struct {
     double G;
@@ -168,7 +181,12 @@ nbody_status nbody_step_host(nbody_ctx *c, double *h_pos, double *h_vel, double 
 nbody_status nbody_direct_forces(nbody_ctx *c, const double *d_pos, const double *d_mass,
                                  int64_t n, const int64_t *d_targets, int64_t nt, double *d_acc);
 
-/* Waits for the context stream and reports any device-side error flag. */
+/* Waits for the context stream and reports the device-side error word set since the last
+ * report: EINVAL (NBODY_FLAG_CHECK_FINITE found a NaN or infinite input in a forest step),
+ * ENOMEM (a forest's trees outgrew the node arrays), ESTACK (a walk ran out of stack entries or
+ * steps: a malformed tree, or limits lowered by nbody_set_walk_limits).  The word is cleared once
+ * reported; the context stays usable, and the next nbody_step recomputes its starting
+ * acceleration. */
 nbody_status nbody_sync(nbody_ctx *c);
 
 /* ---- introspection (copies to caller-provided HOST buffers; synchronous) ---- */
@@ -226,6 +244,16 @@ nbody_status nbody_set_walk_shape(nbody_ctx *c, int32_t shape);
 
 /* The walk shape in use for the context's precision and its threads per block. */
 nbody_status nbody_get_walk_shape(nbody_ctx *c, int32_t *shape, int32_t *threads_per_block);
+
+/* Test aid with no counterpart in the paper: lowers the walk's resources so that its guards can
+ * be exercised.  stack_entries: stack ranges an FP32 group walk may hold (at least 33; the
+ * kernels' own capacity when larger; 0 = that capacity); max_steps: steps one group, span or FP64
+ * warp may take (0 = no limit beyond the node count).  A walk that reaches either limit stops
+ * before any further memory access, its bodies' forces are left incomplete, and the next
+ * nbody_sync returns NBODY_ESTACK.  With the defaults, no valid tree reaches them (the stack
+ * holds at most 32 ranges per level, a walk at most one step per node).
+ * Errors: EINVAL (stack_entries in 1..32, max_steps < 0). */
+nbody_status nbody_set_walk_limits(nbody_ctx *c, int32_t stack_entries, int64_t max_steps);
 
 /* ---- re-sort from the previous step's order (temporal coherence, §4.4) ---- */
 
@@ -292,8 +320,8 @@ nbody_status nbody_forest_step(nbody_ctx *c, double *d_pos, double *d_vel, const
 #define NBODY_NOALLOC_MAX_N 262144
 
 /* The paper has no counterpart to this entry point: it exists for callers that cannot call
- * cudaMalloc -- code running while a CUDA graph is being captured, runtimes that own a fixed
- * device-memory budget or forbid allocation after start-up.  It computes what nbody_build_tree
+ * cudaMalloc -- runtimes that own a fixed device-memory budget, real-time loops that must not
+ * block in the allocator, hosts that forbid allocation after start-up.  It computes what nbody_build_tree
  * followed by nbody_get_keys returns (root box, Morton keys, stable sort by key then id) without
  * a context and without allocating: its working memory is one file-scope device array of about
  * 3.2 MB, which every GPU that loads the library holds until the process exits.
@@ -303,9 +331,11 @@ nbody_status nbody_forest_step(nbody_ctx *c, double *d_pos, double *d_vel, const
  *   index of every sorted body.
  *   cuda_stream: a cudaStream_t (NULL = the legacy default stream); the call is asynchronous.
  * Errors: NBODY_EINVAL when n < 0, n > NBODY_NOALLOC_MAX_N or a pointer is NULL (n == 0 is a
- * no-op); NBODY_ECUDA when a CUDA call fails.
- * The first call on each device looks up the array's device address (cudaGetSymbolAddress) and
- * sets a kernel attribute, so make that first call before any stream capture.  Every call on a
+ * no-op); NBODY_ECUDA when a CUDA call fails, including a CUDA error that earlier work left
+ * pending on the calling thread (the call reads and clears the thread's last error).
+ * Every call looks up the array's device address (cudaGetSymbolAddress, which enqueues nothing);
+ * the first call on each device, and the first after a device reset, also sets a kernel
+ * attribute, so make that first call before any stream capture.  Every call on a
  * device shares the one array and leaves its last contents there: calls whose work overlaps on
  * the GPU (different streams, or host threads without ordering) race and must be serialised by
  * the caller. */
@@ -321,6 +351,11 @@ nbody_status nbody_sort_keys_noalloc(const double *d_pos, const double *d_mass, 
  * it).  It is the measured counterpart of the nominal FP32 peak against which the walk's useful
  * FP32 rate is read.  Errors: EINVAL when h_tflops is NULL; ENOMEM, ECUDA. */
 nbody_status nbody_measure_fp32_rate(void *cuda_stream, double *h_tflops);
+
+/* No counterpart in the paper: the FP64 fused multiply-add rate of the current device in
+ * TFLOP/s (2 flops per FMA), measured like nbody_measure_fp32_rate; the denominator of the FP64
+ * walk's and direct sum's useful rates.  Errors: EINVAL when h_tflops is NULL; ENOMEM, ECUDA. */
+nbody_status nbody_measure_fp64_rate(void *cuda_stream, double *h_tflops);
 
 /* Copies the last error message (NUL-terminated, truncated to cap bytes). */
 nbody_status nbody_last_error(nbody_ctx *c, char *buf, int64_t cap);

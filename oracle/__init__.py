@@ -252,7 +252,7 @@ class Tree:
 
     def quads(self):
         """Quadrupole moments of every node in the order of records(): (n_nodes, 6) as
-        (xx, yy, zz, xy, xz, yz) about each node's centre of mass (§2.1)."""
+        (xx, yy, zz, xy, xz, yz) about each node's centre of mass (§2.2)."""
         nn = self.stats()["nodes"]
         out = np.zeros((max(nn, 1), 6))
         k = _load().orc_tree_quads(self._h, out)
@@ -260,7 +260,7 @@ class Tree:
 
     def forces(self, G=1.0, eps=0.0, theta=0.5, targets=None, quadrupole=False):
         """Barnes-Hut accelerations (3, nt) and counters pp, pc (nt,) uint32.  quadrupole: accepted
-        cells add their quadrupole term (§2.1, softened like the monopole)."""
+        cells add their quadrupole term (§2.2, softened like the monopole)."""
         if targets is None:
             nt = self.n
             tp = None

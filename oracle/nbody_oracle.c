@@ -22,7 +22,7 @@
  *   - Pre-order serialisation with an 8-bit child mask (§4.2).
  *   - Kick-drift-kick leapfrog, eqs. `leapkick1`, `leapdrift`, `leapkick2` (§2.4).
  *   - Energy, §2.3 (pair sum taken over i < j, softened like the force).
- *   - Quadrupole cell terms, eq. `truncmultipole` (§2.1), softened like the monopole.
+ *   - Quadrupole cell terms, eq. `truncmultipole` (§2.2), softened like the monopole.
  *   - Re-sort of last step's sorted order by insertion sort (§4.4, end: bodies move little in
  *     one step, so the list stays almost sorted).
  *   - Grouped acceptance test (Barnes 1990; not in the paper): one interaction list per group of
@@ -471,7 +471,7 @@ int64_t orc_tree_moments(void *h, double *out)
 }
 
 /* ------------------------------------------------------------------ */
-/* Quadrupole moments (§2.1, eq. `truncmultipole` and the coefficients below it): about the     */
+/* Quadrupole moments (§2.2, eq. `truncmultipole` and the coefficients below it): about the     */
 /* cell's centre of mass, where the dipole vanishes,                                            */
 /*   Q_aa = sum_j m_j (3 x_a,j^2 - r_j^2),   Q_ab = sum_j m_j 3 x_a,j x_b,j  (a != b),          */
 /* x_j = r_j - r_J.  Computed here from that definition, body by body, for every cell.          */

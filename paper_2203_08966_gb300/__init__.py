@@ -19,12 +19,13 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libnbody.so")
 
-FP64, FP32, FP32_KAHAN = 0, 1, 2
+FP64, FP32, FP32_KAHAN, FP64_FAST = 0, 1, 2, 3
 WALK_SHAPES = 3  # NBODY_WALK_SHAPES
 FLAG_GROUP_MAC = 1  # NBODY_FLAG_GROUP_MAC: grouped acceptance test (Barnes 1990), FP32 forms
 FLAG_CELL_GROUPS = 2  # NBODY_FLAG_CELL_GROUPS: FP32 walk groups follow the tree's cells
 FLAG_QUADRUPOLE = 4  # NBODY_FLAG_QUADRUPOLE: accepted cells add their quadrupole term
-PRECISIONS = {"fp64": FP64, "fp32": FP32, "fp32_kahan": FP32_KAHAN}
+FLAG_CHECK_FINITE = 8  # NBODY_FLAG_CHECK_FINITE: reject NaN / infinite positions and masses
+PRECISIONS = {"fp64": FP64, "fp32": FP32, "fp32_kahan": FP32_KAHAN, "fp64_fast": FP64_FAST}
 # NBODY_SORT_*: how a build sorts (same order in every mode; re-sort from the previous order, §4.4)
 SORT_AUTO, SORT_FULL, SORT_RESORT = 0, 1, 2
 
@@ -39,7 +40,9 @@ EXPORTS = ("nbody_create", "nbody_destroy", "nbody_set_params", "nbody_build_tre
            "nbody_last_error", "nbody_get_launch_count", "nbody_sort_keys_noalloc",
            "nbody_forest_create", "nbody_forest_forces", "nbody_forest_step",
            "nbody_autotune", "nbody_set_walk_shape", "nbody_get_walk_shape",
-           "nbody_set_sort_mode", "nbody_get_sort_stats", "nbody_measure_fp32_rate")
+           "nbody_set_walk_limits",
+           "nbody_set_sort_mode", "nbody_get_sort_stats", "nbody_measure_fp32_rate",
+           "nbody_measure_fp64_rate")
 
 
 class NBodyError(RuntimeError):
@@ -102,9 +105,11 @@ def load_library(path: str = LIB_PATH):
         "nbody_autotune": [vp, vp, vp, i64, vp, vp],
         "nbody_get_walk_shape": [vp, vp, vp],
         "nbody_set_walk_shape": [vp, i32],
+        "nbody_set_walk_limits": [vp, i32, i64],
         "nbody_set_sort_mode": [vp, i32],
         "nbody_get_sort_stats": [vp, vp, vp],
         "nbody_measure_fp32_rate": [vp, vp],
+        "nbody_measure_fp64_rate": [vp, vp],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -303,6 +308,12 @@ class Context:
     def set_walk_shape(self, shape):
         self._check(self._lib.nbody_set_walk_shape(self._h, int(shape)), "nbody_set_walk_shape")
 
+    def set_walk_limits(self, stack_entries=0, max_steps=0):
+        """Test aid: lowers the walk's stack entries / steps (0 = the defaults); a walk that
+        reaches a limit stops and the next sync() raises NBODY_ESTACK."""
+        self._check(self._lib.nbody_set_walk_limits(self._h, int(stack_entries), int(max_steps)),
+                    "nbody_set_walk_limits")
+
     def walk_shape(self):
         """(shape index, threads per block) of the walk for this context's precision."""
         k, t = ctypes.c_int32(), ctypes.c_int32()
@@ -409,4 +420,18 @@ def measure_fp32_rate(stream=None) -> float:
                                                 ctypes.byref(v))
     if st != 0:
         raise NBodyError(st, "nbody_measure_fp32_rate")
+    return float(v.value)
+
+
+def measure_fp64_rate(stream=None) -> float:
+    """FP64 fused multiply-add rate of the current device in TFLOP/s (a measurement aid; see
+    nbody_measure_fp64_rate in include/nbody.h)."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    v = ctypes.c_double()
+    st = load_library().nbody_measure_fp64_rate(ctypes.c_void_p(stream.cuda_stream),
+                                                ctypes.byref(v))
+    if st != 0:
+        raise NBodyError(st, "nbody_measure_fp64_rate")
     return float(v.value)

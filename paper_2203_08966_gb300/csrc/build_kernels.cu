@@ -309,10 +309,12 @@ constexpr int kSortThreads = 256;
 constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kSortItems = 16;                         // per thread
 constexpr int kSortTile = kSortThreads * kSortItems;   // 4096 keys per tile
-constexpr int kPasses = 8;       // key passes
+constexpr int kPasses = kSortKeyPasses;  // key passes
 constexpr int kSysPasses = 2;    // forest: system passes (systems < 2^16)
 constexpr int kIdPasses = 4;     // at most: passes on the id bytes before the key passes
 constexpr int kHistRows = kPasses + kIdPasses + kSysPasses;  // key, id, system digit totals
+static_assert(kSortTile == kSortTileKeys && kHistRows == kSortHistRows,
+              "sort geometry shared through nbody_internal.cuh");
 
 // Pairs to sort: n, or (d_n non-null) the count on the device, at most n (the grids are sized
 // for n and the blocks past the device count return at once).
@@ -715,7 +717,7 @@ __device__ __forceinline__ D4 ld_cg(const D4 *p)
     return r;
 }
 
-// Adds a mass m at offset (x, y, z) from a centre of mass to a quadrupole (§2.1):
+// Adds a mass m at offset (x, y, z) from a centre of mass to a quadrupole (§2.2):
 // Q_ab += m (3 x_a x_b - r^2 delta_ab), components xx, yy, zz, xy, xz, yz.
 __device__ __forceinline__ void quad_add(double q[6], double m, double x, double y, double z)
 {
@@ -789,7 +791,7 @@ __global__ void link_leaves_kernel(const uint64_t *__restrict__ keys, NodeArrays
             na.com_lo[b] = m;
             na.lo_child[b] = make_int4(0, 0, w.first, 0);
             if (na.q_lo) {
-                // quadrupole of the leaf's bodies about their centre of mass (§2.1): 0 for one
+                // quadrupole of the leaf's bodies about their centre of mass (§2.2): 0 for one
                 // body; a bucket sums over its members
                 double q[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
                 for (int p = w.first; w.count > 1 && p < w.first + w.count; ++p) {
@@ -1279,6 +1281,23 @@ void launch_radix_sort_key_id(uint64_t *keys, uint32_t *ids, int n, int id_bits,
     if (n <= 1) return;
     const int id_passes = std::min(kIdPasses, std::max(1, (id_bits + 7) / 8));
     radix_passes(keys, ids, n, id_passes, sc, s, out_keys, out_ids);
+}
+
+__global__ void check_finite_kernel(const double *__restrict__ pos,
+                                    const double *__restrict__ mass, int n, int *flag)
+{
+    bool bad = false;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        bad = bad || !isfinite(pos[i]) || !isfinite(pos[(size_t)n + i]) ||
+              !isfinite(pos[2 * (size_t)n + i]) || !isfinite(mass[i]);
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, kErrInput);
+}
+
+void launch_check_finite(const double *pos, const double *mass, int n, int *flag, cudaStream_t s)
+{
+    if (n <= 0) return;
+    check_finite_kernel<<<std::min((n + 255) / 256, 152 * 8), 256, 0, s>>>(pos, mass, n, flag);
+    count_launches(1);
 }
 
 void launch_permute(const D4 *aos, const uint32_t *ids, int n, const Box *box, const Systems &ss,

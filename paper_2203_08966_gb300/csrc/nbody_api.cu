@@ -74,6 +74,10 @@ struct nbody_ctx {
     uint32_t *span_off = nullptr, *span_pool = nullptr, *span_tmp = nullptr;
     unsigned *span_next = nullptr;
     int64_t span_n = 0, span_pool_cap = 0, span_tmp_warps = 0;
+    // walk limits (nbody_set_walk_limits; the defaults never bind) and the finite-input check
+    int stack_limit = 1 << 30;
+    int64_t step_limit = INT64_MAX;
+    int *chk = nullptr;             // device word: kErrInput when NBODY_FLAG_CHECK_FINITE fails
     float *dscratch = nullptr;      // FP32 direct sum: sources + partial sums (grown on demand)
     int64_t dscratch_cap = 0;       // floats
     // one forest step captured as a CUDA graph, replayed on its own stream
@@ -152,10 +156,11 @@ bool params_ok(const nbody_params *p)
     if (!isfinite(p->G) || !isfinite(p->dt)) return false;
     if (!(p->eps >= 0.0) || !isfinite(p->eps)) return false;
     if (!(p->theta >= 0.0) || !isfinite(p->theta)) return false;
-    if (p->precision < NBODY_FP64 || p->precision > NBODY_FP32_KAHAN) return false;
+    if (p->precision < NBODY_FP64 || p->precision > NBODY_FP64_FAST) return false;
     const uint32_t fp32_only = NBODY_FLAG_GROUP_MAC | NBODY_FLAG_CELL_GROUPS;
-    if ((p->flags & ~(fp32_only | NBODY_FLAG_QUADRUPOLE)) != 0) return false;
-    if ((p->flags & fp32_only) && p->precision == NBODY_FP64) return false;
+    if ((p->flags & ~(fp32_only | NBODY_FLAG_QUADRUPOLE | NBODY_FLAG_CHECK_FINITE)) != 0)
+        return false;
+    if ((p->flags & fp32_only) && is_fp64(p->precision)) return false;
     return true;
 }
 
@@ -291,7 +296,7 @@ void free_spans(nbody_ctx *c)
 // with the per-body acceptance test and monopole cells.
 bool use_spans(const nbody_ctx *c)
 {
-    return c->n_sys == 0 && c->p.precision != NBODY_FP64 &&
+    return c->n_sys == 0 && !is_fp64(c->p.precision) &&
            (c->p.flags & (NBODY_FLAG_GROUP_MAC | NBODY_FLAG_CELL_GROUPS | NBODY_FLAG_QUADRUPOLE)) == 0;
 }
 
@@ -399,6 +404,11 @@ nbody_status build(nbody_ctx *c, const double *pos, const double *mass, int n,
         return NBODY_OK;
     }
     const Systems one{nullptr, nullptr, 1};
+    const bool check = (c->p.flags & NBODY_FLAG_CHECK_FINITE) != 0;
+    if (check) {
+        CK(cudaMemsetAsync(c->chk, 0, sizeof(int), s));
+        launch_check_finite(pos, mass, n, c->chk, s);
+    }
     if (!have_partials) launch_bbox_partials(pos, mass, n, c->partials, c->nblk, c->aos, s);
     launch_bbox_finalize(c->partials, c->nblk, c->box, c->tab, c->p.theta, s);
     SortScratch sc{c->keys_alt, c->ids_alt, c->hist, c->counts, sort_tiles((int)c->cap), nullptr,
@@ -413,12 +423,18 @@ nbody_status build(nbody_ctx *c, const double *pos, const double *mass, int n,
     CKS(check_launch(c, "tree build"));
     CK(cudaMemcpyAsync(c->h_word, c->node_off + n, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(c->h_word + 1, c->info, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    if (check) CK(cudaMemcpyAsync(c->h_word + 2, c->chk, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    if (check && c->h_word[2] != 0u) {
+        c->n_built = -1;
+        c->order_n = -1;
+        return fail(c, NBODY_EINVAL, "a position or mass is NaN or infinite");
+    }
     const int64_t nn = (int64_t)c->h_word[0];
     const int max_level = (int)c->h_word[1];
     if (nn < 1 || nn > 22 * (int64_t)n)
         return fail(c, NBODY_ECUDA, "node count %lld out of range for n = %d", (long long)nn, n);
-    const bool group = c->p.precision != NBODY_FP64;
+    const bool group = !is_fp64(c->p.precision);
     if (group && nn > (int64_t)kMaxGroupNodes)
         return fail(c, NBODY_EINVAL, "%lld tree nodes: the FP32 walk indexes at most %lld",
                     (long long)nn, (long long)kMaxGroupNodes);
@@ -469,7 +485,7 @@ nbody_status walk(nbody_ctx *c, int n, double *acc, double *vel, double h)
     a.d_ngroups = nullptr;
     a.roots = c->roots;
     a.work = c->work;
-    if (c->p.precision != NBODY_FP64 && cell_groups(c)) {
+    if (!is_fp64(c->p.precision) && cell_groups(c)) {
         a.groups = c->cgroups;
         a.n_groups = (int)std::min<int64_t>(c->cap + 1, INT32_MAX);
         a.d_ngroups = c->cgroups_n;
@@ -478,7 +494,9 @@ nbody_status walk(nbody_ctx *c, int n, double *acc, double *vel, double h)
     a.start = c->sys_start;
     a.group_mac = (c->p.flags & NBODY_FLAG_GROUP_MAC) != 0;
     a.q64 = c->na.q64;
-    a.gq = c->p.precision != NBODY_FP64 ? c->na.gq : nullptr;
+    a.gq = !is_fp64(c->p.precision) ? c->na.gq : nullptr;
+    a.stack_limit = c->stack_limit;
+    a.step_limit = c->step_limit;
     a.span_meta = nullptr;
     a.span_off = a.span_pool = a.span_tmp = nullptr;
     a.span_next = nullptr;
@@ -492,7 +510,7 @@ nbody_status walk(nbody_ctx *c, int n, double *acc, double *vel, double h)
         a.span_tmp = c->span_tmp;
         a.span_next = c->span_next;
     }
-    launch_walk(c->p.precision, a, c->p.precision == NBODY_FP64 ? c->shape64 : c->shape32,
+    launch_walk(c->p.precision, a, is_fp64(c->p.precision) ? c->shape64 : c->shape32,
                 c->stream);
     record(c, 4);
     CKS(check_launch(c, "walk"));
@@ -514,6 +532,7 @@ nbody_status forest_build(nbody_ctx *c, double *pos, const double *mass, double 
     cudaStream_t s = c->stream;
     const int n = (int)c->cap;
     const Systems ss = systems(c);
+    if (c->p.flags & NBODY_FLAG_CHECK_FINITE) launch_check_finite(pos, mass, n, c->err, s);
     launch_forest_boxes(pos, vel, c->acc, mass, n, c->box_chunks, c->n_box_chunks,
                         c->box_chunk_start, c->n_sys, h, c->p.dt, c->box_partials, c->box, c->tab,
                         c->p.theta, c->aos, s);
@@ -531,9 +550,9 @@ nbody_status forest_build(nbody_ctx *c, double *pos, const double *mass, double 
     launch_emit_nodes(c->keys, n, ss, c->node_off, c->na, c->err, s);
     launch_level_order(c->na, s);
     launch_moments(c->keys, kMaxLevel, c->sbody64, c->box, c->tab, ss, c->p.G, c->na, s);
-    if (c->p.precision != NBODY_FP64) launch_group_nodes(c->na, c->box, c->tab, ss, c->p.G, c->gn, s);
+    if (!is_fp64(c->p.precision)) launch_group_nodes(c->na, c->box, c->tab, ss, c->p.G, c->gn, s);
     launch_roots(c->na, c->node_off, ss, c->roots, s);
-    if (c->p.precision != NBODY_FP64 && cell_groups(c)) {
+    if (!is_fp64(c->p.precision) && cell_groups(c)) {
         CK(cudaMemsetAsync(c->cgroups_n, 0, sizeof(unsigned), s));
         launch_cell_groups(c->na, c->node_off, ss, n, 32, c->cgroups, c->cgroups_n, c->cap + 1,
                            c->err, s);
@@ -643,6 +662,7 @@ nbody_status nbody_create(nbody_ctx **out, int64_t n_capacity, const nbody_param
         CK(dalloc(&c->cgroups, cap + 1));
         CK(dalloc(&c->cgroups_n, 1));
         CK(dalloc(&c->work, 1));
+        CK(dalloc(&c->chk, 1));
         CK(cudaMemset(c->err, 0, sizeof(int)));
         CK(cudaMallocHost((void **)&c->h_word, (2 + kOrderStats) * sizeof(uint32_t)));
         CK(dalloc(&c->info, 1));
@@ -685,6 +705,7 @@ nbody_status nbody_destroy(nbody_ctx *c)
     dfree(c->cgroups);
     dfree(c->cgroups_n);
     dfree(c->work);
+    dfree(c->chk);
     free_spans(c);
     dfree(c->sys);
     dfree(c->sys_start);
@@ -828,7 +849,7 @@ nbody_status nbody_direct_forces(nbody_ctx *c, const double *d_pos, const double
     launch_bbox_partials(d_pos, d_mass, (int)n, c->partials, c->nblk, nullptr, c->stream);
     launch_bbox_finalize(c->partials, c->nblk, c->box + 1, c->tab + 1, c->p.theta, c->stream);
     DirectScratch ds{nullptr, nullptr};
-    if (c->p.precision != NBODY_FP64) {
+    if (!is_fp64(c->p.precision)) {
         // FP32 scratch, grown on demand: sources, then per-chunk partial sums
         const int64_t need = (int64_t)4 * n + (int64_t)direct32_chunks((int)n, (int)nt) * 3 * nt;
         if (need > c->dscratch_cap) {
@@ -851,10 +872,16 @@ nbody_status nbody_sync(nbody_ctx *c)
     CK(cudaStreamSynchronize(c->stream));
     int e = 0;
     CK(cudaMemcpy(&e, c->err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (e == 0) return NBODY_OK;
+    // reported once: the word is cleared, and the context stays usable
+    CK(cudaMemsetAsync(c->err, 0, sizeof(int), c->stream));
+    c->acc_n = -1;  // a kept acceleration may come from the failed walk
+    if (e & kErrInput) return fail(c, NBODY_EINVAL, "a position or mass is NaN or infinite");
     if (e & kErrTimeout) return fail(c, NBODY_ETIMEOUT, "a device-side wait gave up");
     if (e & kErrNodeCap) return fail(c, NBODY_ENOMEM, "node capacity exceeded on the device");
-    if (e & kErrStack) return fail(c, NBODY_ESTACK, "a group walk overran its node stack");
-    return NBODY_OK;
+    if (e & kErrStack)
+        return fail(c, NBODY_ESTACK, "a walk ran out of stack entries or steps");
+    return fail(c, NBODY_ECUDA, "device error word %d", e);
 }
 
 nbody_status nbody_get_keys(nbody_ctx *c, uint64_t *h_keys_sorted, uint32_t *h_ids_sorted)
@@ -1000,7 +1027,7 @@ nbody_status nbody_autotune(nbody_ctx *c, const double *d_pos, const double *d_m
     if (c->n_sys) n = c->cap;
     CKS(check_n(c, n));
     if (n > 0 && (!d_pos || !d_mass)) return fail(c, NBODY_EINVAL, "null pointer");
-    int &shape = c->p.precision == NBODY_FP64 ? c->shape64 : c->shape32;
+    int &shape = is_fp64(c->p.precision) ? c->shape64 : c->shape32;
     if (n == 0) {
         if (chosen) *chosen = shape;
         return NBODY_OK;
@@ -1053,7 +1080,7 @@ nbody_status nbody_set_walk_shape(nbody_ctx *c, int32_t shape)
 {
     if (!c) return NBODY_EINVAL;
     if (shape < 0 || shape >= kWalkShapes) return fail(c, NBODY_EINVAL, "shape %d", (int)shape);
-    (c->p.precision == NBODY_FP64 ? c->shape64 : c->shape32) = shape;
+    (is_fp64(c->p.precision) ? c->shape64 : c->shape32) = shape;
     if (c->gexec) {
         cudaGraphExecDestroy(c->gexec);
         c->gexec = nullptr;
@@ -1064,9 +1091,24 @@ nbody_status nbody_set_walk_shape(nbody_ctx *c, int32_t shape)
 nbody_status nbody_get_walk_shape(nbody_ctx *c, int32_t *shape, int32_t *threads_per_block)
 {
     if (!c) return NBODY_EINVAL;
-    const int k = c->p.precision == NBODY_FP64 ? c->shape64 : c->shape32;
+    const int k = is_fp64(c->p.precision) ? c->shape64 : c->shape32;
     if (shape) *shape = k;
     if (threads_per_block) *threads_per_block = walk_shape_threads(c->p.precision, k);
+    return NBODY_OK;
+}
+
+nbody_status nbody_set_walk_limits(nbody_ctx *c, int32_t stack_entries, int64_t max_steps)
+{
+    if (!c) return NBODY_EINVAL;
+    if (stack_entries != 0 && stack_entries < 33)
+        return fail(c, NBODY_EINVAL, "stack_entries %d: 0 or at least 33", (int)stack_entries);
+    if (max_steps < 0) return fail(c, NBODY_EINVAL, "max_steps < 0");
+    c->stack_limit = stack_entries == 0 ? (1 << 30) : stack_entries;
+    c->step_limit = max_steps == 0 ? INT64_MAX : max_steps;
+    if (c->gexec) {  // a captured forest step holds the old limits
+        cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+    }
     return NBODY_OK;
 }
 
@@ -1075,6 +1117,15 @@ nbody_status nbody_measure_fp32_rate(void *cuda_stream, double *h_tflops)
     if (!h_tflops) return NBODY_EINVAL;
     *h_tflops = 0.0;
     const cudaError_t e = measure_fp32_rate((cudaStream_t)cuda_stream, h_tflops);
+    if (e == cudaErrorMemoryAllocation) return NBODY_ENOMEM;
+    return e == cudaSuccess ? NBODY_OK : NBODY_ECUDA;
+}
+
+nbody_status nbody_measure_fp64_rate(void *cuda_stream, double *h_tflops)
+{
+    if (!h_tflops) return NBODY_EINVAL;
+    *h_tflops = 0.0;
+    const cudaError_t e = measure_fp64_rate((cudaStream_t)cuda_stream, h_tflops);
     if (e == cudaErrorMemoryAllocation) return NBODY_ENOMEM;
     return e == cudaSuccess ? NBODY_OK : NBODY_ECUDA;
 }

@@ -71,7 +71,7 @@ __device__ __forceinline__ uint64_t morton_key(double x, double y, double z, con
 }
 
 // Device error word bits.
-enum : int { kErrNodeCap = 1, kErrTimeout = 2, kErrStack = 4 };
+enum : int { kErrNodeCap = 1, kErrTimeout = 2, kErrStack = 4, kErrInput = 8 };
 
 // Per-level tables written with the box.
 struct LevelTables {
@@ -88,6 +88,12 @@ struct Systems {
     int count;
 };
 constexpr int kMaxSystems = 65535;
+
+// FP64 precisions (the bit-exact and the fast form share the FP64 tree and acceptance test).
+inline bool is_fp64(int precision)
+{
+    return precision == NBODY_FP64 || precision == NBODY_FP64_FAST;
+}
 
 // Process-wide count of kernel launches made by the library (every launcher adds its launches).
 void count_launches(int k);
@@ -117,6 +123,12 @@ void launch_forest_boxes(double *pos, double *vel, const double *acc, const doub
 void launch_keys(const double *pos, int n, const Box *box, const Systems &ss, uint64_t *keys,
                  uint32_t *ids, cudaStream_t s, const int *gate = nullptr);
 
+// Radix sort geometry (build_kernels.cu): keys per tile, key passes, and rows of digit totals
+// (8 key passes, up to 4 passes on id bytes, 2 on the system of a forest's bodies).
+constexpr int kSortTileKeys = 4096;
+constexpr int kSortKeyPasses = 8;
+constexpr int kSortHistRows = 14;
+
 struct SortScratch {
     uint64_t *keys_alt;
     uint32_t *ids_alt;
@@ -139,6 +151,9 @@ void launch_radix_sort(uint64_t *keys, uint32_t *ids, int n, const SortScratch &
 void launch_radix_sort_key_id(uint64_t *keys, uint32_t *ids, int n, int id_bits,
                               const SortScratch &sc, cudaStream_t s, uint64_t **out_keys,
                               uint32_t **out_ids);
+
+// Sets *flag (kErrInput bits, OR-ed) when a position or mass of the n bodies is NaN or infinite.
+void launch_check_finite(const double *pos, const double *mass, int n, int *flag, cudaStream_t s);
 
 void launch_permute(const D4 *aos, const uint32_t *ids, int n, const Box *box, const Systems &ss,
                     double G, D4 *sbody64, float4 *sbody32, cudaStream_t s);
@@ -283,6 +298,8 @@ inline const int *order_full_count(const OrderScratch &o)
 // The FP32 fused multiply-add rate of the current device in TFLOP/s (a timed kernel of
 // independent FMA chains on every SM; the call waits for it).
 cudaError_t measure_fp32_rate(cudaStream_t s, double *tflops);
+// The same for FP64 fused multiply-adds.
+cudaError_t measure_fp64_rate(cudaStream_t s, double *tflops);
 
 // ---------------------------------------------------------------- walk_kernels.cu
 struct WalkArgs {
@@ -322,6 +339,10 @@ struct WalkArgs {
     int64_t span_pool_cap;
     uint32_t *span_tmp;   // per far-walk warp: kSpanFarTmp + 2 kSpanFrTmp words
     unsigned *span_next;  // [0] pool words handed out, [1] span counter (zeroed per launch)
+    // test aid (nbody_set_walk_limits): stack entries a group walk may use (at most the
+    // kernel's capacity) and steps per group or span (at most the node count)
+    int stack_limit;
+    int64_t step_limit;
 };
 // Spans of the shared far walk: 8 groups of 32 bodies.  A span's far list holds at most
 // kSpanFarTmp nodes and its frontier at most kSpanFrTmp (else its groups walk from the root).

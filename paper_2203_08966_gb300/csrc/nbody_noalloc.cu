@@ -1,12 +1,11 @@
 // Allocation-free Morton keys + sort: nbody_sort_keys_noalloc.
 //
-// For callers that cannot call cudaMalloc: code running while a CUDA graph is being captured
-// (allocation is not a capturable operation), callers that own a fixed device-memory budget
-// (an embedding runtime with its own pool, a real-time loop that must not block in the
-// allocator), and plugins whose host application forbids allocation after start-up.  The
-// working memory that nbody_build_tree keeps in its context (alternate key and id buffers,
-// digit histograms, box partials) lives here in one file-scope device array instead, which
-// every GPU that loads the library holds until the process exits.
+// For callers that cannot call cudaMalloc: runtimes that own a fixed device-memory budget (an
+// embedding application with its own pool), real-time loops that must not block in the
+// allocator, and plugins whose host application forbids allocation after start-up.  The working
+// memory that nbody_build_tree keeps in its context (alternate key and id buffers, digit
+// histograms, box partials) lives here in one file-scope device array instead, which every GPU
+// that loads the library holds until the process exits.
 #include <mutex>
 
 #include "nbody_internal.cuh"
@@ -19,20 +18,23 @@ constexpr int64_t kMaxN = NBODY_NOALLOC_MAX_N;
 constexpr size_t kAlign = 256;
 constexpr size_t round_up(size_t b) { return (b + kAlign - 1) / kAlign * kAlign; }
 
-constexpr int kSortTileBodies = 4096;  // bodies per radix-sort tile (must match the sort)
-constexpr int64_t kMaxTiles = (kMaxN + kSortTileBodies - 1) / kSortTileBodies;
+constexpr int64_t kMaxTiles = (kMaxN + kSortTileKeys - 1) / kSortTileKeys;
 
 // Scratch layout: alternate keys | alternate ids | digit histogram | per-tile digit counts |
 // box partials | root box | level tables.
 constexpr size_t kOffKeys = 0;
 constexpr size_t kOffIds = kOffKeys + round_up(sizeof(uint64_t) * kMaxN);
 constexpr size_t kOffHist = kOffIds + round_up(sizeof(uint32_t) * kMaxN);
-constexpr size_t kOffCounts = kOffHist + round_up(sizeof(uint32_t) * 8 * 256);
+// the sort of one system clears and fills kSortKeyPasses rows of 256 digit totals
+constexpr size_t kOffCounts = kOffHist + round_up(sizeof(uint32_t) * kSortKeyPasses * 256);
 constexpr size_t kOffPartials = kOffCounts + round_up(sizeof(uint32_t) * 256 * kMaxTiles);
 constexpr size_t kPartialBytes = 64 * 1024;
 constexpr size_t kOffBox = kOffPartials + kPartialBytes;
 constexpr size_t kOffTab = kOffBox + round_up(sizeof(Box));
 constexpr size_t kScratchBytes = kOffTab + round_up(sizeof(LevelTables));
+static_assert(kOffCounts - kOffHist >= sizeof(uint32_t) * kSortKeyPasses * 256 &&
+                  kOffPartials - kOffCounts >= sizeof(uint32_t) * 256 * kMaxTiles,
+              "scratch regions hold what the sort writes");
 
 // The scratch.  In host code this name is only a host-side stand-in for the device array, not a
 // device address: kernels receive the address cudaGetSymbolAddress returns for it.
@@ -42,16 +44,18 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mutex;
 unsigned char *g_dev_scratch[kMaxDevices] = {};
 
-// Once per device, with that device current: the scratch's device address and the sort's
+// With the caller's device current: the scratch's device address, looked up on every call (the
+// lookup enqueues nothing, and a context created after a device reset gets its own address).  The
+// first call on a device, and any call that finds a different address there, also sets the sort's
 // shared-memory attribute.
 nbody_status setup(unsigned char **out)
 {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return NBODY_ECUDA;
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) return NBODY_ECUDA;
     std::lock_guard<std::mutex> lock(g_mutex);
-    if (!g_dev_scratch[dev]) {
-        void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) return NBODY_ECUDA;
+    if (g_dev_scratch[dev] != p) {
         if (sort_prepare() != cudaSuccess) return NBODY_ECUDA;
         g_dev_scratch[dev] = static_cast<unsigned char *>(p);
     }
@@ -88,5 +92,6 @@ extern "C" nbody_status nbody_sort_keys_noalloc(const double *d_pos, const doubl
     // the sort clears its digit histogram itself; every other scratch word is written before
     // it is read
     launch_radix_sort(d_keys_sorted, d_ids_sorted, (int)n, sc, s);
+    // the status covers every launch above and any CUDA error still pending on this thread
     return cudaGetLastError() == cudaSuccess ? NBODY_OK : NBODY_ECUDA;
 }

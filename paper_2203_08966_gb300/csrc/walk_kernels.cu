@@ -54,7 +54,33 @@ __device__ __forceinline__ void pair64(double xj, double yj, double zj, double m
     }
 }
 
-// FP64 cell term with the quadrupole (§2.1, eq. `truncmultipole`): the acceleration of the
+// The same pair term, fast form (NBODY_FP64_FAST): fused multiply-adds and one reciprocal
+// square root; the result differs from pair64 by rounding only.
+__device__ __forceinline__ void pair64_fast(double xj, double yj, double zj, double mj, double xi,
+                                            double yi, double zi, double G, double eps2,
+                                            double &ax, double &ay, double &az)
+{
+    const double dx = xj - xi, dy = yj - yi, dz = zj - zi;
+    const double r2 = fma(dx, dx, fma(dy, dy, fma(dz, dz, eps2)));
+    if (r2 > 0.0) {
+        const double ri = rsqrt(r2);
+        const double f = (G * mj) * (ri * ri * ri);
+        ax = fma(f, dx, ax);
+        ay = fma(f, dy, ay);
+        az = fma(f, dz, az);
+    }
+}
+
+template <bool kFast>
+__device__ __forceinline__ void pair64_any(double xj, double yj, double zj, double mj, double xi,
+                                           double yi, double zi, double G, double eps2,
+                                           double &ax, double &ay, double &az)
+{
+    if (kFast) pair64_fast(xj, yj, zj, mj, xi, yi, zi, G, eps2, ax, ay, az);
+    else pair64(xj, yj, zj, mj, xi, yi, zi, G, eps2, ax, ay, az);
+}
+
+// FP64 cell term with the quadrupole (§2.2, eq. `truncmultipole`): the acceleration of the
 // softened expansion Phi = -G (M / r_s + (x.Q.x) / (2 r_s^5)), x = r_i - r_J,
 // r_s^2 = |x|^2 + eps^2; with d = r_J - r_i:
 //   a += G (M d / r_s^3 - Q d / r_s^5 + 5/2 (d.Q.d) d / r_s^7),
@@ -412,7 +438,7 @@ struct GroupEval {
 };
 
 // kWarps warps per block (a launch shape the autotuner chooses; results do not depend on it).
-// kQuad: accepted cells add their quadrupole term (§2.1).
+// kQuad: accepted cells add their quadrupole term (§2.2).
 // kGroup: the grouped acceptance test (Barnes 1990; not in the paper): a cell is accepted for
 // the whole group when the lower bound of the group's distances passes the test, else it is
 // opened for the whole group; no body masks, no per-body tests.  A body meets its own leaf and
@@ -522,9 +548,10 @@ __device__ __forceinline__ void walk_group(const WalkArgs &a, GroupSmem &S, Quad
 
     // every node is popped at most once per group, so more steps than nodes means a malformed
     // tree: stop with the error word set rather than loop
-    int steps_left = n_nodes;
+    const int stack_cap = min(kStackCap, a.stack_limit);
+    int64_t steps_left = min((int64_t)n_nodes, a.step_limit);
     while (sp > 0) {
-        if (sp > kStackCap - 32 || --steps_left < 0) {  // cannot happen (see kStackCap)
+        if (sp > stack_cap - 32 || --steps_left < 0) {  // cannot happen (see kStackCap)
             if (lane == 0) atomicOr(a.err, kErrStack);
             break;
         }
@@ -944,9 +971,10 @@ __device__ __forceinline__ void walk_group_pb(const WalkArgs &a, PbSmem &S, int 
 
     // every node is popped at most once per group, so more steps than nodes means a malformed
     // tree: stop with the error word set rather than loop
-    int steps_left = n_nodes;
+    const int stack_cap = min(kPbStack, a.stack_limit);
+    int64_t steps_left = min((int64_t)n_nodes, a.step_limit);
     while (sp > 0 || fr_next < fr_n) {
-        if (sp > kPbStack - 32 || --steps_left < 0) {  // cannot happen (see the stack bound)
+        if (sp > stack_cap - 32 || --steps_left < 0) {  // cannot happen (see the stack bound)
             if (lane == 0) atomicOr(a.err, kErrStack);
             break;
         }
@@ -1164,9 +1192,10 @@ __global__ void __launch_bounds__(kWarps * 32) far_walk32_kernel(WalkArgs a)
                 sp = 1;
             }
         }
-        int steps_left = n_nodes;
+        const int stack_cap = min(kPbStack, a.stack_limit);
+        int64_t steps_left = min((int64_t)n_nodes, a.step_limit);
         while (sp > 0) {
-            if (sp > kPbStack - 32 || --steps_left < 0) {  // cannot happen (see the stack bound)
+            if (sp > stack_cap - 32 || --steps_left < 0) {  // cannot happen (see the stack bound)
                 if (lane == 0) atomicOr(a.err, kErrStack);
                 over = true;
                 break;
@@ -1300,7 +1329,8 @@ __global__ void __launch_bounds__(kWarps * 32) far_walk32_kernel(WalkArgs a)
 
 // FP64 walk, operation for operation the plain per-particle definition: the MAC is
 // l^2 < theta^2 d^2 with l^2 of the cell's level and d the distance to its FP64 centre of mass.
-template <int kThreads>
+// kFast (NBODY_FP64_FAST): the same walk and acceptance tests, pair terms by pair64_fast.
+template <int kThreads, bool kFast>
 __global__ void __launch_bounds__(kThreads) walk64_kernel(WalkArgs a)
 {
     const int lane = threadIdx.x & 31;
@@ -1328,9 +1358,16 @@ __global__ void __launch_bounds__(kThreads) walk64_kernel(WalkArgs a)
     uint32_t pp = 0, pc = 0;
     int next = (!live || n_nodes - first < 2 || __ldg(&a.wn[first].count) != 0) ? n_nodes
                                                                                 : first + 1;
+    // the warp visits each node at most once (next only grows), so this budget ends the loop
+    // only when a test lowers it
+    int64_t steps_left = a.step_limit;
     for (;;) {
         const int j = __reduce_min_sync(kFull, next);
         if (j >= n_nodes) break;
+        if (--steps_left < 0) {
+            if (lane == 0) atomicOr(a.err, kErrStack);
+            break;
+        }
         if (next != j) continue;
         const int4 meta = __ldg(reinterpret_cast<const int4 *>(&a.wn[j].skip));
         const int skip = meta.x, first = meta.y, count = meta.z;
@@ -1339,7 +1376,7 @@ __global__ void __launch_bounds__(kThreads) walk64_kernel(WalkArgs a)
             for (int b = first; b < end; ++b) {
                 if (b == i) continue;
                 const D4 s = a.sbody64[b];
-                pair64(s.x, s.y, s.z, s.w, me.x, me.y, me.z, G, eps2, ax, ay, az);
+                pair64_any<kFast>(s.x, s.y, s.z, s.w, me.x, me.y, me.z, G, eps2, ax, ay, az);
                 ++pp;
             }
             next = skip;
@@ -1355,7 +1392,7 @@ __global__ void __launch_bounds__(kThreads) walk64_kernel(WalkArgs a)
                     cell64q(s.x, s.y, s.z, s.w, a.q64 + 6 * (size_t)j, me.x, me.y, me.z, G, eps2,
                             ax, ay, az);
                 else
-                    pair64(s.x, s.y, s.z, s.w, me.x, me.y, me.z, G, eps2, ax, ay, az);
+                    pair64_any<kFast>(s.x, s.y, s.z, s.w, me.x, me.y, me.z, G, eps2, ax, ay, az);
                 ++pc;
                 next = skip;
             } else {
@@ -1441,6 +1478,7 @@ struct alignas(16) Src64 {
     double x, y, z, m;
 };
 
+template <bool kFast>
 __global__ void __launch_bounds__(kDirectThreads) direct64_kernel(
     const double *__restrict__ pos, const double *__restrict__ mass, int n,
     const int64_t *__restrict__ targets, int nt, double G, double eps2, double *__restrict__ acc)
@@ -1472,7 +1510,7 @@ __global__ void __launch_bounds__(kDirectThreads) direct64_kernel(
         for (int k = 0; k < m; ++k) {
             if (base + k == i) continue;
             const Src64 s = tile[k];
-            pair64(s.x, s.y, s.z, s.m, xi, yi, zi, G, eps2, ax, ay, az);
+            pair64_any<kFast>(s.x, s.y, s.z, s.m, xi, yi, zi, G, eps2, ax, ay, az);
         }
     }
     if (live) {
@@ -1599,11 +1637,12 @@ cudaError_t allow_group_smem()
 }
 
 template <int kThreads>
-void launch_w64(const WalkArgs &a, int64_t groups, cudaStream_t s)
+void launch_w64(const WalkArgs &a, int64_t groups, bool fast, cudaStream_t s)
 {
     const int per_block = kThreads / 32;
     const int blocks = (int)((groups + per_block - 1) / per_block);
-    walk64_kernel<kThreads><<<blocks, kThreads, 0, s>>>(a);
+    if (fast) walk64_kernel<kThreads, true><<<blocks, kThreads, 0, s>>>(a);
+    else walk64_kernel<kThreads, false><<<blocks, kThreads, 0, s>>>(a);
 }
 
 }  // namespace
@@ -1635,7 +1674,7 @@ int walk_shape_threads(int precision, int shape)
     static const int group_warps[kWalkShapes] = {2, 4, 8};
     static const int w64_threads[kWalkShapes] = {64, 128, 256};
     if (shape < 0 || shape >= kWalkShapes) shape = kDefaultWalkShape;
-    return precision == NBODY_FP64 ? w64_threads[shape] : 32 * group_warps[shape];
+    return is_fp64(precision) ? w64_threads[shape] : 32 * group_warps[shape];
 }
 
 void launch_walk(int precision, const WalkArgs &a, int shape, cudaStream_t s)
@@ -1647,10 +1686,11 @@ void launch_walk(int precision, const WalkArgs &a, int shape, cudaStream_t s)
     const int64_t groups = a.groups ? (int64_t)a.n_groups : ((int64_t)a.n + 31) / 32;
     if (groups <= 0) return;
     if (shape < 0 || shape >= kWalkShapes) shape = kDefaultWalkShape;
-    if (precision == NBODY_FP64) {
-        if (shape == 0) launch_w64<64>(a, groups, s);
-        else if (shape == 1) launch_w64<128>(a, groups, s);
-        else launch_w64<256>(a, groups, s);
+    if (is_fp64(precision)) {
+        const bool fast = precision == NBODY_FP64_FAST;
+        if (shape == 0) launch_w64<64>(a, groups, fast, s);
+        else if (shape == 1) launch_w64<128>(a, groups, fast, s);
+        else launch_w64<256>(a, groups, fast, s);
     } else {
         const bool kahan = precision == NBODY_FP32_KAHAN;
         cudaMemsetAsync(a.work, 0, sizeof(unsigned), s);
@@ -1675,10 +1715,14 @@ void launch_direct(int precision, const double *pos, const double *mass, int n,
                    double *acc, const DirectScratch &sc, cudaStream_t s)
 {
     if (nt <= 0) return;
-    if (precision == NBODY_FP64) {
+    if (is_fp64(precision)) {
         const int blocks = (nt + kDirectThreads - 1) / kDirectThreads;
-        direct64_kernel<<<blocks, kDirectThreads, 0, s>>>(pos, mass, n, targets, nt, G, eps * eps,
-                                                          acc);
+        if (precision == NBODY_FP64_FAST)
+            direct64_kernel<true><<<blocks, kDirectThreads, 0, s>>>(pos, mass, n, targets, nt, G,
+                                                                    eps * eps, acc);
+        else
+            direct64_kernel<false><<<blocks, kDirectThreads, 0, s>>>(pos, mass, n, targets, nt, G,
+                                                                     eps * eps, acc);
         count_launches(1);
         return;
     }

@@ -59,6 +59,7 @@ def test_null_context_is_rejected_without_gpu(lib_path):
     lib = nb.load_library(lib_path)
     assert lib.nbody_destroy(None) == 1
     assert lib.nbody_sync(None) == 1
+    assert lib.nbody_set_walk_limits(None, 0, 0) == 1
     assert lib.nbody_create(None, 10, None, None) == 1
 
 
@@ -91,7 +92,7 @@ def test_group_mac_flag_rejected_for_fp64_without_gpu(lib_path):
     h = ctypes.c_void_p()
     bad = nb.Params(1.0, 0.01, 0.5, 1e-3, nb.FP64, nb.FLAG_GROUP_MAC)
     assert lib.nbody_create(ctypes.byref(h), 10, ctypes.byref(bad), None) == 1
-    unknown = nb.Params(1.0, 0.01, 0.5, 1e-3, nb.FP32, 8)
+    unknown = nb.Params(1.0, 0.01, 0.5, 1e-3, nb.FP32, 256)
     assert lib.nbody_create(ctypes.byref(h), 10, ctypes.byref(unknown), None) == 1
     cells64 = nb.Params(1.0, 0.01, 0.5, 1e-3, nb.FP64, nb.FLAG_CELL_GROUPS)
     assert lib.nbody_create(ctypes.byref(h), 10, ctypes.byref(cells64), None) == 1

@@ -612,7 +612,7 @@ def test_cell_groups_match_brute_force_rule(name):
     assert max(len(g) for g in got) <= 32
 
 
-# ---- quadrupole moments (§2.1, truncated multipole expansion) ------------------------------
+# ---- quadrupole moments (§2.2, truncated multipole expansion) ------------------------------
 
 def test_quadrupole_two_body_closed_form():
     """Two masses m at (+-a, 0, 0): about their centre of mass Q_xx = 4 m a^2,

@@ -1,4 +1,4 @@
-"""Quadrupole cell terms (NBODY_FLAG_QUADRUPOLE, §2.1) against the oracle's quadrupole walk, whose
+"""Quadrupole cell terms (NBODY_FLAG_QUADRUPOLE, §2.2) against the oracle's quadrupole walk, whose
 moments follow the definition body by body: the same cells are accepted (counters bit-exact),
 the FP64 path agrees to rounding (the library sums quadrupoles bottom-up with the parallel-axis
 shift), the FP32 paths within a relative RMS of 1e-4; and the quadrupole forces are closer to the

@@ -1,10 +1,11 @@
 """The allocation-free keys + sort entry point (nbody_sort_keys_noalloc) against the context
 path (nbody_build_tree + nbody_get_keys), called through the C ABI.
 
-That entry point serves callers that cannot call cudaMalloc (code inside a CUDA graph capture,
-runtimes with a fixed device-memory budget); its scratch is one file-scope device array shared
-by every call, so this test makes two calls in a row on different inputs and checks that the
-second is not affected by what the first left in the array.  This file is collected last."""
+That entry point serves callers that cannot call cudaMalloc (runtimes with a fixed
+device-memory budget, real-time loops that must not block in the allocator); its scratch is one
+file-scope device array shared by every call, so this test makes two calls in a row on different
+inputs and checks that the second is not affected by what the first left in the array, at the
+largest size it accepts and at the smallest ones.  This file is collected last."""
 import ctypes
 
 import numpy as np
@@ -60,6 +61,14 @@ def test_noalloc_matches_context_path_on_two_calls(lib):
     r2 = _context(second[0], second[2])
     assert np.array_equal(k1, r1[0]) and np.array_equal(i1, r1[1])
     assert np.array_equal(k2, r2[0]) and np.array_equal(i2, r2[1])
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4096, 4097])
+def test_noalloc_small_and_tile_edge_sizes(lib, n):
+    pos, _, mass = ics.plummer(n, 20 + n % 7)
+    k, i = _noalloc(lib, pos, mass)
+    r = _context(pos, mass)
+    assert np.array_equal(k, r[0]) and np.array_equal(i, r[1])
 
 
 def test_noalloc_rejects_sizes_beyond_its_maximum(lib):
