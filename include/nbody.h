@@ -203,7 +203,10 @@ nbody_status nbody_get_box(nbody_ctx *c, double *h_box);
 nbody_status nbody_get_tree(nbody_ctx *c, int64_t *n_nodes, nbody_tree_record *h_records,
                             int64_t cap);
 
-/* FP64 moments of the last build, pre-order: h_out[4*k .. 4*k+3] = (m, x, y, z) of node k. */
+/* FP64 moments of the last build, pre-order: h_out[4*k .. 4*k+3] = (m, x, y, z) of node k.
+ * FP64 contexts (and quadrupole contexts) form every cell's centre of mass from its children's
+ * as the oracle does, bit for bit; the other FP32 contexts keep FP64 sums (sum m, sum m r) in
+ * the tree, and their centres of mass, sum m r / sum m, differ from those by rounding. */
 nbody_status nbody_get_moments(nbody_ctx *c, double *h_out, int64_t cap_nodes);
 
 /* Interaction counters of the last force evaluation, user order (n entries each). */
@@ -223,23 +226,34 @@ nbody_status nbody_get_launch_count(int64_t *out);
 
 /* ---- launch-shape autotuning of the walk ---- */
 
-/* Number of launch shapes of the walk: for the FP32 forms 2, 4 or 8 warps per block (one warp
- * per group of 32 bodies), for FP64 64, 128 or 256 threads per block.  The shape changes only
- * how groups map to blocks, never a result. */
-#define NBODY_WALK_SHAPES 3
+/* Number of launch shapes of the walk.  Every shape gives every body the same interaction list
+ * (the same counters); FP64 results are identical in every shape, while the FP32 forms' sums can
+ * differ in rounding between shapes that group or buffer the terms differently (3 .. 7).
+ * FP64 forms: shapes 0, 1, 2 are 64, 128, 256 threads per block (the other shapes run as 1).
+ * FP32 forms (one warp per group of 32 bodies):
+ *   0, 1, 2  2, 4, 8 warps per block, spans of 256 bodies sharing one walk of the far field
+ *   3        4 warps per block, no shared far walk (every group walks from the root)
+ *   4, 5     4 warps per block, spans of 128 and 512 bodies
+ *   6        4 warps per block, spans of 256 bodies, interaction buffers of 96 entries (not 64)
+ *   7        4 warps per block, groups that follow the tree's cells (as NBODY_FLAG_CELL_GROUPS)
+ * The grouped acceptance test and quadrupole cells take only the warps per block of a shape;
+ * forests and NBODY_FLAG_CELL_GROUPS never share far walks. */
+#define NBODY_WALK_SHAPES 8
 
 /* Builds the tree of d_pos/d_mass (n bodies; for a forest context n is ignored and the whole
- * forest is used), times the walk in every launch shape for the context's precision (3 walks
- * each after a warm-up, CUDA events on the context stream; the call waits for them) and keeps
- * the fastest for every later walk of that precision class.  h_ms (host, may be NULL):
- * receives the mean time of each shape in ms (NBODY_WALK_SHAPES floats); chosen (may be NULL):
- * the shape kept.  The kept acceleration of nbody_step is recomputed by the next step.
- * Errors as nbody_forces; on error the default shape (1) is kept. */
+ * forest is used), times the walk in every launch shape that makes a difference for this
+ * context (3 walks each after a warm-up, CUDA events on the context stream; the call waits for
+ * them) and keeps the fastest: for later walks of n' bodies with floor(log2 n') == floor(log2 n)
+ * at the same theta, and as the context's shape for every other size.  h_ms (host, may be NULL):
+ * receives the mean time of each shape in ms (NBODY_WALK_SHAPES floats, 0 for the shapes not
+ * timed); chosen (may be NULL): the shape kept.  The kept acceleration of nbody_step is
+ * recomputed by the next step.  Errors as nbody_forces; on error the shapes are unchanged. */
 nbody_status nbody_autotune(nbody_ctx *c, const double *d_pos, const double *d_mass, int64_t n,
                             float *h_ms, int32_t *chosen);
 
 /* Sets the walk shape (0 .. NBODY_WALK_SHAPES - 1) for the context's precision class without
- * timing anything.  Errors: EINVAL for a shape out of range. */
+ * timing anything, and forgets the autotuner's choices.  Errors: EINVAL for a shape out of
+ * range. */
 nbody_status nbody_set_walk_shape(nbody_ctx *c, int32_t shape);
 
 /* The walk shape in use for the context's precision and its threads per block. */

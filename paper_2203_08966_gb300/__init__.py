@@ -20,7 +20,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libnbody.so")
 
 FP64, FP32, FP32_KAHAN, FP64_FAST = 0, 1, 2, 3
-WALK_SHAPES = 3  # NBODY_WALK_SHAPES
+WALK_SHAPES = 8  # NBODY_WALK_SHAPES
 FLAG_GROUP_MAC = 1  # NBODY_FLAG_GROUP_MAC: grouped acceptance test (Barnes 1990), FP32 forms
 FLAG_CELL_GROUPS = 2  # NBODY_FLAG_CELL_GROUPS: FP32 walk groups follow the tree's cells
 FLAG_QUADRUPOLE = 4  # NBODY_FLAG_QUADRUPOLE: accepted cells add their quadrupole term

@@ -859,6 +859,106 @@ __global__ void moments_level_kernel(int level, NodeArrays na, double G)
 }
 
 // ------------------------------------------------------------------------------------------
+// Moments of FP32 contexts without quadrupoles.  The FP32 walks read each cell's centre of mass
+// in FP32 only, so the leaves-to-root pass keeps FP64 sums instead of FP64 means: every node
+// holds (sum m x, sum m y, sum m z, sum m) over its bodies, a cell adds its children's sums in
+// octant order, and the centre of mass is formed once per node (one FP64 reciprocal, three
+// products) when the level-order copy for the walk is written.  The FP64 contexts, and the
+// quadrupole terms, keep the means of link_leaves / moments_level, bit for bit the oracle's.
+// ------------------------------------------------------------------------------------------
+
+// Leaf sums and the level-order child / body ranges of every node (pre-order pass).
+//   com_lo[b]   leaves: (sum m x, sum m y, sum m z, sum m) of their bodies
+//   lo_child[b] (first child in level order, child count, first body, body count of a leaf)
+__global__ void leaf_sums_kernel(const uint64_t *__restrict__ keys, NodeArrays na,
+                                 const D4 *__restrict__ sbody64)
+{
+    const int n_nodes = (int)min((int64_t)*na.d_nn, na.cap);
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n_nodes; j += gridDim.x * blockDim.x) {
+        const WalkNode w = na.wn[j];
+        const int b = na.order[j];
+        if (w.count != 0) {
+            na.mask[j] = 0;
+            D4 sm = {0.0, 0.0, 0.0, 0.0};
+            for (int p = w.first; p < w.first + w.count; ++p) {
+                const D4 q = sbody64[p];
+                sm.x += q.w * q.x;
+                sm.y += q.w * q.y;
+                sm.z += q.w * q.z;
+                sm.w += q.w;
+            }
+            na.com_lo[b] = sm;
+            na.lo_child[b] = make_int4(0, 0, w.first, w.count);
+            continue;
+        }
+        const int shift = 3 * (kMaxLevel - 1 - na.level[j]);
+        unsigned mask = 0;
+        int nc = 0;
+        for (int c = j + 1; c < w.skip && nc < 8; c = max(na.wn[c].skip, c + 1), ++nc)
+            mask |= 1u << (unsigned)((keys[na.wn[c].first] >> shift) & 7u);
+        na.mask[j] = (uint8_t)mask;
+        na.lo_child[b] = make_int4(na.order[j + 1], __popc(mask), w.first, 0);
+    }
+}
+
+// The cells of one level add their children's sums (one level deeper, already done).
+__global__ void sums_level_kernel(int level, NodeArrays na)
+{
+    const int lo = (int)na.tile_offsets[level * na.tiles];
+    const int hi = (int)na.tile_offsets[(level + 1) * na.tiles];
+    for (int t = lo + blockIdx.x * blockDim.x + threadIdx.x; t < hi; t += gridDim.x * blockDim.x) {
+        const int4 ch = na.lo_child[t];
+        if (ch.y == 0) continue;  // leaf
+        D4 sm = {0.0, 0.0, 0.0, 0.0};
+        for (int k = 0; k < min(ch.y, 8); ++k) {
+            const D4 q = ld_cg(&na.com_lo[ch.x + k]);
+            sm.x += q.x;
+            sm.y += q.y;
+            sm.z += q.z;
+            sm.w += q.w;
+        }
+        na.com_lo[t] = sm;
+    }
+}
+
+// FP32 (x - c, y - c, z - c, G m) of a node from its sums: centre of mass = sums / m.
+__device__ __forceinline__ float4 com32_from_sums(const D4 &sm, const Box *bx, double G)
+{
+    const double r = __drcp_rn(sm.w);
+    return make_float4((float)(sm.x * r - bx->c[0]), (float)(sm.y * r - bx->c[1]),
+                       (float)(sm.z * r - bx->c[2]), (float)(G * sm.w));
+}
+
+// GroupNode records in level order from the sums (coalesced writes): one-body leaves copy their
+// body's FP32 record, buckets and cells form their centre of mass here.
+__global__ void group_nodes_sums_kernel(NodeArrays na, const float4 *__restrict__ sbody32,
+                                        const Box *__restrict__ box,
+                                        const LevelTables *__restrict__ tab, Systems ss, double G,
+                                        GroupNode *gn)
+{
+    const int n_nodes = (int)min((int64_t)*na.d_nn, na.cap);
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < n_nodes; b += gridDim.x * blockDim.x) {
+        const int j = na.inv[b];
+        const int4 lc = na.lo_child[b];
+        const int k = system_of(ss, lc.z);
+        GroupNode g;
+        g.pre = j;
+        if (lc.y == 0) {
+            g.c = lc.w == 1 ? sbody32[lc.z] : com32_from_sums(na.com_lo[b], box + k, G);
+            g.child = lc.z;
+            g.n = -lc.w;
+            g.crit = 0.f;
+        } else {
+            g.c = com32_from_sums(na.com_lo[b], box + k, G);
+            g.child = lc.x;
+            g.n = lc.y;
+            g.crit = tab[k].crit32[na.level[j]];
+        }
+        gn[b] = g;
+    }
+}
+
+// ------------------------------------------------------------------------------------------
 // Level-order copy of the tree for the group walk.  A stable partition of the pre-order nodes by
 // level: within a level the nodes keep their pre-order (Morton) order, so the children of a
 // cell, which are consecutive among the nodes of the next level, get consecutive indices.
@@ -1368,6 +1468,29 @@ void launch_moments(const uint64_t *keys, int max_level, const D4 *sbody64, cons
         moments_level_kernel<<<g, 256, 0, s>>>(lev, na, G);
     }
     count_launches(1 + max(0, depth));
+}
+
+void launch_moments_sums(const uint64_t *keys, int max_level, const D4 *sbody64,
+                         const Systems &ss, NodeArrays na, cudaStream_t s)
+{
+    const int64_t cap = na.cap;
+    leaf_sums_kernel<<<grid_for(cap, 256, kMaxGrid * 4), 256, 0, s>>>(keys, na, sbody64);
+    const int depth = min(max_level, kMaxLevel);
+    for (int lev = depth - 1; lev >= 0; --lev) {
+        const int64_t widest = lev < 10 ? ((int64_t)ss.count << (3 * lev)) : cap;
+        const int g = grid_for(std::min<int64_t>(widest, cap), 256, kMaxGrid * 2);
+        sums_level_kernel<<<g, 256, 0, s>>>(lev, na);
+    }
+    count_launches(1 + max(0, depth));
+}
+
+void launch_group_nodes_sums(const NodeArrays &na, const float4 *sbody32, const Box *box,
+                             const LevelTables *tab, const Systems &ss, double G, GroupNode *gn,
+                             cudaStream_t s)
+{
+    group_nodes_sums_kernel<<<grid_for(na.cap, 256, kMaxGrid * 4), 256, 0, s>>>(
+        na, sbody32, box, tab, ss, G, gn);
+    count_launches(1);
 }
 
 void launch_group_nodes(const NodeArrays &na, const Box *box, const LevelTables *tab,

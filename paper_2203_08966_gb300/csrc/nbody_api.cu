@@ -95,8 +95,16 @@ struct nbody_ctx {
     int last_sort_path = -1;    // 0 full sort, 2 re-sort tried (the device's choice in ord.stats),
                                 // -1 no build yet
 
-    // launch shape of the walk per precision class (FP32 forms, FP64), set by nbody_autotune
+    // launch shape of the walk per precision class (FP32 forms, FP64): set by nbody_set_walk_shape
+    // or by nbody_autotune, which also keeps its choice per (N bucket, theta) in shape_cache
     int shape32 = kDefaultWalkShape, shape64 = kDefaultWalkShape;
+    struct ShapeChoice {
+        int bucket;    // floor(log2(n))
+        double theta;
+        int shape;
+    };
+    std::vector<ShapeChoice> shape_cache;
+    int forced_shape = -1;          // the autotuner's candidate while it times it
 
     // host-buffer stepping: device copies, and a side stream that reads the positions back while
     // the last step's tree and walk run
@@ -292,6 +300,13 @@ void free_spans(nbody_ctx *c)
     c->span_n = c->span_pool_cap = c->span_tmp_warps = 0;
 }
 
+// FP32 contexts without quadrupoles keep FP64 sums in the tree instead of FP64 means (the FP32
+// walk reads FP32 centres of mass only); FP64 contexts and quadrupole terms keep the means.
+bool sums_moments(const nbody_ctx *c)
+{
+    return !is_fp64(c->p.precision) && (c->p.flags & NBODY_FLAG_QUADRUPOLE) == 0;
+}
+
 // Whether the FP32 walk of this context runs the shared far walk of the spans: single systems
 // with the per-body acceptance test and monopole cells.
 bool use_spans(const nbody_ctx *c)
@@ -300,16 +315,57 @@ bool use_spans(const nbody_ctx *c)
            (c->p.flags & (NBODY_FLAG_GROUP_MAC | NBODY_FLAG_CELL_GROUPS | NBODY_FLAG_QUADRUPOLE)) == 0;
 }
 
+// Whether launch shape k changes this context's walk (the autotuner times only those): FP64
+// walks and the flagged FP32 forms take the warps (threads) per block of shapes 0..2; the
+// per-body FP32 walk all shapes, less the spans in a forest or with cell-following groups.
+bool shape_applies(const nbody_ctx *c, int k)
+{
+    if (k < 0 || k >= kWalkShapes) return false;
+    if (k < 3) return true;
+    if (is_fp64(c->p.precision)) return false;
+    if (c->p.flags & (NBODY_FLAG_GROUP_MAC | NBODY_FLAG_QUADRUPOLE)) return false;
+    if (c->n_sys || (c->p.flags & NBODY_FLAG_CELL_GROUPS)) return k == 6 || k == 7;
+    return true;
+}
+
+int size_bucket(int64_t n)
+{
+    int b = 0;
+    while (n > 1) {
+        n >>= 1;
+        ++b;
+    }
+    return b;
+}
+
+// The walk's launch shape for n bodies: the autotuner's candidate while it times one, else its
+// choice for this (N bucket, theta), else the context's shape.
+int walk_shape_for(const nbody_ctx *c, int64_t n)
+{
+    if (c->forced_shape >= 0) return c->forced_shape;
+    const int b = size_bucket(n);
+    for (const auto &e : c->shape_cache)
+        if (e.bucket == b && e.theta == c->p.theta) return e.shape;
+    return is_fp64(c->p.precision) ? c->shape64 : c->shape32;
+}
+
+// Groups that follow the tree's cells: the flags, or (per-body FP32 walks) the launch shape.
+bool cell_groups_for(const nbody_ctx *c, int64_t n)
+{
+    if (is_fp64(c->p.precision)) return false;
+    return cell_groups(c) || walk_shape32(walk_shape_for(c, n)).cell_groups;
+}
+
 // Span scratch for n bodies (grown on demand; never inside a captured forest step).  The pool
 // holds the spans' far lists and frontiers: about 4 / theta^2 node indices per body (clamped to
 // 8 .. 48), plenty at the benchmark's theta; a span that finds no room walks from the root.
 nbody_status ensure_spans(nbody_ctx *c, int n)
 {
-    const int64_t spans = ((int64_t)n + kSpanBodies - 1) / kSpanBodies;
+    const int64_t spans = ((int64_t)n + kSpanMinBodies - 1) / kSpanMinBodies;
     const double th = std::max(c->p.theta, 0.05);
     const int64_t per_body = std::min<int64_t>(48, std::max<int64_t>(8, (int64_t)(4.0 / (th * th))));
     const int64_t pool = std::max<int64_t>(1024, per_body * n);
-    const int64_t warps = span_far_warps(n);
+    const int64_t warps = span_far_warps(n, kSpanMinBodies);
     if (spans <= c->span_n && pool <= c->span_pool_cap && warps <= c->span_tmp_warps)
         return NBODY_OK;
     free_spans(c);
@@ -444,9 +500,14 @@ nbody_status build(nbody_ctx *c, const double *pos, const double *mass, int n,
     c->na.d_nn = c->node_off + n;
     launch_emit_nodes(c->keys, n, one, c->node_off, c->na, c->err, s);
     launch_level_order(c->na, s);
-    launch_moments(c->keys, max_level, c->sbody64, c->box, c->tab, one, c->p.G, c->na, s);
-    if (group) launch_group_nodes(c->na, c->box, c->tab, one, c->p.G, c->gn, s);
-    if (group && cell_groups(c)) {
+    if (sums_moments(c)) {
+        launch_moments_sums(c->keys, max_level, c->sbody64, one, c->na, s);
+        launch_group_nodes_sums(c->na, c->sbody32, c->box, c->tab, one, c->p.G, c->gn, s);
+    } else {
+        launch_moments(c->keys, max_level, c->sbody64, c->box, c->tab, one, c->p.G, c->na, s);
+        if (group) launch_group_nodes(c->na, c->box, c->tab, one, c->p.G, c->gn, s);
+    }
+    if (group && cell_groups_for(c, n)) {
         CK(cudaMemsetAsync(c->cgroups_n, 0, sizeof(unsigned), s));
         launch_cell_groups(c->na, c->node_off, one, n, 32, c->cgroups, c->cgroups_n, c->cap + 1,
                            c->err, s);
@@ -485,7 +546,9 @@ nbody_status walk(nbody_ctx *c, int n, double *acc, double *vel, double h)
     a.d_ngroups = nullptr;
     a.roots = c->roots;
     a.work = c->work;
-    if (!is_fp64(c->p.precision) && cell_groups(c)) {
+    const int shape = walk_shape_for(c, n);
+    const bool cells = cell_groups_for(c, n);
+    if (cells) {
         a.groups = c->cgroups;
         a.n_groups = (int)std::min<int64_t>(c->cap + 1, INT32_MAX);
         a.d_ngroups = c->cgroups_n;
@@ -501,8 +564,11 @@ nbody_status walk(nbody_ctx *c, int n, double *acc, double *vel, double h)
     a.span_off = a.span_pool = a.span_tmp = nullptr;
     a.span_next = nullptr;
     a.span_pool_cap = 0;
-    if (use_spans(c)) {
+    a.span_bodies = 0;
+    const int span = walk_shape32(shape).span_bodies;
+    if (use_spans(c) && !cells && span > 0) {
         CKS(ensure_spans(c, n));
+        a.span_bodies = span;
         a.span_meta = c->span_meta;
         a.span_off = c->span_off;
         a.span_pool = c->span_pool;
@@ -510,8 +576,7 @@ nbody_status walk(nbody_ctx *c, int n, double *acc, double *vel, double h)
         a.span_tmp = c->span_tmp;
         a.span_next = c->span_next;
     }
-    launch_walk(c->p.precision, a, is_fp64(c->p.precision) ? c->shape64 : c->shape32,
-                c->stream);
+    launch_walk(c->p.precision, a, shape, c->stream);
     record(c, 4);
     CKS(check_launch(c, "walk"));
     c->n_forces = n;
@@ -549,10 +614,16 @@ nbody_status forest_build(nbody_ctx *c, double *pos, const double *mass, double 
     c->na.d_nn = c->nn;
     launch_emit_nodes(c->keys, n, ss, c->node_off, c->na, c->err, s);
     launch_level_order(c->na, s);
-    launch_moments(c->keys, kMaxLevel, c->sbody64, c->box, c->tab, ss, c->p.G, c->na, s);
-    if (!is_fp64(c->p.precision)) launch_group_nodes(c->na, c->box, c->tab, ss, c->p.G, c->gn, s);
+    if (sums_moments(c)) {
+        launch_moments_sums(c->keys, kMaxLevel, c->sbody64, ss, c->na, s);
+        launch_group_nodes_sums(c->na, c->sbody32, c->box, c->tab, ss, c->p.G, c->gn, s);
+    } else {
+        launch_moments(c->keys, kMaxLevel, c->sbody64, c->box, c->tab, ss, c->p.G, c->na, s);
+        if (!is_fp64(c->p.precision))
+            launch_group_nodes(c->na, c->box, c->tab, ss, c->p.G, c->gn, s);
+    }
     launch_roots(c->na, c->node_off, ss, c->roots, s);
-    if (!is_fp64(c->p.precision) && cell_groups(c)) {
+    if (cell_groups_for(c, n)) {
         CK(cudaMemsetAsync(c->cgroups_n, 0, sizeof(unsigned), s));
         launch_cell_groups(c->na, c->node_off, ss, n, 32, c->cgroups, c->cgroups_n, c->cap + 1,
                            c->err, s);
@@ -956,7 +1027,23 @@ nbody_status nbody_get_moments(nbody_ctx *c, double *h_out, int64_t cap_nodes)
     if (nn == 0) return NBODY_OK;
     std::vector<D4> m((size_t)nn);
     CK(cudaStreamSynchronize(c->stream));
-    CK(cudaMemcpy(m.data(), c->na.com64, sizeof(D4) * nn, cudaMemcpyDeviceToHost));
+    if (sums_moments(c)) {
+        // the tree holds FP64 sums in level order: centre of mass = sums / mass
+        std::vector<D4> sm((size_t)nn);
+        std::vector<int> inv((size_t)nn);
+        CK(cudaMemcpy(sm.data(), c->na.com_lo, sizeof(D4) * nn, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(inv.data(), c->na.inv, sizeof(int) * nn, cudaMemcpyDeviceToHost));
+        for (int64_t b = 0; b < nn; ++b) {
+            const D4 &q = sm[(size_t)b];
+            D4 &o = m[(size_t)inv[(size_t)b]];
+            o.w = q.w;
+            o.x = q.x / q.w;
+            o.y = q.y / q.w;
+            o.z = q.z / q.w;
+        }
+    } else {
+        CK(cudaMemcpy(m.data(), c->na.com64, sizeof(D4) * nn, cudaMemcpyDeviceToHost));
+    }
     for (int64_t j = 0; j < nn; ++j) {
         h_out[4 * j] = m[j].w;
         h_out[4 * j + 1] = m[j].x;
@@ -1028,22 +1115,26 @@ nbody_status nbody_autotune(nbody_ctx *c, const double *d_pos, const double *d_m
     CKS(check_n(c, n));
     if (n > 0 && (!d_pos || !d_mass)) return fail(c, NBODY_EINVAL, "null pointer");
     int &shape = is_fp64(c->p.precision) ? c->shape64 : c->shape32;
+    if (h_ms)
+        for (int k = 0; k < kWalkShapes; ++k) h_ms[k] = 0.f;
     if (n == 0) {
         if (chosen) *chosen = shape;
         return NBODY_OK;
     }
     const bool timing = c->timing;
     c->timing = false;
+    // one tree for every candidate, with the cell-following groups when a candidate uses them
+    c->forced_shape = shape_applies(c, 7) ? 7 : shape;
     nbody_status st = c->n_sys ? forest_build(c, const_cast<double *>(d_pos), d_mass)
-                               : build(c, d_pos, d_mass, (int)n,
-                                                                        false);
-    float ms[kWalkShapes] = {0.f, 0.f, 0.f};
+                               : build(c, d_pos, d_mass, (int)n, false);
+    float ms[kWalkShapes] = {};
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (st == NBODY_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
         st = fail(c, NBODY_ECUDA, "event creation failed");
     const int reps = 3;
     for (int k = 0; k < kWalkShapes && st == NBODY_OK; ++k) {
-        shape = k;
+        if (!shape_applies(c, k)) continue;
+        c->forced_shape = k;
         st = walk(c, (int)n, c->acc, nullptr, 0.0);  // warm-up of this shape
         if (st == NBODY_OK && cudaEventRecord(e0, c->stream) != cudaSuccess)
             st = fail(c, NBODY_ECUDA, "event record failed");
@@ -1054,18 +1145,25 @@ nbody_status nbody_autotune(nbody_ctx *c, const double *d_pos, const double *d_m
             st = fail(c, NBODY_ECUDA, "timing the walk failed");
         ms[k] /= (float)reps;
     }
+    c->forced_shape = -1;
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     c->timing = timing;
     c->acc_n = -1;  // the walks above overwrote the kept acceleration
-    if (st != NBODY_OK) {
-        shape = kDefaultWalkShape;
-        return st;
-    }
-    int best = 0;
-    for (int k = 1; k < kWalkShapes; ++k)
-        if (ms[k] < ms[best]) best = k;
+    if (st != NBODY_OK) return st;
+    int best = -1;
+    for (int k = 0; k < kWalkShapes; ++k)
+        if (shape_applies(c, k) && (best < 0 || ms[k] < ms[best])) best = k;
     shape = best;
+    // kept for this size bucket and theta; other sizes use it too until tuned themselves
+    const int b = size_bucket(n);
+    bool found = false;
+    for (auto &e : c->shape_cache)
+        if (e.bucket == b && e.theta == c->p.theta) {
+            e.shape = best;
+            found = true;
+        }
+    if (!found) c->shape_cache.push_back({b, c->p.theta, best});
     if (c->gexec) {  // a captured forest step holds the old shape
         cudaGraphExecDestroy(c->gexec);
         c->gexec = nullptr;
@@ -1081,6 +1179,7 @@ nbody_status nbody_set_walk_shape(nbody_ctx *c, int32_t shape)
     if (!c) return NBODY_EINVAL;
     if (shape < 0 || shape >= kWalkShapes) return fail(c, NBODY_EINVAL, "shape %d", (int)shape);
     (is_fp64(c->p.precision) ? c->shape64 : c->shape32) = shape;
+    c->shape_cache.clear();  // an explicit shape replaces the tuned choices
     if (c->gexec) {
         cudaGraphExecDestroy(c->gexec);
         c->gexec = nullptr;

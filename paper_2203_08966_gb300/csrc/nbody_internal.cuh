@@ -231,6 +231,15 @@ int layout_scan_len(int64_t n_nodes);
 // mass relative to its system's origin and its level's FP32 threshold are made here.
 void launch_group_nodes(const NodeArrays &na, const Box *box, const LevelTables *tab,
                         const Systems &ss, double G, GroupNode *gn, cudaStream_t s);
+// FP32 contexts without quadrupoles: leaf FP64 sums (sum m x, sum m y, sum m z, sum m) in
+// com_lo, the level-order child / body ranges in lo_child (w = body count of a leaf), child masks,
+// then the cells' sums level by level up to the roots (no com64, wn unchanged).
+void launch_moments_sums(const uint64_t *keys, int max_level, const D4 *sbody64,
+                         const Systems &ss, NodeArrays na, cudaStream_t s);
+// GroupNode records from those sums, written in level order (one FP64 reciprocal per node).
+void launch_group_nodes_sums(const NodeArrays &na, const float4 *sbody32, const Box *box,
+                             const LevelTables *tab, const Systems &ss, double G, GroupNode *gn,
+                             cudaStream_t s);
 // Walk groups that follow the tree: every cell of at most gmax bodies whose parent holds more
 // (consecutive such siblings merged while they fit in gmax), buckets of more than gmax bodies cut
 // into chunks.  (first body, count, system, 0) entries, *ngroups of them (zeroed by the caller);
@@ -339,21 +348,33 @@ struct WalkArgs {
     int64_t span_pool_cap;
     uint32_t *span_tmp;   // per far-walk warp: kSpanFarTmp + 2 kSpanFrTmp words
     unsigned *span_next;  // [0] pool words handed out, [1] span counter (zeroed per launch)
+    int span_bodies;      // bodies per span (a multiple of 32)
     // test aid (nbody_set_walk_limits): stack entries a group walk may use (at most the
     // kernel's capacity) and steps per group or span (at most the node count)
     int stack_limit;
     int64_t step_limit;
 };
-// Spans of the shared far walk: 8 groups of 32 bodies.  A span's far list holds at most
-// kSpanFarTmp nodes and its frontier at most kSpanFrTmp (else its groups walk from the root).
-constexpr int kSpanBodies = 256;
+// Spans of the shared far walk: groups of 32 bodies, span_bodies (128, 256 or 512) per span.  A
+// span's far list holds at most kSpanFarTmp nodes and its frontier at most kSpanFrTmp (else its
+// groups walk from the root).
+constexpr int kSpanMinBodies = 128;
 constexpr int kSpanFarTmp = 8192;
 constexpr int kSpanFrTmp = 2048;
-// Far-walk warps launched (the span_tmp slices needed), for n bodies.
-int span_far_warps(int n);
-// Launch shapes of the walks (see walk_shape_threads); results do not depend on the shape.
-constexpr int kWalkShapes = 3;
+// Far-walk warps launched (the span_tmp slices needed), for n bodies in spans of span_bodies.
+int span_far_warps(int n, int span_bodies);
+// Launch shapes of the walks; results do not depend on the shape.  FP64 walks: shapes 0, 1, 2
+// are 64, 128, 256 threads per block (the others run as 1).  FP32 walks: walk_shape32; the
+// grouped acceptance test and quadrupole cells use only its warps per block, forests neither
+// spans nor (shapes 3..5) anything but shape 1.
+struct WalkShape {
+    int warps;         // warps (groups) per block
+    int span_bodies;   // bodies per span of the shared far walk; 0: every group from the root
+    int buf;           // interaction-buffer entries
+    bool cell_groups;  // groups follow the tree's cells (as NBODY_FLAG_CELL_GROUPS)
+};
+constexpr int kWalkShapes = 8;
 constexpr int kDefaultWalkShape = 1;
+WalkShape walk_shape32(int shape);
 int walk_shape_threads(int precision, int shape);
 cudaError_t walk_prepare();  // one-time function attributes (dynamic shared memory)
 void launch_walk(int precision, const WalkArgs &a, int shape, cudaStream_t s);

@@ -796,14 +796,14 @@ __global__ void __launch_bounds__(kWarps * 32) group_walk32_kernel(WalkArgs a)
 // ------------------------------------------------------------------------------------------
 
 constexpr int kPbStack = 22 * 32;  // at least 32 ranges for each level 1..21 (see above)
-constexpr int kPbF = 64;           // full-group entries
-constexpr int kPbP = 64;           // partial entries: leaves at 0.., cells at ..kPbP-1
 
+// kBuf entries in each interaction buffer (a launch shape: 64 or 96).
+template <int kBuf>
 struct PbSmem {
     uint2 st[kPbStack];   // (first node | (count - 1) << 28, bodies that still need the range)
-    float4 f[kPbF];       // full-group sources, pair-interleaved (put_entry)
-    float4 p[kPbP];       // partial sources, pair-interleaved
-    uint32_t pm[kPbP];    // their body masks
+    float4 f[kBuf];       // full-group sources, pair-interleaved (put_entry)
+    float4 p[kBuf];       // partial sources, pair-interleaved: leaves at 0.., cells at ..kBuf-1
+    uint32_t pm[kBuf];    // their body masks
     float4 mx[32];        // this step's mixed cells (x, y, z, crit), pair-interleaved
 };
 
@@ -854,10 +854,11 @@ __device__ __forceinline__ uint32_t eval_partial(const float4 *__restrict__ p,
     return cnt;
 }
 
-template <bool kKahan, bool kGuard>
-__device__ __forceinline__ void walk_group_pb(const WalkArgs &a, PbSmem &S, int lane, int g0,
-                                              int gcount, int root)
+template <bool kKahan, bool kGuard, int kBuf>
+__device__ __forceinline__ void walk_group_pb(const WalkArgs &a, PbSmem<kBuf> &S, int lane,
+                                              int g0, int gcount, int root)
 {
+    constexpr int kPbF = kBuf, kPbP = kBuf;
     const int i = g0 + lane;
     const int n_nodes = (int)*a.d_nn;
     const unsigned lt = lanemask_lt_w();
@@ -943,7 +944,7 @@ __device__ __forceinline__ void walk_group_pb(const WalkArgs &a, PbSmem &S, int 
     int far_n = -1, fr_n = 0, fr_next = 0;
     const uint32_t *far = nullptr;
     if (a.span_meta && !a.groups) {
-        const int si = g0 / kSpanBodies;
+        const int si = g0 / a.span_bodies;
         const int4 m = a.span_meta[si];
         if (m.x >= 0) {
             far = a.span_pool + a.span_off[si];
@@ -1116,11 +1117,11 @@ __device__ __forceinline__ void walk_group_pb(const WalkArgs &a, PbSmem &S, int 
         write_out(a, i, (double)r.x, (double)r.y, (double)r.z, ufl + npl, ufc + npc);
 }
 
-template <int kWarps, bool kKahan, bool kGuard>
+template <int kWarps, bool kKahan, bool kGuard, int kBuf>
 __global__ void __launch_bounds__(kWarps * 32) pb_walk32_kernel(WalkArgs a)
 {
     extern __shared__ __align__(16) unsigned char pb_smem[];
-    PbSmem &S = reinterpret_cast<PbSmem *>(pb_smem)[threadIdx.x >> 5];
+    PbSmem<kBuf> &S = reinterpret_cast<PbSmem<kBuf> *>(pb_smem)[threadIdx.x >> 5];
     const int lane = threadIdx.x & 31;
     // persistent warps: each takes the next group from the shared counter until none is left
     for (;;) {
@@ -1129,7 +1130,7 @@ __global__ void __launch_bounds__(kWarps * 32) pb_walk32_kernel(WalkArgs a)
         gi = __shfl_sync(kFull, gi, 0);
         int g0, gcount, root;
         if (!group_of(a, (int)gi, g0, gcount, root)) break;  // uniform per warp
-        walk_group_pb<kKahan, kGuard>(a, S, lane, g0, gcount, root);
+        walk_group_pb<kKahan, kGuard, kBuf>(a, S, lane, g0, gcount, root);
         __syncwarp();
     }
 }
@@ -1157,13 +1158,14 @@ __global__ void __launch_bounds__(kWarps * 32) far_walk32_kernel(WalkArgs a)
     uint32_t *tfr = tfar + kSpanFarTmp;   // frontier nodes
     uint32_t *tlev = tfr + kSpanFrTmp;    // their levels
     const int n_nodes = (int)*a.d_nn;
-    const int n_spans = (a.n + kSpanBodies - 1) / kSpanBodies;
+    const int span = a.span_bodies;
+    const int n_spans = (a.n + span - 1) / span;
     for (;;) {
         unsigned si = 0;
         if (lane == 0) si = atomicAdd(a.span_next + 1, 1u);
         si = __shfl_sync(kFull, si, 0);
         if ((int)si >= n_spans) break;
-        const int s0 = (int)si * kSpanBodies, s1 = min(s0 + kSpanBodies, a.n);
+        const int s0 = (int)si * span, s1 = min(s0 + span, a.n);
         float lx = INFINITY, ly = INFINITY, lz = INFINITY;
         float hx = -INFINITY, hy = -INFINITY, hz = -INFINITY;
         for (int b = s0 + lane; b < s1; b += 32) {
@@ -1552,7 +1554,7 @@ void launch_group_variant(const WalkArgs &a, int64_t groups, cudaStream_t s)
         <<<blocks, kWarps * 32, group_smem_bytes<kQuad>() * kWarps, s>>>(a);
 }
 
-template <int kWarps, bool kKahan, bool kGuard>
+template <int kWarps, bool kKahan, bool kGuard, int kBuf>
 int pb_persistent_blocks(int64_t groups)
 {
     static int resident = 0;  // per kernel instance, per process
@@ -1561,29 +1563,37 @@ int pb_persistent_blocks(int64_t groups)
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &per_sm, pb_walk32_kernel<kWarps, kKahan, kGuard>, kWarps * 32,
-            sizeof(PbSmem) * kWarps);
+            &per_sm, pb_walk32_kernel<kWarps, kKahan, kGuard, kBuf>, kWarps * 32,
+            sizeof(PbSmem<kBuf>) * kWarps);
         resident = std::max(1, sms) * std::max(1, per_sm);
     }
     return (int)std::min<int64_t>((groups + kWarps - 1) / kWarps, resident);
 }
 
 constexpr int kFarWarps = 4;       // warps per block of the far walk
-constexpr int kFarBlocksPerSm = 4;
+constexpr int kFarBlocksPerSm = 8;
+
+template <int kWarps, bool kKahan, bool kGuard, int kBuf>
+void launch_pb(const WalkArgs &a, int64_t groups, cudaStream_t s)
+{
+    const int blocks = pb_persistent_blocks<kWarps, kKahan, kGuard, kBuf>(groups);
+    pb_walk32_kernel<kWarps, kKahan, kGuard, kBuf>
+        <<<blocks, kWarps * 32, sizeof(PbSmem<kBuf>) * kWarps, s>>>(a);
+}
 
 template <int kWarps, bool kKahan, bool kGuard>
-void launch_group(const WalkArgs &a, int64_t groups, cudaStream_t s)
+void launch_group(const WalkArgs &a, int64_t groups, int buf, cudaStream_t s)
 {
     const bool quad = a.gq != nullptr;
     if (!a.group_mac && !quad) {
         if (a.span_meta && !a.groups) {
             cudaMemsetAsync(a.span_next, 0, 2 * sizeof(unsigned), s);
-            far_walk32_kernel<kFarWarps><<<span_far_warps(a.n) / kFarWarps, kFarWarps * 32, 0, s>>>(a);
+            far_walk32_kernel<kFarWarps>
+                <<<span_far_warps(a.n, a.span_bodies) / kFarWarps, kFarWarps * 32, 0, s>>>(a);
             count_launches(1);
         }
-        const int blocks = pb_persistent_blocks<kWarps, kKahan, kGuard>(groups);
-        pb_walk32_kernel<kWarps, kKahan, kGuard>
-            <<<blocks, kWarps * 32, sizeof(PbSmem) * kWarps, s>>>(a);
+        if (buf == 96) launch_pb<kWarps, kKahan, kGuard, 96>(a, groups, s);
+        else launch_pb<kWarps, kKahan, kGuard, 64>(a, groups, s);
         return;
     }
     if (a.group_mac) {
@@ -1595,14 +1605,15 @@ void launch_group(const WalkArgs &a, int64_t groups, cudaStream_t s)
 }
 
 template <int kWarps>
-void launch_group(const WalkArgs &a, int64_t groups, bool kahan, bool guard, cudaStream_t s)
+void launch_group(const WalkArgs &a, int64_t groups, bool kahan, bool guard, int buf,
+                  cudaStream_t s)
 {
     if (kahan) {
-        if (guard) launch_group<kWarps, true, true>(a, groups, s);
-        else launch_group<kWarps, true, false>(a, groups, s);
+        if (guard) launch_group<kWarps, true, true>(a, groups, buf, s);
+        else launch_group<kWarps, true, false>(a, groups, buf, s);
     } else {
-        if (guard) launch_group<kWarps, false, true>(a, groups, s);
-        else launch_group<kWarps, false, false>(a, groups, s);
+        if (guard) launch_group<kWarps, false, true>(a, groups, buf, s);
+        else launch_group<kWarps, false, false>(a, groups, buf, s);
     }
 }
 
@@ -1621,9 +1632,14 @@ cudaError_t allow_group_smem_kg()
             cudaFuncSetAttribute(fns[k], cudaFuncAttributeMaxDynamicSharedMemorySize, bytes[k]);
         if (e != cudaSuccess) return e;
     }
-    return cudaFuncSetAttribute((const void *)pb_walk32_kernel<kWarps, kKahan, kGuard>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)(sizeof(PbSmem) * kWarps));
+    cudaError_t e = cudaFuncSetAttribute((const void *)pb_walk32_kernel<kWarps, kKahan, kGuard, 64>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(sizeof(PbSmem<64>) * kWarps));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute((const void *)pb_walk32_kernel<kWarps, kKahan, kGuard, 96>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(sizeof(PbSmem<96>) * kWarps));
+    return e;
 }
 
 template <int kWarps>
@@ -1647,7 +1663,7 @@ void launch_w64(const WalkArgs &a, int64_t groups, bool fast, cudaStream_t s)
 
 }  // namespace
 
-int span_far_warps(int n)
+int span_far_warps(int n, int span_bodies)
 {
     static int sms = 0;
     if (sms == 0) {
@@ -1656,7 +1672,7 @@ int span_far_warps(int n)
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         sms = std::max(1, sms);
     }
-    const int spans = (n + kSpanBodies - 1) / kSpanBodies;
+    const int spans = (n + span_bodies - 1) / std::max(32, span_bodies);
     const int blocks = std::max(1, std::min((spans + kFarWarps - 1) / kFarWarps, sms * kFarBlocksPerSm));
     return blocks * kFarWarps;
 }
@@ -1669,12 +1685,22 @@ cudaError_t walk_prepare()
     return e;
 }
 
+WalkShape walk_shape32(int shape)
+{
+    // warps per block, span of the shared far walk (0: none), interaction buffer entries,
+    // groups that follow the tree's cells
+    static const WalkShape table[kWalkShapes] = {
+        {2, 256, 64, false}, {4, 256, 64, false}, {8, 256, 64, false}, {4, 0, 64, false},
+        {4, 128, 64, false}, {4, 512, 64, false}, {4, 256, 96, false}, {4, 0, 64, true}};
+    if (shape < 0 || shape >= kWalkShapes) shape = kDefaultWalkShape;
+    return table[shape];
+}
+
 int walk_shape_threads(int precision, int shape)
 {
-    static const int group_warps[kWalkShapes] = {2, 4, 8};
-    static const int w64_threads[kWalkShapes] = {64, 128, 256};
+    static const int w64_threads[3] = {64, 128, 256};
     if (shape < 0 || shape >= kWalkShapes) shape = kDefaultWalkShape;
-    return is_fp64(precision) ? w64_threads[shape] : 32 * group_warps[shape];
+    return is_fp64(precision) ? w64_threads[shape < 3 ? shape : 1] : 32 * walk_shape32(shape).warps;
 }
 
 void launch_walk(int precision, const WalkArgs &a, int shape, cudaStream_t s)
@@ -1689,14 +1715,15 @@ void launch_walk(int precision, const WalkArgs &a, int shape, cudaStream_t s)
     if (is_fp64(precision)) {
         const bool fast = precision == NBODY_FP64_FAST;
         if (shape == 0) launch_w64<64>(a, groups, fast, s);
-        else if (shape == 1) launch_w64<128>(a, groups, fast, s);
-        else launch_w64<256>(a, groups, fast, s);
+        else if (shape == 2) launch_w64<256>(a, groups, fast, s);
+        else launch_w64<128>(a, groups, fast, s);
     } else {
         const bool kahan = precision == NBODY_FP32_KAHAN;
+        const WalkShape sh = walk_shape32(shape);
         cudaMemsetAsync(a.work, 0, sizeof(unsigned), s);
-        if (shape == 0) launch_group<2>(a, groups, kahan, guard, s);
-        else if (shape == 1) launch_group<4>(a, groups, kahan, guard, s);
-        else launch_group<8>(a, groups, kahan, guard, s);
+        if (sh.warps == 2) launch_group<2>(a, groups, kahan, guard, sh.buf, s);
+        else if (sh.warps == 8) launch_group<8>(a, groups, kahan, guard, sh.buf, s);
+        else launch_group<4>(a, groups, kahan, guard, sh.buf, s);
     }
     count_launches(1);
 }
