@@ -840,7 +840,7 @@ __device__ __forceinline__ uint32_t eval_partial(const float4 *__restrict__ p,
 {
     uint32_t cnt = 0;
     const uint2 *pm2 = reinterpret_cast<const uint2 *>(pm);
-#pragma unroll 2
+#pragma unroll 4
     for (int k = k0; k < k1; ++k) {
         const float4 a = p[2 * k];
         float4 b = p[2 * k + 1];
