@@ -230,11 +230,11 @@ nbody_status nbody_get_launch_count(int64_t *out);
  * (the same counters); FP64 results are identical in every shape, while the FP32 forms' sums can
  * differ in rounding between shapes that group or buffer the terms differently (3 .. 7).
  * FP64 forms: shapes 0, 1, 2 are 64, 128, 256 threads per block (the other shapes run as 1).
- * FP32 forms (one warp per group of 32 bodies):
+ * FP32 forms (one warp per group of 32 bodies; interaction buffers of 128 entries unless noted):
  *   0, 1, 2  2, 4, 8 warps per block, spans of 256 bodies sharing one walk of the far field
  *   3        4 warps per block, no shared far walk (every group walks from the root)
  *   4, 5     4 warps per block, spans of 128 and 512 bodies
- *   6        4 warps per block, spans of 256 bodies, interaction buffers of 96 entries (not 64)
+ *   6        4 warps per block, spans of 256 bodies, interaction buffers of 64 entries
  *   7        4 warps per block, groups that follow the tree's cells (as NBODY_FLAG_CELL_GROUPS)
  * The grouped acceptance test and quadrupole cells take only the warps per block of a shape;
  * forests and NBODY_FLAG_CELL_GROUPS never share far walks. */
@@ -259,15 +259,19 @@ nbody_status nbody_set_walk_shape(nbody_ctx *c, int32_t shape);
 /* The walk shape in use for the context's precision and its threads per block. */
 nbody_status nbody_get_walk_shape(nbody_ctx *c, int32_t *shape, int32_t *threads_per_block);
 
-/* Test aid with no counterpart in the paper: lowers the walk's resources so that its guards can
- * be exercised.  stack_entries: stack ranges an FP32 group walk may hold (at least 33; the
- * kernels' own capacity when larger; 0 = that capacity); max_steps: steps one group, span or FP64
- * warp may take (0 = no limit beyond the node count).  A walk that reaches either limit stops
- * before any further memory access, its bodies' forces are left incomplete, and the next
- * nbody_sync returns NBODY_ESTACK.  With the defaults, no valid tree reaches them (the stack
- * holds at most 32 ranges per level, a walk at most one step per node).
- * Errors: EINVAL (stack_entries in 1..32, max_steps < 0). */
-nbody_status nbody_set_walk_limits(nbody_ctx *c, int32_t stack_entries, int64_t max_steps);
+/* Test aid with no counterpart in the paper: lowers the walk's resources so that its guards and
+ * its overflow path can be exercised.  stack_entries: stack ranges an FP32 group walk may hold
+ * (at least 33; the kernels' own capacity when larger; 0 = that capacity); max_steps: steps one
+ * group, span or FP64 warp may take (0 = no limit beyond the node count); fast_entries: stack
+ * ranges of the per-body FP32 walk's fast kernel (at least 64; 0 = its 256), past which a group
+ * is handed, untouched, to a second walk with the full stack (its sums are then taken in another
+ * order; its interaction list is the same).  A walk that reaches stack_entries or max_steps
+ * stops before any further memory access, its bodies' forces are left incomplete, and the next
+ * nbody_sync returns NBODY_ESTACK.  With the defaults, no valid tree reaches them (the stack holds
+ * at most 32 ranges per level, a walk at most one step per node).  Errors: EINVAL (stack_entries
+ * in 1..32, max_steps < 0, fast_entries in 1..63). */
+nbody_status nbody_set_walk_limits(nbody_ctx *c, int32_t stack_entries, int64_t max_steps,
+                                   int32_t fast_entries);
 
 /* ---- re-sort from the previous step's order (temporal coherence, §4.4) ---- */
 

@@ -105,7 +105,7 @@ def load_library(path: str = LIB_PATH):
         "nbody_autotune": [vp, vp, vp, i64, vp, vp],
         "nbody_get_walk_shape": [vp, vp, vp],
         "nbody_set_walk_shape": [vp, i32],
-        "nbody_set_walk_limits": [vp, i32, i64],
+        "nbody_set_walk_limits": [vp, i32, i64, i32],
         "nbody_set_sort_mode": [vp, i32],
         "nbody_get_sort_stats": [vp, vp, vp],
         "nbody_measure_fp32_rate": [vp, vp],
@@ -308,10 +308,12 @@ class Context:
     def set_walk_shape(self, shape):
         self._check(self._lib.nbody_set_walk_shape(self._h, int(shape)), "nbody_set_walk_shape")
 
-    def set_walk_limits(self, stack_entries=0, max_steps=0):
+    def set_walk_limits(self, stack_entries=0, max_steps=0, fast_entries=0):
         """Test aid: lowers the walk's stack entries / steps (0 = the defaults); a walk that
-        reaches a limit stops and the next sync() raises NBODY_ESTACK."""
-        self._check(self._lib.nbody_set_walk_limits(self._h, int(stack_entries), int(max_steps)),
+        reaches a limit stops and the next sync() raises NBODY_ESTACK.  fast_entries lowers the
+        stack of the FP32 walk's fast kernel (deeper groups go to the full-stack walk)."""
+        self._check(self._lib.nbody_set_walk_limits(self._h, int(stack_entries), int(max_steps),
+                                                    int(fast_entries)),
                     "nbody_set_walk_limits")
 
     def walk_shape(self):

@@ -77,6 +77,10 @@ struct nbody_ctx {
     // walk limits (nbody_set_walk_limits; the defaults never bind) and the finite-input check
     int stack_limit = 1 << 30;
     int64_t step_limit = INT64_MAX;
+    int fast_stack_limit = 1 << 30;
+    int4 *overflow = nullptr;       // FP32 per-body walk: groups handed to the full-stack walk
+    unsigned *n_overflow = nullptr;
+    int64_t overflow_cap = 0;
     int *chk = nullptr;             // device word: kErrInput when NBODY_FLAG_CHECK_FINITE fails
     float *dscratch = nullptr;      // FP32 direct sum: sources + partial sums (grown on demand)
     int64_t dscratch_cap = 0;       // floats
@@ -380,6 +384,21 @@ nbody_status ensure_spans(nbody_ctx *c, int n)
     return NBODY_OK;
 }
 
+// The FP32 per-body walk's overflow list: one entry per group of the capacity (first FP32 walk
+// of a single system; forests at creation, since their steps may be captured).
+nbody_status ensure_overflow(nbody_ctx *c)
+{
+    const int64_t need = c->n_sys ? (int64_t)c->n_groups : (c->cap + 31) / 32;
+    if (is_fp64(c->p.precision) || (c->overflow && c->overflow_cap >= need)) return NBODY_OK;
+    dfree(c->overflow);
+    dfree(c->n_overflow);
+    c->overflow_cap = 0;
+    CK(dalloc(&c->overflow, (size_t)std::max<int64_t>(need, c->cap + 1)));
+    CK(dalloc(&c->n_overflow, 1));
+    c->overflow_cap = std::max<int64_t>(need, c->cap + 1);
+    return NBODY_OK;
+}
+
 nbody_status check_launch(nbody_ctx *c, const char *what)
 {
     cudaError_t e = cudaGetLastError();
@@ -560,6 +579,10 @@ nbody_status walk(nbody_ctx *c, int n, double *acc, double *vel, double h)
     a.gq = !is_fp64(c->p.precision) ? c->na.gq : nullptr;
     a.stack_limit = c->stack_limit;
     a.step_limit = c->step_limit;
+    a.fast_stack_limit = c->fast_stack_limit;
+    CKS(ensure_overflow(c));
+    a.overflow = c->overflow;
+    a.n_overflow = c->n_overflow;
     a.span_meta = nullptr;
     a.span_off = a.span_pool = a.span_tmp = nullptr;
     a.span_next = nullptr;
@@ -732,7 +755,7 @@ nbody_status nbody_create(nbody_ctx **out, int64_t n_capacity, const nbody_param
         CK(dalloc(&c->err, 1));
         CK(dalloc(&c->cgroups, cap + 1));
         CK(dalloc(&c->cgroups_n, 1));
-        CK(dalloc(&c->work, 1));
+        CK(dalloc(&c->work, 2));
         CK(dalloc(&c->chk, 1));
         CK(cudaMemset(c->err, 0, sizeof(int)));
         CK(cudaMallocHost((void **)&c->h_word, (2 + kOrderStats) * sizeof(uint32_t)));
@@ -777,6 +800,8 @@ nbody_status nbody_destroy(nbody_ctx *c)
     dfree(c->cgroups_n);
     dfree(c->work);
     dfree(c->chk);
+    dfree(c->overflow);
+    dfree(c->n_overflow);
     free_spans(c);
     dfree(c->sys);
     dfree(c->sys_start);
@@ -1196,14 +1221,18 @@ nbody_status nbody_get_walk_shape(nbody_ctx *c, int32_t *shape, int32_t *threads
     return NBODY_OK;
 }
 
-nbody_status nbody_set_walk_limits(nbody_ctx *c, int32_t stack_entries, int64_t max_steps)
+nbody_status nbody_set_walk_limits(nbody_ctx *c, int32_t stack_entries, int64_t max_steps,
+                                   int32_t fast_entries)
 {
     if (!c) return NBODY_EINVAL;
     if (stack_entries != 0 && stack_entries < 33)
         return fail(c, NBODY_EINVAL, "stack_entries %d: 0 or at least 33", (int)stack_entries);
     if (max_steps < 0) return fail(c, NBODY_EINVAL, "max_steps < 0");
+    if (fast_entries != 0 && fast_entries < 64)
+        return fail(c, NBODY_EINVAL, "fast_entries %d: 0 or at least 64", (int)fast_entries);
     c->stack_limit = stack_entries == 0 ? (1 << 30) : stack_entries;
     c->step_limit = max_steps == 0 ? INT64_MAX : max_steps;
+    c->fast_stack_limit = fast_entries == 0 ? (1 << 30) : fast_entries;
     if (c->gexec) {  // a captured forest step holds the old limits
         cudaGraphExecDestroy(c->gexec);
         c->gexec = nullptr;
@@ -1325,6 +1354,7 @@ nbody_status nbody_forest_create(nbody_ctx **out, int32_t n_systems, const int64
         CKS(ensure_nodes(c, 4 * n + 22 * (int64_t)S + 1024));
         CKS(ensure_quad(c));
         CKS(ensure_order(c));  // the re-sort's scratch: never allocated inside a (captured) step
+        CKS(ensure_overflow(c));
         if (c->na.cap > kMaxGroupNodes)
             return fail(c, NBODY_EINVAL, "forest of %lld bodies exceeds the node index range",
                         (long long)n);

@@ -338,7 +338,7 @@ struct WalkArgs {
     const double *q64;    // quadrupoles (pre-order) for the FP64 walk, null without them
     const float4 *gq;     // G * quadrupoles (level order) for the FP32 walk, null without them
     const unsigned *d_ngroups;  // groups built on the device: their count (n_groups = capacity)
-    unsigned *work;       // FP32 walk: group counter of the persistent warps (zeroed per launch)
+    unsigned *work;       // FP32 walk: group counters of the persistent warps (2, zeroed per launch)
     // spans of kSpanBodies consecutive bodies sharing one far walk (single systems, per-body
     // test, monopole cells); span_meta null: every group walks from the root
     int4 *span_meta;      // per span: far count (-1: walk from the root), frontier count, far
@@ -353,6 +353,11 @@ struct WalkArgs {
     // kernel's capacity) and steps per group or span (at most the node count)
     int stack_limit;
     int64_t step_limit;
+    int fast_stack_limit; // test aid: stack entries of the fast per-body walk (at least 64)
+    // FP32 per-body walk: groups whose stack outgrew the fast walk's, walked afterwards with the
+    // full stack ((first body, count, system, 0), as many entries as groups); null: none
+    int4 *overflow;
+    unsigned *n_overflow;
 };
 // Spans of the shared far walk: groups of 32 bodies, span_bodies (128, 256 or 512) per span.  A
 // span's far list holds at most kSpanFarTmp nodes and its frontier at most kSpanFrTmp (else its
@@ -369,7 +374,7 @@ int span_far_warps(int n, int span_bodies);
 struct WalkShape {
     int warps;         // warps (groups) per block
     int span_bodies;   // bodies per span of the shared far walk; 0: every group from the root
-    int buf;           // interaction-buffer entries
+    int buf;           // interaction-buffer entries (64 or 128)
     bool cell_groups;  // groups follow the tree's cells (as NBODY_FLAG_CELL_GROUPS)
 };
 constexpr int kWalkShapes = 8;

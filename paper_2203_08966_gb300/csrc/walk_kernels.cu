@@ -796,11 +796,15 @@ __global__ void __launch_bounds__(kWarps * 32) group_walk32_kernel(WalkArgs a)
 // ------------------------------------------------------------------------------------------
 
 constexpr int kPbStack = 22 * 32;  // at least 32 ranges for each level 1..21 (see above)
+// The walk runs with a stack of kPbFast entries (walks rarely go deeper: the two-cluster
+// benchmark peaks near 120), which leaves room for more warps per SM.  A group whose stack would
+// overflow it writes nothing and goes to the overflow list, walked afterwards with kPbStack.
+constexpr int kPbFast = 8 * 32;
 
-// kBuf entries in each interaction buffer (a launch shape: 64 or 96).
-template <int kBuf>
+// kBuf entries in each interaction buffer (a launch shape: 128 or 64); kStackN stack entries.
+template <int kBuf, int kStackN>
 struct PbSmem {
-    uint2 st[kPbStack];   // (first node | (count - 1) << 28, bodies that still need the range)
+    uint2 st[kStackN];    // (first node | (count - 1) << 28, bodies that still need the range)
     float4 f[kBuf];       // full-group sources, pair-interleaved (put_entry)
     float4 p[kBuf];       // partial sources, pair-interleaved: leaves at 0.., cells at ..kBuf-1
     uint32_t pm[kBuf];    // their body masks
@@ -854,9 +858,9 @@ __device__ __forceinline__ uint32_t eval_partial(const float4 *__restrict__ p,
     return cnt;
 }
 
-template <bool kKahan, bool kGuard, int kBuf>
-__device__ __forceinline__ void walk_group_pb(const WalkArgs &a, PbSmem<kBuf> &S, int lane,
-                                              int g0, int gcount, int root)
+template <bool kKahan, bool kGuard, int kBuf, int kStackN>
+__device__ __forceinline__ void walk_group_pb(const WalkArgs &a, PbSmem<kBuf, kStackN> &S,
+                                              int lane, int g0, int gcount, int root, int sys)
 {
     constexpr int kPbF = kBuf, kPbP = kBuf;
     const int i = g0 + lane;
@@ -972,11 +976,17 @@ __device__ __forceinline__ void walk_group_pb(const WalkArgs &a, PbSmem<kBuf> &S
 
     // every node is popped at most once per group, so more steps than nodes means a malformed
     // tree: stop with the error word set rather than loop
-    const int stack_cap = min(kPbStack, a.stack_limit);
+    // the fast kernel hands a group that would overflow its stack to the overflow walk (the
+    // test aid lowers that point); the full-stack walk reports it (cannot happen: stack bound)
+    constexpr bool kFast = kStackN < kPbStack;
+    const int stack_cap = min(kStackN, kFast ? min(a.stack_limit, a.fast_stack_limit)
+                                             : a.stack_limit);
     int64_t steps_left = min((int64_t)n_nodes, a.step_limit);
+    bool handed = false;  // the group went to the overflow walk: write nothing
     while (sp > 0 || fr_next < fr_n) {
-        if (sp > stack_cap - 32 || --steps_left < 0) {  // cannot happen (see the stack bound)
-            if (lane == 0) atomicOr(a.err, kErrStack);
+        if (sp > stack_cap - 32 || --steps_left < 0) {
+            handed = kFast && a.overflow && sp > stack_cap - 32;
+            if (!handed && lane == 0) atomicOr(a.err, kErrStack);  // cannot happen
             break;
         }
         __syncwarp();
@@ -1111,17 +1121,21 @@ __device__ __forceinline__ void walk_group_pb(const WalkArgs &a, PbSmem<kBuf> &S
             }
         }
     }
+    if (handed) {  // nothing written: the overflow walk does this group
+        if (lane == 0) a.overflow[atomicAdd(a.n_overflow, 1u)] = make_int4(g0, gcount, sys, 0);
+        return;
+    }
     drain();
     const float3 r = acc.result();
     if (lane < gcount)
         write_out(a, i, (double)r.x, (double)r.y, (double)r.z, ufl + npl, ufc + npc);
 }
 
-template <int kWarps, bool kKahan, bool kGuard, int kBuf>
+template <int kWarps, bool kKahan, bool kGuard, int kBuf, int kStackN>
 __global__ void __launch_bounds__(kWarps * 32) pb_walk32_kernel(WalkArgs a)
 {
     extern __shared__ __align__(16) unsigned char pb_smem[];
-    PbSmem<kBuf> &S = reinterpret_cast<PbSmem<kBuf> *>(pb_smem)[threadIdx.x >> 5];
+    PbSmem<kBuf, kStackN> &S = reinterpret_cast<PbSmem<kBuf, kStackN> *>(pb_smem)[threadIdx.x >> 5];
     const int lane = threadIdx.x & 31;
     // persistent warps: each takes the next group from the shared counter until none is left
     for (;;) {
@@ -1130,7 +1144,8 @@ __global__ void __launch_bounds__(kWarps * 32) pb_walk32_kernel(WalkArgs a)
         gi = __shfl_sync(kFull, gi, 0);
         int g0, gcount, root;
         if (!group_of(a, (int)gi, g0, gcount, root)) break;  // uniform per warp
-        walk_group_pb<kKahan, kGuard, kBuf>(a, S, lane, g0, gcount, root);
+        const int sys = a.groups ? a.groups[gi].z : 0;
+        walk_group_pb<kKahan, kGuard, kBuf, kStackN>(a, S, lane, g0, gcount, root, sys);
         __syncwarp();
     }
 }
@@ -1554,7 +1569,7 @@ void launch_group_variant(const WalkArgs &a, int64_t groups, cudaStream_t s)
         <<<blocks, kWarps * 32, group_smem_bytes<kQuad>() * kWarps, s>>>(a);
 }
 
-template <int kWarps, bool kKahan, bool kGuard, int kBuf>
+template <int kWarps, bool kKahan, bool kGuard, int kBuf, int kStackN>
 int pb_persistent_blocks(int64_t groups)
 {
     static int resident = 0;  // per kernel instance, per process
@@ -1563,8 +1578,8 @@ int pb_persistent_blocks(int64_t groups)
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &per_sm, pb_walk32_kernel<kWarps, kKahan, kGuard, kBuf>, kWarps * 32,
-            sizeof(PbSmem<kBuf>) * kWarps);
+            &per_sm, pb_walk32_kernel<kWarps, kKahan, kGuard, kBuf, kStackN>, kWarps * 32,
+            sizeof(PbSmem<kBuf, kStackN>) * kWarps);
         resident = std::max(1, sms) * std::max(1, per_sm);
     }
     return (int)std::min<int64_t>((groups + kWarps - 1) / kWarps, resident);
@@ -1573,12 +1588,24 @@ int pb_persistent_blocks(int64_t groups)
 constexpr int kFarWarps = 4;       // warps per block of the far walk
 constexpr int kFarBlocksPerSm = 8;
 
+// The walk with the fast stack, then the overflow walk of the groups it handed on (a launch that
+// finds an empty list and returns at once, unless a group was that deep).
 template <int kWarps, bool kKahan, bool kGuard, int kBuf>
 void launch_pb(const WalkArgs &a, int64_t groups, cudaStream_t s)
 {
-    const int blocks = pb_persistent_blocks<kWarps, kKahan, kGuard, kBuf>(groups);
-    pb_walk32_kernel<kWarps, kKahan, kGuard, kBuf>
-        <<<blocks, kWarps * 32, sizeof(PbSmem<kBuf>) * kWarps, s>>>(a);
+    const int blocks = pb_persistent_blocks<kWarps, kKahan, kGuard, kBuf, kPbFast>(groups);
+    pb_walk32_kernel<kWarps, kKahan, kGuard, kBuf, kPbFast>
+        <<<blocks, kWarps * 32, sizeof(PbSmem<kBuf, kPbFast>) * kWarps, s>>>(a);
+    WalkArgs o = a;
+    o.groups = a.overflow;
+    o.n_groups = (int)std::min<int64_t>(groups, INT32_MAX);
+    o.d_ngroups = a.n_overflow;
+    o.overflow = nullptr;
+    o.work = a.work + 1;
+    const int ob = pb_persistent_blocks<4, kKahan, kGuard, 64, kPbStack>(groups);
+    pb_walk32_kernel<4, kKahan, kGuard, 64, kPbStack>
+        <<<ob, 4 * 32, sizeof(PbSmem<64, kPbStack>) * 4, s>>>(o);
+    count_launches(1);
 }
 
 template <int kWarps, bool kKahan, bool kGuard>
@@ -1592,7 +1619,7 @@ void launch_group(const WalkArgs &a, int64_t groups, int buf, cudaStream_t s)
                 <<<span_far_warps(a.n, a.span_bodies) / kFarWarps, kFarWarps * 32, 0, s>>>(a);
             count_launches(1);
         }
-        if (buf == 96) launch_pb<kWarps, kKahan, kGuard, 96>(a, groups, s);
+        if (buf == 128) launch_pb<kWarps, kKahan, kGuard, 128>(a, groups, s);
         else launch_pb<kWarps, kKahan, kGuard, 64>(a, groups, s);
         return;
     }
@@ -1632,13 +1659,18 @@ cudaError_t allow_group_smem_kg()
             cudaFuncSetAttribute(fns[k], cudaFuncAttributeMaxDynamicSharedMemorySize, bytes[k]);
         if (e != cudaSuccess) return e;
     }
-    cudaError_t e = cudaFuncSetAttribute((const void *)pb_walk32_kernel<kWarps, kKahan, kGuard, 64>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(sizeof(PbSmem<64>) * kWarps));
+    cudaError_t e = cudaFuncSetAttribute(
+        (const void *)pb_walk32_kernel<kWarps, kKahan, kGuard, 64, kPbFast>,
+        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(PbSmem<64, kPbFast>) * kWarps));
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute((const void *)pb_walk32_kernel<kWarps, kKahan, kGuard, 96>,
+        e = cudaFuncSetAttribute(
+            (const void *)pb_walk32_kernel<kWarps, kKahan, kGuard, 128, kPbFast>,
+            cudaFuncAttributeMaxDynamicSharedMemorySize,
+            (int)(sizeof(PbSmem<128, kPbFast>) * kWarps));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute((const void *)pb_walk32_kernel<4, kKahan, kGuard, 64, kPbStack>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(sizeof(PbSmem<96>) * kWarps));
+                                 (int)(sizeof(PbSmem<64, kPbStack>) * 4));
     return e;
 }
 
@@ -1690,8 +1722,8 @@ WalkShape walk_shape32(int shape)
     // warps per block, span of the shared far walk (0: none), interaction buffer entries,
     // groups that follow the tree's cells
     static const WalkShape table[kWalkShapes] = {
-        {2, 256, 64, false}, {4, 256, 64, false}, {8, 256, 64, false}, {4, 0, 64, false},
-        {4, 128, 64, false}, {4, 512, 64, false}, {4, 256, 96, false}, {4, 0, 64, true}};
+        {2, 256, 128, false}, {4, 256, 128, false}, {8, 256, 128, false}, {4, 0, 128, false},
+        {4, 128, 128, false}, {4, 512, 128, false}, {4, 256, 64, false},  {4, 0, 128, true}};
     if (shape < 0 || shape >= kWalkShapes) shape = kDefaultWalkShape;
     return table[shape];
 }
@@ -1720,7 +1752,8 @@ void launch_walk(int precision, const WalkArgs &a, int shape, cudaStream_t s)
     } else {
         const bool kahan = precision == NBODY_FP32_KAHAN;
         const WalkShape sh = walk_shape32(shape);
-        cudaMemsetAsync(a.work, 0, sizeof(unsigned), s);
+        cudaMemsetAsync(a.work, 0, 2 * sizeof(unsigned), s);
+        if (a.n_overflow) cudaMemsetAsync(a.n_overflow, 0, sizeof(unsigned), s);
         if (sh.warps == 2) launch_group<2>(a, groups, kahan, guard, sh.buf, s);
         else if (sh.warps == 8) launch_group<8>(a, groups, kahan, guard, sh.buf, s);
         else launch_group<4>(a, groups, kahan, guard, sh.buf, s);

@@ -59,7 +59,7 @@ def test_null_context_is_rejected_without_gpu(lib_path):
     lib = nb.load_library(lib_path)
     assert lib.nbody_destroy(None) == 1
     assert lib.nbody_sync(None) == 1
-    assert lib.nbody_set_walk_limits(None, 0, 0) == 1
+    assert lib.nbody_set_walk_limits(None, 0, 0, 0) == 1
     assert lib.nbody_create(None, 10, None, None) == 1
 
 

@@ -75,8 +75,31 @@ def test_fp64_walk_step_limit_reports_estack_then_recovers():
 
 def test_walk_limits_reject_bad_arguments():
     with nb.Context(16) as ctx:
-        for bad in ((1, 0), (32, 0), (0, -1)):
+        for bad in ((1, 0, 0), (32, 0, 0), (0, -1, 0), (0, 0, 63), (0, 0, 1)):
             _expect(EINVAL, lambda: ctx.set_walk_limits(*bad))
+
+
+@pytest.mark.parametrize("prec", [nb.FP32, nb.FP32_KAHAN])
+def test_stack_overflow_walk_keeps_the_lists(prec):
+    """The per-body walk's fast kernel gets a stack of 64 ranges instead of 256, so that deep
+    groups (theta 0.3) are handed to the full-stack walk: every body keeps its interaction list
+    (identical counters); those groups' sums are taken in another order (rounding only)."""
+    pos, _, mass = ics.two_plummer(60000, seeds=(4, 5))
+    n = mass.shape[0]
+    out = []
+    for shared in (0, 64):
+        with nb.Context(n, 1.0, 0.002, 0.3, 1e-3, prec) as ctx:
+            for shape in (1, 6):
+                ctx.set_walk_shape(shape)
+                ctx.set_walk_limits(0, 0, shared)
+                a = ctx.forces(dev(pos), dev(mass)).cpu().numpy()
+                ctx.sync()
+                out.append((shared, shape, a, *ctx.counters(n)))
+    for s0, sh0, a0, pp0, pc0 in out[:2]:
+        for s1, sh1, a1, pp1, pc1 in out[2:]:
+            if sh1 == sh0:
+                assert np.array_equal(pp0, pp1) and np.array_equal(pc0, pc1)
+                assert np.sqrt(((a0 - a1) ** 2).sum() / (a0 ** 2).sum()) <= 1e-6
 
 
 @pytest.mark.parametrize("prec", [nb.FP64, nb.FP32_KAHAN])
