@@ -82,6 +82,9 @@ def parse():
     ap.add_argument("--batch-only", action="store_true",
                     help="only the 512-system forest (FP32-Kahan), one JSON line with its figures")
     ap.add_argument("--batch-steps", type=int, default=100, help="graph-replayed forest steps")
+    ap.add_argument("--walk-shape", type=int, default=None,
+                    help="use this walk launch shape instead of the autotuner's choice (profiling "
+                         "runs: the autotuner's timings are not meaningful under a profiler)")
     return ap.parse_args()
 
 
@@ -464,7 +467,11 @@ def run_ours(args):
 
     ctx = nb.Context(n, 1.0, w["eps"], w["theta"], w["dt"], prec, stream=stream)
     ctx.set_sort_mode(nb.SORT_FULL if args.sort == "full" else nb.SORT_AUTO)
-    shape, shape_ms = ctx.autotune(tp, tm)   # launch shape of the walk, before any timing
+    if args.walk_shape is None:
+        shape, shape_ms = ctx.autotune(tp, tm)   # launch shape of the walk, before any timing
+    else:
+        ctx.set_walk_shape(args.walk_shape)
+        shape, shape_ms = args.walk_shape, None
     shape_threads = ctx.walk_shape()[1]
     ctx.enable_timing(True)
     for _ in range(args.warmup):
