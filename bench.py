@@ -384,7 +384,7 @@ def measure_energy_drift(nb, torch, dev, stream):
 # the walk kernel's source: its DRAM traffic from the committed capture is reported only while
 # this file is unchanged
 WALK_SOURCES = ("paper_2203_08966_gb300/csrc/walk_kernels.cu",)
-WALK_PROFILE = "profiles/group_walk32_two_plummer_16m.md"
+WALK_PROFILE = "profiles/pb_walk32_two_plummer_16m.md"
 
 
 def walk_source_hash():
