@@ -26,3 +26,17 @@ def test_reference_arm_under_two_gloo_ranks():
     assert line["value"] > 0 and line["unit"] == "bodies/s"
     assert line["cpu_baseline"]["kind"] == "oracle"
     assert line["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_bench_energy_report_matches_the_oracle_energy():
+    """The bench's energy report uses its own numpy pair sum (the bench executes the oracle only
+    for its CPU baseline); on the 4096-body Plummer state it agrees with the oracle's §2.3 energy
+    to rounding."""
+    sys.path.insert(0, ROOT)
+    import bench
+    import ics
+    import oracle
+    w = ics.WORKLOADS["plummer_4k"]
+    pos, vel, mass = ics.plummer(w["n"], w["seed"])
+    ref = oracle.energy(pos, vel, mass, 1.0, w["eps"])[2]
+    assert abs(bench.plain_energy(pos, vel, mass, w["eps"]) - ref) <= 1e-12 * abs(ref)
