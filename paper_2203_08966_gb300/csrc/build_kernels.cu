@@ -867,60 +867,6 @@ __global__ void moments_level_kernel(int level, NodeArrays na, double G)
 // quadrupole terms, keep the means of link_leaves / moments_level, bit for bit the oracle's.
 // ------------------------------------------------------------------------------------------
 
-// Leaf sums and the level-order child / body ranges of every node (pre-order pass).
-//   com_lo[b]   leaves: (sum m x, sum m y, sum m z, sum m) of their bodies
-//   lo_child[b] (first child in level order, child count, first body, body count of a leaf)
-__global__ void leaf_sums_kernel(const uint64_t *__restrict__ keys, NodeArrays na,
-                                 const D4 *__restrict__ sbody64)
-{
-    const int n_nodes = (int)min((int64_t)*na.d_nn, na.cap);
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n_nodes; j += gridDim.x * blockDim.x) {
-        const WalkNode w = na.wn[j];
-        const int b = na.order[j];
-        if (w.count != 0) {
-            na.mask[j] = 0;
-            D4 sm = {0.0, 0.0, 0.0, 0.0};
-            for (int p = w.first; p < w.first + w.count; ++p) {
-                const D4 q = sbody64[p];
-                sm.x += q.w * q.x;
-                sm.y += q.w * q.y;
-                sm.z += q.w * q.z;
-                sm.w += q.w;
-            }
-            na.com_lo[b] = sm;
-            na.lo_child[b] = make_int4(0, 0, w.first, w.count);
-            continue;
-        }
-        const int shift = 3 * (kMaxLevel - 1 - na.level[j]);
-        unsigned mask = 0;
-        int nc = 0;
-        for (int c = j + 1; c < w.skip && nc < 8; c = max(na.wn[c].skip, c + 1), ++nc)
-            mask |= 1u << (unsigned)((keys[na.wn[c].first] >> shift) & 7u);
-        na.mask[j] = (uint8_t)mask;
-        na.lo_child[b] = make_int4(na.order[j + 1], __popc(mask), w.first, 0);
-    }
-}
-
-// The cells of one level add their children's sums (one level deeper, already done).
-__global__ void sums_level_kernel(int level, NodeArrays na)
-{
-    const int lo = (int)na.tile_offsets[level * na.tiles];
-    const int hi = (int)na.tile_offsets[(level + 1) * na.tiles];
-    for (int t = lo + blockIdx.x * blockDim.x + threadIdx.x; t < hi; t += gridDim.x * blockDim.x) {
-        const int4 ch = na.lo_child[t];
-        if (ch.y == 0) continue;  // leaf
-        D4 sm = {0.0, 0.0, 0.0, 0.0};
-        for (int k = 0; k < min(ch.y, 8); ++k) {
-            const D4 q = ld_cg(&na.com_lo[ch.x + k]);
-            sm.x += q.x;
-            sm.y += q.y;
-            sm.z += q.z;
-            sm.w += q.w;
-        }
-        na.com_lo[t] = sm;
-    }
-}
-
 // FP32 (x - c, y - c, z - c, G m) of a node from its sums: centre of mass = sums / m.
 __device__ __forceinline__ float4 com32_from_sums(const D4 &sm, const Box *bx, double G)
 {
@@ -929,32 +875,262 @@ __device__ __forceinline__ float4 com32_from_sums(const D4 &sm, const Box *bx, d
                        (float)(sm.z * r - bx->c[2]), (float)(G * sm.w));
 }
 
-// GroupNode records in level order from the sums (coalesced writes): one-body leaves copy their
-// body's FP32 record, buckets and cells form their centre of mass here.
-__global__ void group_nodes_sums_kernel(NodeArrays na, const float4 *__restrict__ sbody32,
-                                        const Box *__restrict__ box,
-                                        const LevelTables *__restrict__ tab, Systems ss, double G,
-                                        GroupNode *gn)
+// One block per pre-order tile of kSubT nodes.  A node's subtree is the pre-order range
+// [j, skip); when it ends inside the tile the block finishes the node here: a leaf's sums over its
+// bodies in sorted order, a cell's as its children's sums in octant order, level by level from
+// the deepest up, in shared memory.  Every node gets its child mask and its level-order GroupNode
+// record.  The nodes whose subtree runs past the tile are ancestors of the first node after it,
+// at most one per level: their records are written without the centre of mass, and their
+// level-order index goes to spine[level * tiles + tile] (-1 where the tile has none) for
+// spine_sums_kernel.  The FP64 pipe is narrow, so its work runs on compacted lists: the tile's
+// cells are counting-sorted by level (deepest first), and each level's cells, then all of them
+// for the centres of mass, take one thread each.
+constexpr int kSubT = 1024;
+constexpr int kSubThreads = 256;
+constexpr int kSubPer = kSubT / kSubThreads;
+
+__global__ void __launch_bounds__(kSubThreads, 4)
+subtree_sums_kernel(const uint64_t *__restrict__ keys, NodeArrays na,
+                    const D4 *__restrict__ sbody64, const float4 *__restrict__ sbody32,
+                    const Box *__restrict__ box, const LevelTables *__restrict__ tab, Systems ss,
+                    double G, GroupNode *__restrict__ gn, int4 *__restrict__ spine, int tiles)
+{
+    __shared__ D4 s_sum[kSubT];
+    __shared__ int s_skip[kSubT];          // skip - j0 (past kSubT for the spine)
+    __shared__ uint16_t s_list[kSubT];     // the tile's cells, deepest level first
+    __shared__ uint16_t s_sys[kSubT];      // system of the node
+    __shared__ uint8_t s_oct[kSubT];       // octant of the node in its parent
+    __shared__ uint8_t s_mask[kSubT];      // child mask of a cell finished here
+    __shared__ int s_cnt[kMaxLevel];       // cells per level
+    __shared__ int s_start[kMaxLevel + 1]; // start of each level's run in s_list; [kMaxLevel] all
+    __shared__ int4 s_spine[kMaxLevel];    // (level-order index, first child, child count, system)
+    const int tile = blockIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int n_nodes = (int)min((int64_t)*na.d_nn, na.cap);
+    const int j0 = tile * kSubT;
+    if (threadIdx.x < kMaxLevel) {
+        s_spine[threadIdx.x] = make_int4(-1, 0, 0, 0);
+        s_cnt[threadIdx.x] = 0;
+    }
+    __syncthreads();
+    // the loads of all four nodes first (independent of one another), then their use
+    int4 w[kSubPer];  // skip, first, count, crit bits
+    int lev[kSubPer];
+#pragma unroll
+    for (int q = 0; q < kSubPer; ++q) {
+        const int j = j0 + threadIdx.x + q * kSubThreads;
+        w[q] = make_int4(0, 0, -1, 0);
+        lev[q] = -1;
+        if (j < n_nodes) {
+            w[q] = reinterpret_cast<const int4 *>(na.wn + j)[1];
+            lev[q] = na.level[j];
+        }
+    }
+    uint64_t key[kSubPer];
+#pragma unroll
+    for (int q = 0; q < kSubPer; ++q) key[q] = lev[q] > 0 ? keys[w[q].y] : 0ull;
+    // single-body leaves: their body's record straight into the sums slot (async copy, no
+    // registers); products formed below
+#pragma unroll
+    for (int q = 0; q < kSubPer; ++q) {
+        const int i = threadIdx.x + q * kSubThreads;
+        if (w[q].z == 1) {
+            const unsigned dst = (unsigned)__cvta_generic_to_shared(&s_sum[i]);
+            const D4 *src = sbody64 + w[q].y;
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src));
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst + 16u),
+                         "l"(reinterpret_cast<const char *>(src) + 16));
+        }
+    }
+    asm volatile("cp.async.commit_group;\n" ::);
+    // cells: their rank within their level (warp-aggregated counts)
+    int rank[kSubPer];
+#pragma unroll
+    for (int q = 0; q < kSubPer; ++q) {
+        const int i = threadIdx.x + q * kSubThreads;
+        const bool cell = lev[q] >= 0 && w[q].z == 0;
+        const unsigned peers = __match_any_sync(kFull, cell ? lev[q] : -1);
+        rank[q] = 0;
+        if (cell) {
+            const int leader = __ffs(peers) - 1;
+            int base = 0;
+            if (lane == leader) base = atomicAdd(&s_cnt[lev[q]], __popc(peers));
+            base = __shfl_sync(peers, base, leader);
+            rank[q] = base + __popc(peers & lanemask_lt());
+        }
+        if (lev[q] < 0) continue;
+        s_skip[i] = w[q].x - j0;
+        s_oct[i] = lev[q] == 0 ? 0 : (uint8_t)((key[q] >> (3 * (kMaxLevel - lev[q]))) & 7u);
+        s_sys[i] = (uint16_t)system_of(ss, w[q].y);
+        if (w[q].z > 1) {  // a level-21 bucket
+            D4 sm = {0.0, 0.0, 0.0, 0.0};
+            for (int p = w[q].y; p < w[q].y + w[q].z; ++p) {
+                const D4 b = sbody64[p];
+                sm.x += b.w * b.x;
+                sm.y += b.w * b.y;
+                sm.z += b.w * b.z;
+                sm.w += b.w;
+            }
+            s_sum[i] = sm;
+        }
+    }
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+#pragma unroll
+    for (int q = 0; q < kSubPer; ++q) {
+        const int i = threadIdx.x + q * kSubThreads;
+        if (w[q].z == 1) {
+            D4 &r = s_sum[i];
+            const D4 b = r;
+            D4 sm = {0.0, 0.0, 0.0, 0.0};
+            sm.x += b.w * b.x;
+            sm.y += b.w * b.y;
+            sm.z += b.w * b.z;
+            sm.w += b.w;
+            r = sm;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int acc = 0;
+        for (int l = kMaxLevel - 1; l >= 0; --l) {
+            s_start[l] = acc;
+            acc += s_cnt[l];
+        }
+        s_start[kMaxLevel] = acc;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < kSubPer; ++q)
+        if (lev[q] >= 0 && w[q].z == 0)
+            s_list[s_start[lev[q]] + rank[q]] = (uint16_t)(threadIdx.x + q * kSubThreads);
+    __syncthreads();
+    // cells whose subtree ends in the tile, deepest level first: children one level deeper are
+    // done; a cell has at most 8 children (the bound also ends a malformed skip chain)
+    for (int l = kMaxLevel - 1; l >= 0; --l) {
+        const int e = s_start[l] + s_cnt[l];
+        if (s_cnt[l] == 0) continue;  // the same for the whole block
+        for (int t = s_start[l] + threadIdx.x; t < e; t += kSubThreads) {
+            const int i = s_list[t];
+            const int sk = s_skip[i];
+            if (sk > kSubT) continue;  // spine cell: later
+            D4 sm = {0.0, 0.0, 0.0, 0.0};
+            unsigned m = 0;
+            int k = 0;
+            for (int c = i + 1; c < sk && k < 8; c = max(s_skip[c], c + 1), ++k) {
+                const D4 r = s_sum[c];
+                sm.x += r.x;
+                sm.y += r.y;
+                sm.z += r.z;
+                sm.w += r.w;
+                m |= 1u << s_oct[c];
+            }
+            s_sum[i] = sm;
+            s_mask[i] = (uint8_t)m;
+        }
+        __syncthreads();
+    }
+    // centres of mass of the cells finished here (all lanes busy), with their FP64 sums
+    for (int t = threadIdx.x; t < s_start[kMaxLevel]; t += kSubThreads) {
+        const int i = s_list[t];
+        if (s_skip[i] > kSubT) continue;
+        const int b = na.order[j0 + i];
+        const D4 sm = s_sum[i];
+        na.com_lo[b] = sm;
+        reinterpret_cast<float4 *>(gn + b)[0] = com32_from_sums(sm, box + s_sys[i], G);
+    }
+    // the rest of every record: the loads of all four nodes first
+    int b[kSubPer], nxt[kSubPer];
+    float4 c1[kSubPer];
+#pragma unroll
+    for (int q = 0; q < kSubPer; ++q) {
+        const int j = j0 + threadIdx.x + q * kSubThreads;
+        b[q] = 0;
+        nxt[q] = 0;
+        c1[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (lev[q] >= 0) {
+            b[q] = na.order[j];
+            if (w[q].z == 0) nxt[q] = na.order[j + 1];
+            if (w[q].z == 1) c1[q] = sbody32[w[q].y];
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < kSubPer; ++q) {
+        const int i = threadIdx.x + q * kSubThreads;
+        const int j = j0 + i;
+        if (lev[q] < 0) continue;
+        const int k = s_sys[i];
+        if (w[q].z != 0) {
+            const D4 sm = s_sum[i];
+            GroupNode g;
+            g.c = w[q].z == 1 ? c1[q] : com32_from_sums(sm, box + k, G);
+            g.child = w[q].y;
+            g.n = -w[q].z;
+            g.crit = 0.f;
+            g.pre = j;
+            gn[b[q]] = g;
+            na.com_lo[b[q]] = sm;
+            na.mask[j] = 0;
+        } else {
+            unsigned m;
+            if (w[q].x <= j0 + kSubT) {
+                m = s_mask[i];
+            } else {
+                // a spine cell: its children's octants, past the tile from the keys
+                const int shift = 3 * (kMaxLevel - 1 - lev[q]);
+                m = 0;
+                int k8 = 0;
+                for (int c = j + 1; c < w[q].x && k8 < 8; ++k8) {
+                    int nc;
+                    if (c < j0 + kSubT) {
+                        nc = s_skip[c - j0] + j0;
+                        m |= 1u << s_oct[c - j0];
+                    } else {
+                        const int2 v = reinterpret_cast<const int2 *>(na.wn + c)[2];  // skip, first
+                        nc = v.x;
+                        m |= 1u << (unsigned)((keys[v.y] >> shift) & 7u);
+                    }
+                    c = max(nc, c + 1);
+                }
+                s_spine[lev[q]] = make_int4(b[q], nxt[q], __popc(m), k);
+            }
+            reinterpret_cast<int4 *>(gn + b[q])[1] =
+                make_int4(nxt[q], __popc(m), __float_as_int(tab[k].crit32[lev[q]]), j);
+            na.mask[j] = (uint8_t)m;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < kMaxLevel && tile < tiles) spine[threadIdx.x * tiles + tile] = s_spine[threadIdx.x];
+}
+
+// The spine cells of one level (one per tile at most): sums of their children (finished by
+// subtree_sums_kernel or by this kernel at a deeper level) in octant order, and the centre of
+// mass of their record.  Launched for the levels from the deepest up to the roots.
+__global__ void spine_sums_kernel(int level, NodeArrays na, const Box *__restrict__ box, double G,
+                                  GroupNode *__restrict__ gn, const int4 *__restrict__ spine,
+                                  int tiles)
 {
     const int n_nodes = (int)min((int64_t)*na.d_nn, na.cap);
-    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < n_nodes; b += gridDim.x * blockDim.x) {
-        const int j = na.inv[b];
-        const int4 lc = na.lo_child[b];
-        const int k = system_of(ss, lc.z);
-        GroupNode g;
-        g.pre = j;
-        if (lc.y == 0) {
-            g.c = lc.w == 1 ? sbody32[lc.z] : com32_from_sums(na.com_lo[b], box + k, G);
-            g.child = lc.z;
-            g.n = -lc.w;
-            g.crit = 0.f;
-        } else {
-            g.c = com32_from_sums(na.com_lo[b], box + k, G);
-            g.child = lc.x;
-            g.n = lc.y;
-            g.crit = tab[k].crit32[na.level[j]];
+    const int used = min(tiles, (n_nodes + kSubT - 1) / kSubT);
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < used; t += gridDim.x * blockDim.x) {
+        const int4 e = spine[level * tiles + t];  // (level-order index, first child, count, system)
+        if (e.x < 0) continue;
+        const int nc = min(e.z, 8);
+        D4 q[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            if (k < nc) q[k] = ld_cg(&na.com_lo[e.y + k]);
+        D4 sm = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            if (k < nc) {
+                sm.x += q[k].x;
+                sm.y += q[k].y;
+                sm.z += q[k].z;
+                sm.w += q[k].w;
+            }
         }
-        gn[b] = g;
+        na.com_lo[e.x] = sm;
+        reinterpret_cast<float4 *>(gn + e.x)[0] = com32_from_sums(sm, box + e.w, G);
     }
 }
 
@@ -1470,27 +1646,24 @@ void launch_moments(const uint64_t *keys, int max_level, const D4 *sbody64, cons
     count_launches(1 + max(0, depth));
 }
 
-void launch_moments_sums(const uint64_t *keys, int max_level, const D4 *sbody64,
-                         const Systems &ss, NodeArrays na, cudaStream_t s)
+int subtree_tiles(int64_t cap)
 {
-    const int64_t cap = na.cap;
-    leaf_sums_kernel<<<grid_for(cap, 256, kMaxGrid * 4), 256, 0, s>>>(keys, na, sbody64);
-    const int depth = min(max_level, kMaxLevel);
-    for (int lev = depth - 1; lev >= 0; --lev) {
-        const int64_t widest = lev < 10 ? ((int64_t)ss.count << (3 * lev)) : cap;
-        const int g = grid_for(std::min<int64_t>(widest, cap), 256, kMaxGrid * 2);
-        sums_level_kernel<<<g, 256, 0, s>>>(lev, na);
-    }
-    count_launches(1 + max(0, depth));
+    return (int)((std::max<int64_t>(cap, 1) + kSubT - 1) / kSubT);
 }
 
-void launch_group_nodes_sums(const NodeArrays &na, const float4 *sbody32, const Box *box,
-                             const LevelTables *tab, const Systems &ss, double G, GroupNode *gn,
-                             cudaStream_t s)
+void launch_subtree_sums(const uint64_t *keys, int max_level, const D4 *sbody64,
+                         const float4 *sbody32, const Box *box, const LevelTables *tab,
+                         const Systems &ss, double G, NodeArrays na, GroupNode *gn,
+                         cudaStream_t s)
 {
-    group_nodes_sums_kernel<<<grid_for(na.cap, 256, kMaxGrid * 4), 256, 0, s>>>(
-        na, sbody32, box, tab, ss, G, gn);
-    count_launches(1);
+    const int tiles = subtree_tiles(na.cap);
+    subtree_sums_kernel<<<tiles, kSubThreads, 0, s>>>(keys, na, sbody64, sbody32, box, tab, ss, G,
+                                                      gn, na.spine, tiles);
+    const int depth = min(max_level, kMaxLevel);
+    const int g = grid_for(tiles, 256, kMaxGrid);
+    for (int lev = depth - 1; lev >= 0; --lev)
+        spine_sums_kernel<<<g, 256, 0, s>>>(lev, na, box, G, gn, na.spine, tiles);
+    count_launches(1 + max(0, depth));
 }
 
 void launch_group_nodes(const NodeArrays &na, const Box *box, const LevelTables *tab,

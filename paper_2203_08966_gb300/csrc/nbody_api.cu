@@ -202,6 +202,7 @@ void free_nodes(nbody_ctx *c)
     dfree(c->na.inv);
     dfree(c->na.com_lo);
     dfree(c->na.lo_child);
+    dfree(c->na.spine);
     dfree(c->na.tile_offsets);
     dfree(c->na.block_sums);
     dfree(c->gn);
@@ -249,6 +250,7 @@ nbody_status ensure_nodes(nbody_ctx *c, int64_t need)
     CK(dalloc(&c->na.inv, cap));
     CK(dalloc(&c->na.com_lo, cap));
     CK(dalloc(&c->na.lo_child, cap));
+    CK(dalloc(&c->na.spine, (size_t)kMaxLevel * subtree_tiles(cap)));
     const int len = layout_scan_len(cap);
     CK(dalloc(&c->na.tile_offsets, (size_t)len));
     CK(dalloc(&c->na.block_sums, (size_t)scan_tiles(len) + 1));
@@ -520,8 +522,8 @@ nbody_status build(nbody_ctx *c, const double *pos, const double *mass, int n,
     launch_emit_nodes(c->keys, n, one, c->node_off, c->na, c->err, s);
     launch_level_order(c->na, s);
     if (sums_moments(c)) {
-        launch_moments_sums(c->keys, max_level, c->sbody64, one, c->na, s);
-        launch_group_nodes_sums(c->na, c->sbody32, c->box, c->tab, one, c->p.G, c->gn, s);
+        launch_subtree_sums(c->keys, max_level, c->sbody64, c->sbody32, c->box, c->tab, one,
+                            c->p.G, c->na, c->gn, s);
     } else {
         launch_moments(c->keys, max_level, c->sbody64, c->box, c->tab, one, c->p.G, c->na, s);
         if (group) launch_group_nodes(c->na, c->box, c->tab, one, c->p.G, c->gn, s);
@@ -638,8 +640,8 @@ nbody_status forest_build(nbody_ctx *c, double *pos, const double *mass, double 
     launch_emit_nodes(c->keys, n, ss, c->node_off, c->na, c->err, s);
     launch_level_order(c->na, s);
     if (sums_moments(c)) {
-        launch_moments_sums(c->keys, kMaxLevel, c->sbody64, ss, c->na, s);
-        launch_group_nodes_sums(c->na, c->sbody32, c->box, c->tab, ss, c->p.G, c->gn, s);
+        launch_subtree_sums(c->keys, kMaxLevel, c->sbody64, c->sbody32, c->box, c->tab, ss,
+                            c->p.G, c->na, c->gn, s);
     } else {
         launch_moments(c->keys, kMaxLevel, c->sbody64, c->box, c->tab, ss, c->p.G, c->na, s);
         if (!is_fp64(c->p.precision))

@@ -86,6 +86,29 @@ def test_keys_sort_box_tree_moments_bit_exact(name):
     assert np.array_equal(mom, t.moments())
 
 
+@pytest.mark.parametrize("prec", [nb.FP32, nb.FP32_KAHAN])
+@pytest.mark.parametrize("name", sorted(CASES) + ["plummer_200000"])
+def test_fp32_tree_moments_match_the_oracle(name, prec):
+    """FP32 contexts keep FP64 sums (sum m x, sum m y, sum m z, sum m) in the tree: leaves over
+    their bodies in sorted order, cells over their children in octant order, finished per
+    pre-order tile of the tree and, for the cells whose subtree crosses a tile's end, level by
+    level afterwards.  Masses are the oracle's Algorithm 2 masses bit for bit (the same sums in
+    the same order); the centres of mass the library reports (sums / m) agree with the oracle's
+    means to FP64 rounding, within 1e-12 of the box side."""
+    pos, _, mass = CASES[name] if name in CASES else ics.plummer(200000, 9)
+    n = mass.shape[0]
+    with nb.Context(n, precision=prec) as ctx:
+        ctx.build_tree(dev(pos), dev(mass))
+        rec = ctx.tree()
+        mom = ctx.moments()
+        side = ctx.box()[3]
+    t = oracle.Tree(pos, mass)
+    assert np.array_equal(rec, t.records())
+    ref = t.moments()
+    assert np.array_equal(mom[:, 0], ref[:, 0])
+    assert np.max(np.abs(mom[:, 1:] - ref[:, 1:])) <= 1e-12 * side
+
+
 @pytest.mark.parametrize("name", sorted(CASES))
 @pytest.mark.parametrize("theta", [0.0, 0.3, 0.5, 0.7, 1.0])
 def test_fp64_forces_and_counters_bit_exact(name, theta):
