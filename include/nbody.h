@@ -205,8 +205,11 @@ nbody_status nbody_get_tree(nbody_ctx *c, int64_t *n_nodes, nbody_tree_record *h
 
 /* FP64 moments of the last build, pre-order: h_out[4*k .. 4*k+3] = (m, x, y, z) of node k.
  * FP64 contexts (and quadrupole contexts) form every cell's centre of mass from its children's
- * as the oracle does, bit for bit; the other FP32 contexts keep FP64 sums (sum m, sum m r) in
- * the tree, and their centres of mass, sum m r / sum m, differ from those by rounding. */
+ * as the oracle does, bit for bit; the other FP32 contexts build from FP64 sums (sum m, sum m r,
+ * a cell adding its children's in octant order), so their masses are the oracle's bit for bit
+ * and their centres of mass, sum m r / sum m, differ from its means by rounding.  Those contexts
+ * keep only the sums their build reads, so this call runs the sums pass again on the same tree
+ * (on the context's stream, synchronised) before copying them. */
 nbody_status nbody_get_moments(nbody_ctx *c, double *h_out, int64_t cap_nodes);
 
 /* Interaction counters of the last force evaluation, user order (n entries each). */

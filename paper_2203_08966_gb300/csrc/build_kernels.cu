@@ -882,7 +882,8 @@ __device__ __forceinline__ float4 com32_from_sums(const D4 &sm, const Box *bx, d
 // record.  The nodes whose subtree runs past the tile are ancestors of the first node after it,
 // at most one per level: their records are written without the centre of mass, and their
 // level-order index goes to spine[level * tiles + tile] (-1 where the tile has none) for
-// spine_sums_kernel.  The FP64 pipe is narrow, so its work runs on compacted lists: the tile's
+// spine_sums_kernel.  com_lo keeps the FP64 sums of the nodes the spine cells read (those whose
+// parent is not finished in the same tile), or of every node with all_sums.  The FP64 pipe is narrow, so its work runs on compacted lists: the tile's
 // cells are counting-sorted by level (deepest first), and each level's cells, then all of them
 // for the centres of mass, take one thread each.
 constexpr int kSubT = 1024;
@@ -893,7 +894,8 @@ __global__ void __launch_bounds__(kSubThreads, 4)
 subtree_sums_kernel(const uint64_t *__restrict__ keys, NodeArrays na,
                     const D4 *__restrict__ sbody64, const float4 *__restrict__ sbody32,
                     const Box *__restrict__ box, const LevelTables *__restrict__ tab, Systems ss,
-                    double G, GroupNode *__restrict__ gn, int4 *__restrict__ spine, int tiles)
+                    double G, GroupNode *__restrict__ gn, int4 *__restrict__ spine, int tiles,
+                    int all_sums)
 {
     __shared__ D4 s_sum[kSubT];
     __shared__ int s_skip[kSubT];          // skip - j0 (past kSubT for the spine)
@@ -901,6 +903,7 @@ subtree_sums_kernel(const uint64_t *__restrict__ keys, NodeArrays na,
     __shared__ uint16_t s_sys[kSubT];      // system of the node
     __shared__ uint8_t s_oct[kSubT];       // octant of the node in its parent
     __shared__ uint8_t s_mask[kSubT];      // child mask of a cell finished here
+    __shared__ uint8_t s_in[kSubT];        // its parent is finished here too
     __shared__ int s_cnt[kMaxLevel];       // cells per level
     __shared__ int s_start[kMaxLevel + 1]; // start of each level's run in s_list; [kMaxLevel] all
     __shared__ int4 s_spine[kMaxLevel];    // (level-order index, first child, child count, system)
@@ -960,6 +963,7 @@ subtree_sums_kernel(const uint64_t *__restrict__ keys, NodeArrays na,
         }
         if (lev[q] < 0) continue;
         s_skip[i] = w[q].x - j0;
+        s_in[i] = 0;
         s_oct[i] = lev[q] == 0 ? 0 : (uint8_t)((key[q] >> (3 * (kMaxLevel - lev[q]))) & 7u);
         s_sys[i] = (uint16_t)system_of(ss, w[q].y);
         if (w[q].z > 1) {  // a level-21 bucket
@@ -1023,6 +1027,7 @@ subtree_sums_kernel(const uint64_t *__restrict__ keys, NodeArrays na,
                 sm.z += r.z;
                 sm.w += r.w;
                 m |= 1u << s_oct[c];
+                s_in[c] = 1;
             }
             s_sum[i] = sm;
             s_mask[i] = (uint8_t)m;
@@ -1035,7 +1040,7 @@ subtree_sums_kernel(const uint64_t *__restrict__ keys, NodeArrays na,
         if (s_skip[i] > kSubT) continue;
         const int b = na.order[j0 + i];
         const D4 sm = s_sum[i];
-        na.com_lo[b] = sm;
+        if (all_sums || !s_in[i]) na.com_lo[b] = sm;
         reinterpret_cast<float4 *>(gn + b)[0] = com32_from_sums(sm, box + s_sys[i], G);
     }
     // the rest of every record: the loads of all four nodes first
@@ -1068,7 +1073,7 @@ subtree_sums_kernel(const uint64_t *__restrict__ keys, NodeArrays na,
             g.crit = 0.f;
             g.pre = j;
             gn[b[q]] = g;
-            na.com_lo[b[q]] = sm;
+            if (all_sums || !s_in[i]) na.com_lo[b[q]] = sm;
             na.mask[j] = 0;
         } else {
             unsigned m;
@@ -1654,11 +1659,11 @@ int subtree_tiles(int64_t cap)
 void launch_subtree_sums(const uint64_t *keys, int max_level, const D4 *sbody64,
                          const float4 *sbody32, const Box *box, const LevelTables *tab,
                          const Systems &ss, double G, NodeArrays na, GroupNode *gn,
-                         cudaStream_t s)
+                         bool all_sums, cudaStream_t s)
 {
     const int tiles = subtree_tiles(na.cap);
     subtree_sums_kernel<<<tiles, kSubThreads, 0, s>>>(keys, na, sbody64, sbody32, box, tab, ss, G,
-                                                      gn, na.spine, tiles);
+                                                      gn, na.spine, tiles, all_sums ? 1 : 0);
     const int depth = min(max_level, kMaxLevel);
     const int g = grid_for(tiles, 256, kMaxGrid);
     for (int lev = depth - 1; lev >= 0; --lev)

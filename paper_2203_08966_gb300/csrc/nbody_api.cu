@@ -523,7 +523,7 @@ nbody_status build(nbody_ctx *c, const double *pos, const double *mass, int n,
     launch_level_order(c->na, s);
     if (sums_moments(c)) {
         launch_subtree_sums(c->keys, max_level, c->sbody64, c->sbody32, c->box, c->tab, one,
-                            c->p.G, c->na, c->gn, s);
+                            c->p.G, c->na, c->gn, false, s);
     } else {
         launch_moments(c->keys, max_level, c->sbody64, c->box, c->tab, one, c->p.G, c->na, s);
         if (group) launch_group_nodes(c->na, c->box, c->tab, one, c->p.G, c->gn, s);
@@ -641,7 +641,7 @@ nbody_status forest_build(nbody_ctx *c, double *pos, const double *mass, double 
     launch_level_order(c->na, s);
     if (sums_moments(c)) {
         launch_subtree_sums(c->keys, kMaxLevel, c->sbody64, c->sbody32, c->box, c->tab, ss,
-                            c->p.G, c->na, c->gn, s);
+                            c->p.G, c->na, c->gn, false, s);
     } else {
         launch_moments(c->keys, kMaxLevel, c->sbody64, c->box, c->tab, ss, c->p.G, c->na, s);
         if (!is_fp64(c->p.precision))
@@ -1055,7 +1055,12 @@ nbody_status nbody_get_moments(nbody_ctx *c, double *h_out, int64_t cap_nodes)
     std::vector<D4> m((size_t)nn);
     CK(cudaStreamSynchronize(c->stream));
     if (sums_moments(c)) {
-        // the tree holds FP64 sums in level order: centre of mass = sums / mass
+        // the build keeps FP64 sums only where its own passes read them: the sums pass runs
+        // again on the same tree with every node's sums kept (centre of mass = sums / mass)
+        const Systems one{nullptr, nullptr, 1};
+        launch_subtree_sums(c->keys, kMaxLevel, c->sbody64, c->sbody32, c->box, c->tab, one,
+                            c->p.G, c->na, c->gn, true, c->stream);
+        CK(cudaStreamSynchronize(c->stream));
         std::vector<D4> sm((size_t)nn);
         std::vector<int> inv((size_t)nn);
         CK(cudaMemcpy(sm.data(), c->na.com_lo, sizeof(D4) * nn, cudaMemcpyDeviceToHost));

@@ -232,16 +232,16 @@ int layout_scan_len(int64_t n_nodes);
 // mass relative to its system's origin and its level's FP32 threshold are made here.
 void launch_group_nodes(const NodeArrays &na, const Box *box, const LevelTables *tab,
                         const Systems &ss, double G, GroupNode *gn, cudaStream_t s);
-// FP32 contexts without quadrupoles: every node's FP64 sums (sum m x, sum m y, sum m z, sum m)
-// in com_lo, its child mask, and its GroupNode record with the FP32 centre of mass formed from
-// those sums (one FP64 reciprocal per node); one pass over pre-order tiles, then the tiles'
-// spine cells level by level (levels max_level - 1 .. 0).  lo_child, kind and com64 are not
-// written.
+// FP32 contexts without quadrupoles: every node's FP64 sums (sum m x, sum m y, sum m z, sum m),
+// its child mask, and its GroupNode record with the FP32 centre of mass formed from those sums
+// (one FP64 reciprocal per node); one pass over pre-order tiles, then the tiles' spine cells
+// level by level (levels max_level - 1 .. 0).  com_lo receives the sums the spine cells read, or
+// every node's with all_sums (nbody_get_moments).  lo_child, kind and com64 are not written.
 int subtree_tiles(int64_t cap);
 void launch_subtree_sums(const uint64_t *keys, int max_level, const D4 *sbody64,
                          const float4 *sbody32, const Box *box, const LevelTables *tab,
                          const Systems &ss, double G, NodeArrays na, GroupNode *gn,
-                         cudaStream_t s);
+                         bool all_sums, cudaStream_t s);
 // Walk groups that follow the tree: every cell of at most gmax bodies whose parent holds more
 // (consecutive such siblings merged while they fit in gmax), buckets of more than gmax bodies cut
 // into chunks.  (first body, count, system, 0) entries, *ngroups of them (zeroed by the caller);
