@@ -1427,7 +1427,8 @@ __global__ void __launch_bounds__(kThreads) walk64_kernel(WalkArgs a)
 // ------------------------------------------------------------------------------------------
 
 constexpr int kDirectThreads = 256;   // FP64 direct sum
-constexpr int kD32Threads = 128;      // FP32 direct sum: targets per block
+constexpr int kD32Threads = 128;      // FP32 direct sum: threads per block
+constexpr int kD32Per = 2;            // targets per thread
 constexpr int kD32Tile = 256;         // sources per shared-memory tile
 constexpr int kD32MinChunk = 4096;    // sources per block at least
 
@@ -1442,23 +1443,28 @@ __global__ void direct32_prep_kernel(const double *__restrict__ pos, const doubl
                              (float)(pos[2 * (size_t)n + j] - cz), (float)(G * mass[j]));
 }
 
-// One block: kD32Threads targets against one chunk of the sources (blockIdx.y), two sources at a
-// time with packed FP32 arithmetic.  A target meets itself in its own chunk at zero separation,
-// which adds exactly zero.  Partial sums go to part[chunk][3][nt].
+// One block: kD32Threads * kD32Per targets against one chunk of the sources (blockIdx.y), two
+// sources at a time with packed FP32 arithmetic; each thread keeps kD32Per targets, so a source
+// pair read from shared memory serves all of them.  A target meets itself in its own chunk at
+// zero separation, which adds exactly zero.  Partial sums go to part[chunk][3][nt].
 template <bool kGuard>
 __global__ void __launch_bounds__(kD32Threads) direct32_chunk_kernel(
     const float4 *__restrict__ src, int n, const int64_t *__restrict__ targets, int nt,
     float eps2s, int chunk, float *__restrict__ part)
 {
     __shared__ float4 tile[kD32Tile];   // pair-interleaved (see put_entry)
-    const int t = blockIdx.x * kD32Threads + threadIdx.x;
-    const bool live = t < nt;
-    const int i = live ? (targets ? (int)targets[t] : t) : 0;
-    const float4 me = src[i];
-    const float2 nme[3] = {make_float2(-me.x, -me.x), make_float2(-me.y, -me.y),
-                           make_float2(-me.z, -me.z)};
     const float2 eps2 = make_float2(eps2s, eps2s);
-    float2 ax = make_float2(0.f, 0.f), ay = ax, az = ax;
+    float2 nme[kD32Per][3], ax[kD32Per], ay[kD32Per], az[kD32Per];
+#pragma unroll
+    for (int k = 0; k < kD32Per; ++k) {
+        const int t = (blockIdx.x * kD32Per + k) * kD32Threads + threadIdx.x;
+        const int i = t < nt ? (targets ? (int)targets[t] : t) : 0;
+        const float4 me = src[i];
+        nme[k][0] = make_float2(-me.x, -me.x);
+        nme[k][1] = make_float2(-me.y, -me.y);
+        nme[k][2] = make_float2(-me.z, -me.z);
+        ax[k] = ay[k] = az[k] = make_float2(0.f, 0.f);
+    }
     const int lo = blockIdx.y * chunk, hi = min(n, lo + chunk);
     for (int base = lo; base < hi; base += kD32Tile) {
         __syncthreads();
@@ -1468,15 +1474,22 @@ __global__ void __launch_bounds__(kD32Threads) direct32_chunk_kernel(
         }
         __syncthreads();
         const int pairs = (min(kD32Tile, hi - base) + 1) >> 1;
-#pragma unroll 4
-        for (int q = 0; q < pairs; ++q)
-            pair32x2<kGuard>(tile[2 * q], tile[2 * q + 1], nme[0], nme[1], nme[2], eps2, ax, ay, az);
+#pragma unroll 2
+        for (int q = 0; q < pairs; ++q) {
+            const float4 u = tile[2 * q], v = tile[2 * q + 1];
+#pragma unroll
+            for (int k = 0; k < kD32Per; ++k)
+                pair32x2<kGuard>(u, v, nme[k][0], nme[k][1], nme[k][2], eps2, ax[k], ay[k], az[k]);
+        }
     }
-    if (live) {
+#pragma unroll
+    for (int k = 0; k < kD32Per; ++k) {
+        const int t = (blockIdx.x * kD32Per + k) * kD32Threads + threadIdx.x;
+        if (t >= nt) continue;
         float *o = part + (size_t)blockIdx.y * 3 * nt;
-        o[t] = ax.x + ax.y;
-        o[(size_t)nt + t] = ay.x + ay.y;
-        o[2 * (size_t)nt + t] = az.x + az.y;
+        o[t] = ax[k].x + ax[k].y;
+        o[(size_t)nt + t] = ay[k].x + ay[k].y;
+        o[2 * (size_t)nt + t] = az[k].x + az[k].y;
     }
 }
 
@@ -1763,9 +1776,10 @@ void launch_walk(int precision, const WalkArgs &a, int shape, cudaStream_t s)
 
 int direct32_chunks(int n, int nt)
 {
-    // enough blocks for every SM several times over, chunks of at least kD32MinChunk sources
-    const int tblocks = (nt + kD32Threads - 1) / kD32Threads;
-    int chunks = (152 * 8 + tblocks - 1) / std::max(1, tblocks);
+    // about 64 blocks per SM (16,384 targets x 1M sources: 49 TFLOP/s with 8 per SM, 52.7 with
+    // 32, 53.1 with 64), chunks of at least kD32MinChunk sources
+    const int tblocks = (nt + kD32Threads * kD32Per - 1) / (kD32Threads * kD32Per);
+    int chunks = (152 * 64 + tblocks - 1) / std::max(1, tblocks);
     chunks = std::min(chunks, std::max(1, n / kD32MinChunk));
     return std::max(1, chunks);
 }
@@ -1790,7 +1804,7 @@ void launch_direct(int precision, const double *pos, const double *mass, int n,
     const int chunk = (n + chunks - 1) / chunks;
     direct32_prep_kernel<<<std::min((n + 255) / 256, 152 * 16), 256, 0, s>>>(pos, mass, n, G, box,
                                                                             sc.src);
-    const dim3 grid((nt + kD32Threads - 1) / kD32Threads, chunks);
+    const dim3 grid((nt + kD32Threads * kD32Per - 1) / (kD32Threads * kD32Per), chunks);
     const float eps2 = (float)(eps * eps);
     if (eps > 0.0)
         direct32_chunk_kernel<false><<<grid, kD32Threads, 0, s>>>(sc.src, n, targets, nt, eps2,
