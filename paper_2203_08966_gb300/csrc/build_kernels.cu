@@ -134,8 +134,25 @@ __global__ void __launch_bounds__(kBoxThreads) bbox_partials_kernel(const double
     block_reduce10(v, partials + kPart * blockIdx.x);
 }
 
-// Kick and drift of the leapfrog (eqs. leapkick1, leapdrift of §2.4), FP64 with separately
-// rounded products and sums, fused with the box and centre-of-mass partials of the new positions.
+// One kick-and-drift coordinate (eqs. leapkick1, leapdrift of §2.4) in FP64: separately rounded
+// products and sums as the oracle does them (FP64 contexts), or fused multiply-adds (FP32
+// contexts, whose forces are FP32 anyway: half the FP64 operations, which bound these passes on
+// GB300's narrow FP64 pipe).
+template <bool kFused>
+__device__ __forceinline__ void kick_drift1(double &v, double &x, double a, double h, double dt)
+{
+    if (kFused) {
+        v = __fma_rn(a, h, v);
+        x = __fma_rn(v, dt, x);
+    } else {
+        v = __dadd_rn(v, __dmul_rn(a, h));
+        x = __dadd_rn(x, __dmul_rn(v, dt));
+    }
+}
+
+// Kick and drift of the leapfrog (eqs. leapkick1, leapdrift of §2.4), fused with the box and
+// centre-of-mass partials of the new positions.
+template <bool kFused>
 __global__ void __launch_bounds__(kBoxThreads) kick_drift_bbox_kernel(
     double *__restrict__ pos, double *__restrict__ vel, const double *__restrict__ acc,
     const double *__restrict__ mass, int n, double h, double dt, double *partials,
@@ -148,8 +165,9 @@ __global__ void __launch_bounds__(kBoxThreads) kick_drift_bbox_kernel(
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
             const size_t k = (size_t)d * n + i;
-            const double vh = __dadd_rn(vel[k], __dmul_rn(acc[k], h));
-            x[d] = __dadd_rn(pos[k], __dmul_rn(vh, dt));
+            double vh = vel[k];
+            x[d] = pos[k];
+            kick_drift1<kFused>(vh, x[d], acc[k], h, dt);
             vel[k] = vh;
             pos[k] = x[d];
         }
@@ -221,6 +239,7 @@ __global__ void __launch_bounds__(kBoxThreads) bbox_finalize_kernel(const double
 // with a step's kick and drift fused in when vel is non-null (the same operations as
 // kick_drift_bbox_kernel), writing the (x, y, z, m) records.  chunks[b] = (first body, end,
 // system).
+template <bool kFused>
 __global__ void __launch_bounds__(kBoxThreads) forest_box_partials_kernel(
     double *__restrict__ pos, double *__restrict__ vel, const double *__restrict__ acc,
     const double *__restrict__ mass, int n, const int4 *__restrict__ chunks, double h, double dt,
@@ -235,9 +254,10 @@ __global__ void __launch_bounds__(kBoxThreads) forest_box_partials_kernel(
         for (int d = 0; d < 3; ++d) {
             const size_t k = (size_t)d * n + i;
             if (vel) {
-                const double vh = __dadd_rn(vel[k], __dmul_rn(acc[k], h));
+                double vh = vel[k];
+                r[d] = pos[k];
+                kick_drift1<kFused>(vh, r[d], acc[k], h, dt);
                 vel[k] = vh;
-                r[d] = __dadd_rn(pos[k], __dmul_rn(vh, dt));
                 pos[k] = r[d];
             } else {
                 r[d] = pos[k];
@@ -1431,11 +1451,15 @@ void launch_bbox_partials(const double *pos, const double *mass, int n, double *
 }
 
 void launch_kick_drift_bbox(double *pos, double *vel, const double *acc, const double *mass, int n,
-                            double h, double dt, double *partials, int nblk, D4 *aos,
+                            double h, double dt, double *partials, int nblk, D4 *aos, bool fused,
                             cudaStream_t s)
 {
-    kick_drift_bbox_kernel<<<nblk, kBoxThreads, 0, s>>>(pos, vel, acc, mass, n, h, dt, partials,
-                                                        aos);
+    if (fused)
+        kick_drift_bbox_kernel<true><<<nblk, kBoxThreads, 0, s>>>(pos, vel, acc, mass, n, h, dt,
+                                                                  partials, aos);
+    else
+        kick_drift_bbox_kernel<false><<<nblk, kBoxThreads, 0, s>>>(pos, vel, acc, mass, n, h, dt,
+                                                                   partials, aos);
     count_launches(1);
 }
 
@@ -1449,11 +1473,14 @@ void launch_bbox_finalize(const double *partials, int nblk, Box *box, LevelTable
 void launch_forest_boxes(double *pos, double *vel, const double *acc, const double *mass, int n,
                          const int4 *chunks, int nchunks, const int *chunk_start, int n_sys,
                          double h, double dt, double *partials, Box *box, LevelTables *tab,
-                         double theta, D4 *aos, cudaStream_t s)
+                         double theta, D4 *aos, bool fused, cudaStream_t s)
 {
-    if (nchunks > 0)
-        forest_box_partials_kernel<<<nchunks, kBoxThreads, 0, s>>>(pos, vel, acc, mass, n, chunks,
-                                                                   h, dt, partials, aos);
+    if (nchunks > 0 && fused)
+        forest_box_partials_kernel<true><<<nchunks, kBoxThreads, 0, s>>>(
+            pos, vel, acc, mass, n, chunks, h, dt, partials, aos);
+    else if (nchunks > 0)
+        forest_box_partials_kernel<false><<<nchunks, kBoxThreads, 0, s>>>(
+            pos, vel, acc, mass, n, chunks, h, dt, partials, aos);
     forest_box_finalize_kernel<<<n_sys, kBoxThreads, 0, s>>>(partials, chunk_start, box, tab,
                                                              theta);
     count_launches(nchunks > 0 ? 2 : 1);

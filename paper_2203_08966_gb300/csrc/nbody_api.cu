@@ -625,7 +625,7 @@ nbody_status forest_build(nbody_ctx *c, double *pos, const double *mass, double 
     if (c->p.flags & NBODY_FLAG_CHECK_FINITE) launch_check_finite(pos, mass, n, c->err, s);
     launch_forest_boxes(pos, vel, c->acc, mass, n, c->box_chunks, c->n_box_chunks,
                         c->box_chunk_start, c->n_sys, h, c->p.dt, c->box_partials, c->box, c->tab,
-                        c->p.theta, c->aos, s);
+                        c->p.theta, c->aos, !is_fp64(c->p.precision), s);
     SortScratch sc{c->keys_alt, c->ids_alt, c->hist, c->counts, sort_tiles(n), c->sys,
                    c->sys_hist};
     CKS(sort_bodies(c, pos, n, ss, sc));
@@ -688,7 +688,7 @@ nbody_status step_once(nbody_ctx *c, double *pos, double *vel, const double *mas
     const double h = 0.5 * c->p.dt;
     CKS(begin_timing(c));
     launch_kick_drift_bbox(pos, vel, c->acc, mass, (int)n, h, c->p.dt, c->partials, c->nblk,
-                           c->aos, c->stream);
+                           c->aos, !is_fp64(c->p.precision), c->stream);
     CKS(check_launch(c, "kick/drift"));
     if (drifted) CK(cudaEventRecord(drifted, c->stream));
     CKS(build(c, pos, mass, (int)n, true));

@@ -108,7 +108,7 @@ void launch_bbox_partials(const double *pos, const double *mass, int n, double *
                           int nblk, D4 *aos, cudaStream_t s);
 void launch_kick_drift_bbox(double *pos, double *vel, const double *acc, const double *mass,
                             int n, double h, double dt, double *partials, int nblk, D4 *aos,
-                            cudaStream_t s);
+                            bool fused, cudaStream_t s);
 void launch_bbox_finalize(const double *partials, int nblk, Box *box, LevelTables *tab,
                           double theta, cudaStream_t s);
 constexpr int kForestBoxChunk = 4096;  // forest: bodies per partial-box block
@@ -118,7 +118,7 @@ constexpr int kForestBoxChunk = 4096;  // forest: bodies per partial-box block
 void launch_forest_boxes(double *pos, double *vel, const double *acc, const double *mass, int n,
                          const int4 *chunks, int nchunks, const int *chunk_start, int n_sys,
                          double h, double dt, double *partials, Box *box, LevelTables *tab,
-                         double theta, D4 *aos, cudaStream_t s);
+                         double theta, D4 *aos, bool fused, cudaStream_t s);
 // gate (may be null): a device count; the kernel does nothing when it is 0.
 void launch_keys(const double *pos, int n, const Box *box, const Systems &ss, uint64_t *keys,
                  uint32_t *ids, cudaStream_t s, const int *gate = nullptr);
