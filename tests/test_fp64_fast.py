@@ -14,7 +14,7 @@ pytestmark = pytest.mark.gpu
 import paper_2203_08966_gb300 as nb  # noqa: E402
 
 DEV = "cuda:0"
-TOL = 1e-12   # relative RMS; the benchmark spec FP64 bar is 1e-6
+TOL = 1e-12   # relative RMS; the FP64 force bar is 1e-6
 
 
 @pytest.fixture(scope="module", autouse=True)
