@@ -258,6 +258,19 @@ def measure_batch(nb, torch, dev, stream, steps=100, with_fp64=True):
     ev[3].record(stream)
     torch.cuda.synchronize()
     ctx.sync()
+    # the walk of one force evaluation of the same forest: its useful FP32 rate (outside the
+    # timed region), against the FP32 peak of the main line
+    ctx.enable_timing(True)
+    acc = ctx.forest_forces(tp, tm)
+    acc = ctx.forest_forces(tp, tm, acc)
+    walk_ms = float(ctx.timings()[3])
+    pp, pc = ctx.counters(n)
+    ctx.enable_timing(False)
+    inter = float(pp.astype(np.float64).sum() + pc.astype(np.float64).sum())
+    peaks, _ = load_peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak_tf = sms * FP32_LANES_PER_SM * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    tf = inter * FLOP_PER_INTERACTION / (walk_ms * 1e-3) / 1e12
     ctx.close()
     ms = ev[0].elapsed_time(ev[1])
     ms_launched = ev[2].elapsed_time(ev[3]) / k
@@ -281,6 +294,8 @@ def measure_batch(nb, torch, dev, stream, steps=100, with_fp64=True):
             "gpu_launches": int(launches), "precision": "fp32_kahan",
             "walk_shape": {"chosen": shape, "threads_per_block": shape_threads,
                            "autotune_ms": shape_ms},
+            "walk": {"ms": walk_ms, "interactions": inter, "achieved_tflops": tf,
+                     "peak_tflops": peak_tf, "frac": tf / peak_tf, "bound": "alu"},
             "theta": w["theta"], "eps": w["eps"], "dt": w["dt"]}
 
 
