@@ -157,7 +157,9 @@ nbody_status nbody_forces(nbody_ctx *c, const double *d_pos, const double *d_mas
                           double *d_acc);
 
 /* Advances d_pos/d_vel in place by nsteps kick-drift-kick steps of the context's dt (§2.4):
- * v += a dt/2; r += v dt; a = BH(r); v += a dt/2.  The acceleration at the current positions
+ * v += a dt/2; r += v dt; a = BH(r); v += a dt/2, in FP64 (FP64 contexts round every product
+ * and sum separately, as the oracle does; FP32 contexts take the first kick and the drift as
+ * FP64 fused multiply-adds).  The acceleration at the current positions
  * is kept in the context between calls; the first call after create, set_params or a change
  * of n computes it first.  Synchronises once per step (node count), twice when the step
  * re-sorts from the previous order.  nsteps >= 0. */
