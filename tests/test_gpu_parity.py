@@ -109,6 +109,25 @@ def test_fp32_tree_moments_match_the_oracle(name, prec):
     assert np.max(np.abs(mom[:, 1:] - ref[:, 1:])) <= 1e-12 * side
 
 
+def test_fp32_tree_moments_after_steps():
+    """nbody_get_moments of an FP32 context after leapfrog steps: the sums pass runs again on
+    the tree of the last build (the positions of the last drift, which the final kick leaves
+    unchanged), so the moments match the oracle's tree of the current positions."""
+    pos, vel, mass = ics.two_plummer(20000, seeds=(14, 15))
+    tp, tv, tm = dev(pos), dev(vel), dev(mass)
+    with nb.Context(20000, 1.0, 0.01, 0.5, 1e-3, nb.FP32_KAHAN) as ctx:
+        ctx.step(tp, tv, tm, 3)
+        ctx.sync()
+        mom = ctx.moments()
+        side = ctx.box()[3]
+    p = tp.cpu().numpy()
+    t = oracle.Tree(p, mass)
+    ref = t.moments()
+    assert mom.shape == ref.shape
+    assert np.array_equal(mom[:, 0], ref[:, 0])
+    assert np.max(np.abs(mom[:, 1:] - ref[:, 1:])) <= 1e-12 * side
+
+
 @pytest.mark.parametrize("name", sorted(CASES))
 @pytest.mark.parametrize("theta", [0.0, 0.3, 0.5, 0.7, 1.0])
 def test_fp64_forces_and_counters_bit_exact(name, theta):
