@@ -218,10 +218,11 @@ nbody_status nbody_get_moments(nbody_ctx *c, double *h_out, int64_t cap_nodes);
 nbody_status nbody_get_counters(nbody_ctx *c, uint32_t *h_pp, uint32_t *h_pc);
 
 /* Device time in milliseconds of the phases of the last build/force/step call (for
- * nbody_step: of its last step), measured with CUDA events recorded on the context stream:
- * [0] kick/drift + box + keys (re-sort: + the extract phase), [1] sort (radix sort, or the
- * re-sort's merge phase), [2] permutation + node split + moments, [3] walk, [4] whole call.  Recorded only while timing is enabled with nbody_enable_timing;
- * nbody_get_timings waits for the last call's final event. */
+ * nbody_step: of its last step; for a forest, of its last nbody_forest_forces), measured with
+ * CUDA events recorded on the context stream: [0] kick/drift + box + keys (re-sort: + the
+ * extract phase), [1] sort (radix sort, or the re-sort's merge phase), [2] permutation + node
+ * split + moments, [3] walk, [4] whole call.  Recorded only while timing is enabled with
+ * nbody_enable_timing; nbody_get_timings waits for the last call's final event. */
 nbody_status nbody_enable_timing(nbody_ctx *c, int32_t on);
 nbody_status nbody_get_timings(nbody_ctx *c, float *h_ms5);
 

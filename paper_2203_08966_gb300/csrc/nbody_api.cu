@@ -629,6 +629,7 @@ nbody_status forest_build(nbody_ctx *c, double *pos, const double *mass, double 
     SortScratch sc{c->keys_alt, c->ids_alt, c->hist, c->counts, sort_tiles(n), c->sys,
                    c->sys_hist};
     CKS(sort_bodies(c, pos, n, ss, sc));
+    record(c, 2);
     launch_permute(c->aos, c->ids, n, c->box, ss, c->p.G, c->sbody64, c->sbody32, s);
     CK(cudaMemsetAsync(c->info, 0, sizeof(unsigned), s));
     launch_count_nodes(c->keys, n, ss, c->node_off, c->info, s);
@@ -653,6 +654,7 @@ nbody_status forest_build(nbody_ctx *c, double *pos, const double *mass, double 
         launch_cell_groups(c->na, c->node_off, ss, n, 32, c->cgroups, c->cgroups_n, c->cap + 1,
                            c->err, s);
     }
+    record(c, 3);
     CKS(check_launch(c, "forest build"));
     c->n_built = n;
     c->n_nodes = -1;  // on the device only
